@@ -1,0 +1,408 @@
+/*
+ * FP64 CPU oracle for the partial-ADMM deconvolution with incomplete
+ * observations (Simoes, Almeida, Bioucas-Dias, Chanussot, arXiv:1602.01410).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code with the
+ * CUDA path: its convolutions are direct spatial sums, its DFT is its own
+ * recursive mixed-radix transform, and its solve follows the paper's steps in
+ * the paper's order.  It is deliberately plain and slow.
+ *
+ * Layout: images are row-major M x N doubles (M rows of the extended grid,
+ * Sec. I-A); C channels are stacked [C][M][N] (Sec. III-C, demosaicing).  The
+ * kernel h is (2b+1) x (2b+1) row-major with its origin at h[b][b].
+ *
+ * Parity status: every function here is pinned by the CPU test suite
+ * (naive DFT and numpy.fft for the FFT, scipy convolution for the blurs,
+ * adjoint identities, brute-force prox, normal equations, Lemma 3
+ * monotonicity, the lambda = 0 closed form and a dense standard-ADMM run).
+ * The gradient (reverse pass) is pinned by central finite differences and a
+ * dot-product test.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef double complex cplx;
+
+/* ---------------------------------------------------------------- DFT ---
+ * X[k] = sum_n x[n] exp(sign * 2 pi i n k / L).  Recursive decimation in time
+ * on the smallest prime factor p of L: L = p m, the p interleaved
+ * sub-sequences x[p j + r] are transformed (length m), then combined with
+ * X[k + q m] = sum_r exp(sign 2 pi i r (k + q m) / L) Y_r[k].  Plain
+ * textbook Cooley-Tukey; a prime length is a direct DFT.
+ */
+static int smallest_factor(int n) {
+  for (int p = 2; p * p <= n; ++p)
+    if (n % p == 0) return p;
+  return n;
+}
+
+/* Roots of unity of the top-level length L, tw[k] = exp(sign 2 pi i k / L),
+ * from libm cos/sin in double; a sub-transform of length n uses
+ * exp(sign 2 pi i idx / n) = tw[(idx mod n) * (L / n)]. */
+typedef struct {
+  int L;
+  cplx *tw;
+} roots;
+
+static roots make_roots(int L, int sign) {
+  roots r = {L, malloc(sizeof(cplx) * (size_t)L)};
+  for (int k = 0; k < L; ++k) {
+    double a = sign * 2.0 * M_PI * (double)k / (double)L;
+    r.tw[k] = cos(a) + I * sin(a);
+  }
+  return r;
+}
+
+static void fft_rec(const cplx *in, int stride, cplx *out, int n, const roots *w, cplx *scratch) {
+  if (n == 1) {
+    out[0] = in[0];
+    return;
+  }
+  int p = smallest_factor(n);
+  int m = n / p;
+  int step = w->L / n;
+  for (int r = 0; r < p; ++r) fft_rec(in + (size_t)r * stride, stride * p, out + (size_t)r * m, m, w, scratch);
+  for (int q = 0; q < p; ++q)
+    for (int k = 0; k < m; ++k) {
+      cplx acc = 0;
+      for (int r = 0; r < p; ++r) acc += out[(size_t)r * m + k] * w->tw[(size_t)((r * (k + q * m)) % n) * step];
+      scratch[(size_t)q * m + k] = acc;
+    }
+  memcpy(out, scratch, sizeof(cplx) * (size_t)n);
+}
+
+/* In-place 1-D DFT of n interleaved (re, im) doubles; unnormalised. */
+int or_fft1d(double *data, int n, int sign) {
+  if (n <= 0) return -1;
+  cplx *in = malloc(sizeof(cplx) * n), *out = malloc(sizeof(cplx) * n), *scr = malloc(sizeof(cplx) * n);
+  roots w = make_roots(n, sign);
+  for (int i = 0; i < n; ++i) in[i] = data[2 * i] + I * data[2 * i + 1];
+  fft_rec(in, 1, out, n, &w, scr);
+  free(w.tw);
+  for (int i = 0; i < n; ++i) {
+    data[2 * i] = creal(out[i]);
+    data[2 * i + 1] = cimag(out[i]);
+  }
+  free(in); free(out); free(scr);
+  return 0;
+}
+
+/* 2-D DFT of an M x N complex array: every row, then every column. */
+static void fft2(cplx *a, int M, int N, int sign) {
+  roots wr = make_roots(N, sign), wc = make_roots(M, sign);
+#pragma omp parallel
+  {
+    int L = M > N ? M : N;
+    cplx *in = malloc(sizeof(cplx) * L), *out = malloc(sizeof(cplx) * L), *scr = malloc(sizeof(cplx) * L);
+#pragma omp for
+    for (int i = 0; i < M; ++i) {
+      fft_rec(a + (size_t)i * N, 1, out, N, &wr, scr);
+      memcpy(a + (size_t)i * N, out, sizeof(cplx) * N);
+    }
+#pragma omp for
+    for (int j = 0; j < N; ++j) {
+      for (int i = 0; i < M; ++i) in[i] = a[(size_t)i * N + j];
+      fft_rec(in, 1, out, M, &wc, scr);
+      for (int i = 0; i < M; ++i) a[(size_t)i * N + j] = out[i];
+    }
+    free(in); free(out); free(scr);
+  }
+  free(wr.tw);
+  free(wc.tw);
+}
+
+int or_fft2d(double *data, int M, int N, int sign) {
+  size_t P = (size_t)M * N;
+  cplx *a = malloc(sizeof(cplx) * P);
+  for (size_t i = 0; i < P; ++i) a[i] = data[2 * i] + I * data[2 * i + 1];
+  fft2(a, M, N, sign);
+  for (size_t i = 0; i < P; ++i) {
+    data[2 * i] = creal(a[i]);
+    data[2 * i + 1] = cimag(a[i]);
+  }
+  free(a);
+  return 0;
+}
+
+/* ------------------------------------------------------ blur operators ---
+ * Eq. (4): T~ is the BCCB matrix of the circular convolution with h on the
+ * M x N grid, (T~x)[i][j] = sum_{p,q=-b..b} h[p+b][q+b] x[(i-p)%M][(j-q)%N].
+ * Eq. (1): T is the linear 'valid' convolution, defined on the central
+ * (M-2b) x (N-2b) region.  Both are written as direct sums.
+ */
+static inline int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+/* Periodic extension of x by b pixels on every side: xp[i+b][j+b] = x[i%M][j%N]. */
+static double *periodic_pad(const double *x, int M, int N, int b) {
+  int W = N + 2 * b;
+  double *xp = malloc(sizeof(double) * (size_t)(M + 2 * b) * W);
+  for (int i = -b; i < M + b; ++i)
+    for (int j = -b; j < N + b; ++j) xp[(size_t)(i + b) * W + (j + b)] = x[(size_t)wrap(i, M) * N + wrap(j, N)];
+  return xp;
+}
+
+void or_conv_circ(const double *x, int M, int N, const double *h, int K, double *out) {
+  int b = K / 2, W = N + 2 * b;
+  double *xp = periodic_pad(x, M, N, b);
+#pragma omp parallel for
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < N; ++j) {
+      double s = 0.0;
+      for (int p = -b; p <= b; ++p)
+        for (int q = -b; q <= b; ++q) s += h[(p + b) * K + (q + b)] * xp[(size_t)(i - p + b) * W + (j - q + b)];
+      out[(size_t)i * N + j] = s;
+    }
+  free(xp);
+}
+
+/* T~^T: circular correlation, (T~^T y)[i][j] = sum h[p+b][q+b] y[(i+p)%M][(j+q)%N]. */
+void or_conv_circ_adj(const double *y, int M, int N, const double *h, int K, double *out) {
+  int b = K / 2, W = N + 2 * b;
+  double *yp = periodic_pad(y, M, N, b);
+#pragma omp parallel for
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < N; ++j) {
+      double s = 0.0;
+      for (int p = -b; p <= b; ++p)
+        for (int q = -b; q <= b; ++q) s += h[(p + b) * K + (q + b)] * yp[(size_t)(i + p + b) * W + (j + q + b)];
+      out[(size_t)i * N + j] = s;
+    }
+  free(yp);
+}
+
+/* T x on the valid region: out[(i-b)][(j-b)] for i in [b, M-b), j in [b, N-b). */
+void or_conv_valid(const double *x, int M, int N, const double *h, int K, double *out) {
+  int b = K / 2, m = M - 2 * b, n = N - 2 * b;
+#pragma omp parallel for
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int p = -b; p <= b; ++p)
+        for (int q = -b; q <= b; ++q) s += h[(p + b) * K + (q + b)] * x[(size_t)(i + b - p) * N + (j + b - q)];
+      out[(size_t)i * n + j] = s;
+    }
+}
+
+/* -------------------------------------------------- first differences ---
+ * Sec. III-B (isotropic TV): D_h, D_v are horizontal and vertical first-order
+ * differences with periodic boundaries; here forward differences,
+ * (D_h x)[i][j] = x[i][j+1] - x[i][j], (D_v x)[i][j] = x[i+1][j] - x[i][j].
+ */
+void or_diff_fwd(const double *x, int M, int N, double *dh, double *dv) {
+#pragma omp parallel for
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < N; ++j) {
+      double c = x[(size_t)i * N + j];
+      dh[(size_t)i * N + j] = x[(size_t)i * N + wrap(j + 1, N)] - c;
+      dv[(size_t)i * N + j] = x[(size_t)wrap(i + 1, M) * N + j] - c;
+    }
+}
+
+/* D^T [u_h; u_v] = D_h^T u_h + D_v^T u_v, the transpose of or_diff_fwd. */
+void or_diff_adj(const double *uh, const double *uv, int M, int N, double *out) {
+#pragma omp parallel for
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < N; ++j) {
+      size_t o = (size_t)i * N + j;
+      out[o] = uh[(size_t)i * N + wrap(j - 1, N)] - uh[o] + uv[(size_t)wrap(i - 1, M) * N + j] - uv[o];
+    }
+}
+
+/* ----------------------------------------------------- vector soft ---
+ * Sec. III-B: the prox of tau * sum_j ||a_j|| (isotropic, or vectorial over
+ * channels for Sec. III-C demosaicing) is the vector soft-threshold,
+ * v_j = max(||a_j|| - tau, 0) a_j / ||a_j||, v_j = 0 when ||a_j|| <= tau.
+ * a is laid out as `dim` planes of n values; the norm at pixel j runs over the
+ * planes.
+ */
+void or_vsoft(const double *a, int n, int dim, double tau, double *v) {
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int c = 0; c < dim; ++c) s += a[(size_t)c * n + j] * a[(size_t)c * n + j];
+    double nrm = sqrt(s);
+    double g = nrm > tau ? (nrm - tau) / nrm : 0.0;
+    for (int c = 0; c < dim; ++c) v[(size_t)c * n + j] = g * a[(size_t)c * n + j];
+  }
+}
+
+/* ------------------------------------------------------- x-step solve ---
+ * Eq. (dual_x_iter_resolved_boundaries): x = (H^T H + mu D^T D)^{-1} rhs with
+ * H^T H = T~^T T~ (BCCB) and D^T D BCCB; the paper solves it in the DFT
+ * domain.  The eigenvalues of the BCCB matrix A = T~^T T~ + mu D^T D are the
+ * DFT of its first column, A e_0, which is computed here with the spatial
+ * operators above: den = DFT2(A e_0).
+ */
+static double *solve_denominator(int M, int N, const double *h, int K, double mu) {
+  size_t P = (size_t)M * N;
+  double *e = calloc(P, sizeof(double)), *t = malloc(P * sizeof(double)), *a = malloc(P * sizeof(double));
+  double *uh = malloc(P * sizeof(double)), *uv = malloc(P * sizeof(double)), *dd = malloc(P * sizeof(double));
+  e[0] = 1.0;
+  or_conv_circ(e, M, N, h, K, t);
+  or_conv_circ_adj(t, M, N, h, K, a);
+  or_diff_fwd(e, M, N, uh, uv);
+  or_diff_adj(uh, uv, M, N, dd);
+  cplx *s = malloc(sizeof(cplx) * P);
+  for (size_t i = 0; i < P; ++i) s[i] = a[i] + mu * dd[i];
+  fft2(s, M, N, -1);
+  double *den = malloc(P * sizeof(double));
+  for (size_t i = 0; i < P; ++i) den[i] = creal(s[i]); /* A is symmetric: real spectrum */
+  free(e); free(t); free(a); free(uh); free(uv); free(dd); free(s);
+  return den;
+}
+
+static void solve_x(const double *rhs, const double *den, int M, int N, double *x, cplx *work) {
+  size_t P = (size_t)M * N;
+  for (size_t i = 0; i < P; ++i) work[i] = rhs[i];
+  fft2(work, M, N, -1);
+  for (size_t i = 0; i < P; ++i) work[i] /= den[i];
+  fft2(work, M, N, +1);
+  for (size_t i = 0; i < P; ++i) x[i] = creal(work[i]) / (double)P;
+}
+
+/* Public wrapper for tests: x = (T~^T T~ + mu D^T D)^{-1} rhs. */
+void or_solve_x(const double *rhs, int M, int N, const double *h, int K, double mu, double *x) {
+  double *den = solve_denominator(M, N, h, K, mu);
+  cplx *w = malloc(sizeof(cplx) * (size_t)M * N);
+  solve_x(rhs, den, M, N, x, w);
+  free(den); free(w);
+}
+
+/* ------------------------------------------------------ initial state ---
+ * Sec. III-B: x is initialised by padding the observed image with its
+ * border pixels.  Reading used here (the paper is silent on interior holes):
+ * an unobserved pixel of the boundary band takes the value at the clamped
+ * valid-region index when that pixel is observed; every other unobserved
+ * pixel takes the mean of the observed values of its channel (computed in
+ * double, then rounded once with `round_f32`).  y~0 is that padded image.
+ */
+void or_init_ytilde(const double *y, const uint8_t *mask, int M, int N, int K, int round_f32, double *yt) {
+  int b = K / 2;
+  double s = 0.0;
+  long cnt = 0;
+  for (size_t i = 0; i < (size_t)M * N; ++i)
+    if (mask[i]) {
+      s += y[i];
+      ++cnt;
+    }
+  double mean = cnt ? s / (double)cnt : 0.0;
+  if (round_f32) mean = (double)(float)mean;
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < N; ++j) {
+      size_t o = (size_t)i * N + j;
+      if (mask[o]) {
+        yt[o] = y[o];
+        continue;
+      }
+      int band = (i < b || i >= M - b || j < b || j >= N - b);
+      double v = mean;
+      if (band) {
+        int ic = i < b ? b : (i >= M - b ? M - b - 1 : i);
+        int jc = j < b ? b : (j >= N - b ? N - b - 1 : j);
+        size_t oc = (size_t)ic * N + jc;
+        if (mask[oc]) v = y[oc];
+      }
+      yt[o] = v;
+    }
+}
+
+/* ------------------------------------------------------ partial ADMM ---
+ * Eqs. (admm_aprox_1)-(admm_aprox_4) with one block-Gauss-Seidel pass, the
+ * closed forms (dual_x_iter_resolved_boundaries) for x and the over-relaxed
+ * z-update z = relax * M_z H x - (relax - 1) z (relax = 2 in Sec. II-B,
+ * relax = 1 is the plain Eq. (dual_z_iter_resolved_boundaries)).  C channels
+ * share the blur; the TV norm couples them (vectorial TV, Sec. III-C).
+ *
+ * State (in/out when init == 0, out when init == 1): yt = y~ (observed
+ * entries hold y, unobserved hold z), d = d_x as [C][2][M][N] (h then v
+ * component), v = v_x with the same layout.  Output x = x^{iters}.
+ * stats (nullable) receives per iteration
+ *   [ ||d^{i+1}-d^i||^2, ||z^{i+1}-z^i||^2, mu ||v^{i+1}-v^i||^2, J(x^{i+1}) ]
+ * with J(x) = 1/2 sum_obs (y - T~x)^2 + lambda sum_j ||(Dx)_j||, the
+ * objective of Eq. (problem_xz) minimised over z.
+ */
+int or_admm(int C, int M, int N, int K, const double *h, const double *y, const uint8_t *mask,
+            double lambda, double mu, double relax, int iters, int init, int round_f32,
+            double *yt, double *d, double *v, double *x, double *stats) {
+  size_t P = (size_t)M * N;
+  double *den = solve_denominator(M, N, h, K, mu);
+  double *rhs = malloc(P * sizeof(double)), *tmp = malloc(P * sizeof(double));
+  double *dx = malloc(2 * C * P * sizeof(double)), *a = malloc(2 * C * P * sizeof(double));
+  double *vn = malloc(2 * C * P * sizeof(double));
+  cplx *work = malloc(sizeof(cplx) * P);
+
+  if (init) {
+    for (int c = 0; c < C; ++c) {
+      or_init_ytilde(y + c * P, mask + c * P, M, N, K, round_f32, yt + c * P);
+      or_diff_fwd(yt + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P); /* v0 = D x0, x0 = y~0 */
+    }
+    memset(d, 0, 2 * C * P * sizeof(double));
+  }
+  for (int it = 0; it < iters; ++it) {
+    /* (admm_aprox_1): x = (H^T H + mu D^T D)^{-1} [H^T [y; z] + mu D^T (v - d)] */
+    for (int c = 0; c < C; ++c) {
+      double *uh = a + 2 * c * P, *uv = a + (2 * c + 1) * P;
+      for (size_t i = 0; i < P; ++i) {
+        uh[i] = v[2 * c * P + i] - d[2 * c * P + i];
+        uv[i] = v[(2 * c + 1) * P + i] - d[(2 * c + 1) * P + i];
+      }
+      or_diff_adj(uh, uv, M, N, tmp);
+      or_conv_circ_adj(yt + c * P, M, N, h, K, rhs);
+      for (size_t i = 0; i < P; ++i) rhs[i] += mu * tmp[i];
+      solve_x(rhs, den, M, N, x + c * P, work);
+    }
+    /* (admm_aprox_2), over-relaxed: z = relax M_z H x - (relax - 1) z */
+    double dz2 = 0.0;
+    for (int c = 0; c < C; ++c) {
+      or_conv_circ(x + c * P, M, N, h, K, tmp);
+      for (size_t i = 0; i < P; ++i)
+        if (!mask[c * P + i]) {
+          double zn = relax * tmp[i] - (relax - 1.0) * yt[c * P + i];
+          dz2 += (zn - yt[c * P + i]) * (zn - yt[c * P + i]);
+          yt[c * P + i] = zn;
+        }
+    }
+    /* (admm_aprox_3): v = vector-soft(D x + d, lambda / mu) */
+    for (int c = 0; c < C; ++c) or_diff_fwd(x + c * P, M, N, dx + 2 * c * P, dx + (2 * c + 1) * P);
+    for (size_t i = 0; i < 2 * C * P; ++i) a[i] = dx[i] + d[i];
+    or_vsoft(a, (int)P, 2 * C, lambda / mu, vn);
+    /* (admm_aprox_4): d = d - (v - D x) = a - v */
+    double dd2 = 0.0, dv2 = 0.0;
+    for (size_t i = 0; i < 2 * C * P; ++i) {
+      double dn = a[i] - vn[i];
+      dd2 += (dn - d[i]) * (dn - d[i]);
+      dv2 += (vn[i] - v[i]) * (vn[i] - v[i]);
+      d[i] = dn;
+      v[i] = vn[i];
+    }
+    if (stats) {
+      double fit = 0.0, tv = 0.0;
+      for (int c = 0; c < C; ++c) {
+        or_conv_circ(x + c * P, M, N, h, K, tmp);
+        for (size_t i = 0; i < P; ++i)
+          if (mask[c * P + i]) fit += (y[c * P + i] - tmp[i]) * (y[c * P + i] - tmp[i]);
+      }
+      for (size_t i = 0; i < P; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < 2 * C; ++k) s += dx[k * P + i] * dx[k * P + i];
+        tv += sqrt(s);
+      }
+      stats[4 * it + 0] = dd2;
+      stats[4 * it + 1] = dz2;
+      stats[4 * it + 2] = mu * dv2;
+      stats[4 * it + 3] = 0.5 * fit + lambda * tv;
+    }
+  }
+  free(den); free(rhs); free(tmp); free(dx); free(a); free(vn); free(work);
+  return 0;
+}

@@ -1,0 +1,205 @@
+"""Pins of the oracle's partial-ADMM iteration (no GPU).
+
+* T5  x-step: the normal equations of Eq. (dual_x_iter_resolved_boundaries)
+      hold when evaluated with the spatial operators.
+* z-, v-, d-steps: Eq. (admm_aprox_2) over-relaxed, (admm_aprox_3),
+      (admm_aprox_4) wiring after one iteration.
+* T6  Lemma 3: with one BGS pass and no over-relaxation, the G-norm of
+      w^{i+1} - w^i, G = diag(I_d, mu I, mu I), never increases.
+* T7  lambda = 0 with every pixel observed: each DFT coefficient follows
+      X^{n} = X* + rho^n (X^0 - X*), rho = mu|D|^2 / (|H|^2 + mu|D|^2),
+      X* = Y / H (derived from the x-step closed form).
+* T8  KKT conditions (proof of Lemma 2, Eqs. (primal)-(dual_v_x)) at a
+      converged run.
+* T9  the converged x is no worse than random perturbations of it for the
+      objective of Eq. (problem_xz) minimised over z.
+* T11 standard ADMM (Eqs. (admm_xz_1)-(admm_xz_3)) with a dense joint solve
+      reaches the same minimiser as the partial ADMM (Sec. III-B reports that
+      different correct solvers agree to RMSE 1e-7).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_01410_gb300 import inputs
+
+
+def small_problem(seed=0, M=12, N=14, K=3, frac=0.3, lam=2e-3, mu=5e-2):
+    rng = np.random.default_rng(seed)
+    b = K // 2
+    x = inputs.scene_shapes(rng, M, N)
+    h = inputs.psf_gaussian(K, 0.8)
+    m = inputs.mask_random_missing(rng, M, N, b, frac)
+    y = inputs.observe(rng, x, h, m, 40.0)
+    return x, y, m, h, lam, mu
+
+
+def test_x_step_satisfies_normal_equations():
+    x_true, y, m, h, lam, mu = small_problem(1)
+    rng = np.random.default_rng(2)
+    M, N = y.shape
+    st = oracle.State(rng.standard_normal((1, M, N)), rng.standard_normal((1, 2, M, N)),
+                      rng.standard_normal((1, 2, M, N)))
+    x1, st1, _ = oracle.admm(y[None], m[None], h, lam, mu, 1, relax=2.0, state=st)
+    x1 = x1[0]
+    rhs = oracle.conv_circ_adj(st.yt[0], h) + mu * oracle.diff_adj(st.v[0, 0] - st.d[0, 0], st.v[0, 1] - st.d[0, 1])
+    lhs = oracle.conv_circ_adj(oracle.conv_circ(x1, h), h) + mu * oracle.diff_adj(*oracle.diff_fwd(x1))
+    assert np.linalg.norm(lhs - rhs) <= 1e-12 * np.linalg.norm(rhs)
+    # z-step (over-relaxed), observed entries unchanged
+    t = oracle.conv_circ(x1, h)
+    obs = m != 0
+    assert np.array_equal(st1.yt[0][obs], st.yt[0][obs])
+    assert np.allclose(st1.yt[0][~obs], 2 * t[~obs] - st.yt[0][~obs], rtol=0, atol=1e-13)
+    # v-step and d-step
+    a = np.stack(oracle.diff_fwd(x1)) + st.d[0]
+    v = oracle.vsoft(a, lam / mu)
+    assert np.allclose(st1.v[0], v, rtol=0, atol=1e-14)
+    assert np.allclose(st1.d[0], st.d[0] - (v - np.stack(oracle.diff_fwd(x1))), rtol=0, atol=1e-13)
+
+
+def test_lemma3_gnorm_monotone_relax1():
+    x_true, y, m, h, lam, mu = small_problem(3, M=16, N=16, K=5)
+    _, _, s = oracle.admm(y[None], m[None], h, lam, mu, 400, relax=1.0, stats=True)
+    g = s[:, 1] + s[:, 2] + mu * s[:, 0]
+    # Lemma 2 uses the optimality conditions of the previous iteration, so the
+    # sequence is compared from the second difference on.
+    inc = g[2:] - g[1:-1]
+    assert np.all(inc <= 1e-12 * g[1:-1] + 1e-28), inc.max()
+    assert g[-1] < 1e-3 * g[1]
+
+
+def test_lambda0_full_observation_closed_form():
+    rng = np.random.default_rng(4)
+    M, N, K, mu = 16, 20, 5, 0.3
+    h = inputs.psf_gaussian(K, 0.7)
+    y = rng.random((M, N))
+    m = np.ones((M, N), np.uint8)
+    n_it = 7
+    x, st, _ = oracle.admm(y[None], m[None], h, 0.0, mu, n_it, relax=2.0, round_f32=False)
+    assert np.all(st.d == 0)
+    g = np.zeros((M, N))
+    b = K // 2
+    for p in range(-b, b + 1):
+        for q in range(-b, b + 1):
+            g[p % M, q % N] += h[p + b, q + b]
+    H = np.fft.fft2(g)
+    k1 = np.arange(M)[:, None]
+    k2 = np.arange(N)[None, :]
+    D2 = 4 * np.sin(np.pi * k1 / M) ** 2 + 4 * np.sin(np.pi * k2 / N) ** 2
+    rho = mu * D2 / (np.abs(H) ** 2 + mu * D2)
+    Y = np.fft.fft2(y)
+    Xs = Y / H
+    Xn = Xs + rho ** n_it * (Y - Xs)
+    want = np.real(np.fft.ifft2(Xn))
+    assert np.max(np.abs(x[0] - want)) < 1e-9 * np.max(np.abs(want))
+
+
+def objective(x, y, m, h, lam):
+    t = oracle.conv_circ(x, h)
+    dh, dv = oracle.diff_fwd(x)
+    return 0.5 * np.sum(((y - t) ** 2)[m != 0]) + lam * np.sum(np.sqrt(dh * dh + dv * dv))
+
+
+@pytest.fixture(scope="module")
+def converged():
+    x_true, y, m, h, lam, mu = small_problem(5, M=10, N=10, K=3, frac=0.2, lam=1e-2, mu=2e-2)
+    x, st, s = oracle.admm(y[None], m[None], h, lam, mu, 30000, relax=2.0, stats=True)
+    return x[0], st, s, y, m, h, lam, mu
+
+
+def test_kkt_at_convergence(converged):
+    x, st, s, y, m, h, lam, mu = converged
+    yt = st.yt[0]
+    d = st.d[0]
+    # z = M_z T~ x  (Eq. (dual_z_iter_resolved_boundaries) at the fixed point)
+    t = oracle.conv_circ(x, h)
+    assert np.max(np.abs((yt - t)[m == 0])) < 1e-9
+    # -mu D^T d = grad_x f = T~^T (T~ x - y~)   (Eq. (dual_x))
+    r = oracle.conv_circ_adj(t - yt, h) + mu * oracle.diff_adj(d[0], d[1])
+    assert np.max(np.abs(r)) < 1e-9
+    # mu d_j in the subdifferential of lambda ||.|| at (Dx)_j   (Eq. (dual_v_x))
+    nrm = mu * np.sqrt(d[0] ** 2 + d[1] ** 2)
+    assert np.all(nrm <= lam * (1 + 1e-9))
+    dh, dv = oracle.diff_fwd(x)
+    g = np.sqrt(dh ** 2 + dv ** 2)
+    active = g > 1e-7
+    assert np.allclose(nrm[active], lam, rtol=1e-6)
+    cosang = (dh * d[0] + dv * d[1])[active] / (g[active] * np.sqrt(d[0] ** 2 + d[1] ** 2)[active])
+    assert np.all(cosang > 1 - 1e-6)
+
+
+def test_objective_minimal_against_perturbations(converged):
+    x, st, s, y, m, h, lam, mu = converged
+    j0 = objective(x, y, m, h, lam)
+    assert np.isclose(s[-1, 3], j0, rtol=1e-12)
+    rng = np.random.default_rng(0)
+    for scale in (1e-2, 1e-4, 1e-6):
+        for _ in range(20):
+            assert objective(x + scale * rng.standard_normal(x.shape), y, m, h, lam) >= j0 - 1e-15
+
+
+def dense_standard_admm(y, m, h, lam, mu, iters):
+    """Standard ADMM on u = [x; z] with a dense joint solve (Eqs. (admm_xz_1)-(admm_xz_3))."""
+    M, N = y.shape
+    P = M * N
+    K = h.shape[0]
+    b = K // 2
+    T = np.zeros((P, P))
+    for i in range(M):
+        for j in range(N):
+            for p in range(-b, b + 1):
+                for q in range(-b, b + 1):
+                    T[i * N + j, ((i - p) % M) * N + (j - q) % N] += h[p + b, q + b]
+    E = np.eye(P)
+    Dh = np.zeros((P, P))
+    Dv = np.zeros((P, P))
+    for i in range(M):
+        for j in range(N):
+            Dh[i * N + j, i * N + (j + 1) % N] += 1
+            Dv[i * N + j, ((i + 1) % M) * N + j] += 1
+    Dh -= E
+    Dv -= E
+    D = np.vstack([Dh, Dv])
+    obs = m.ravel() != 0
+    Sy, Sz = E[:, obs], E[:, ~obs]
+    yo = y.ravel()[obs]
+    d_ = Sz.shape[1]
+    A = np.block([[T.T @ T + mu * D.T @ D, -T.T @ Sz], [-Sz.T @ T, (1 + mu) * np.eye(d_)]])
+    Ainv = np.linalg.inv(A)
+    vx = np.zeros(2 * P)
+    dx = np.zeros(2 * P)
+    vz = np.zeros(d_)
+    dz = np.zeros(d_)
+    for _ in range(iters):
+        rhs = np.concatenate([T.T @ Sy @ yo + mu * D.T @ (vx - dx), mu * (vz - dz)])
+        u = Ainv @ rhs
+        x, z = u[:P], u[P:]
+        a = D @ x + dx
+        ah, av = a[:P], a[P:]
+        nrm = np.sqrt(ah * ah + av * av)
+        g = np.where(nrm > lam / mu, 1 - (lam / mu) / np.maximum(nrm, 1e-300), 0.0)
+        vx = np.concatenate([g * ah, g * av])
+        vz = z + dz
+        dx = dx - (vx - D @ x)
+        dz = dz - (vz - z)
+    return x.reshape(M, N)
+
+
+def test_standard_admm_dense_reaches_same_minimiser(converged):
+    x, st, s, y, m, h, lam, mu = converged
+    xs = dense_standard_admm(y, m, h, lam, mu, 30000)
+    assert np.sqrt(np.mean((xs - x) ** 2)) < 1e-7
+    x1, _, _ = oracle.admm(y[None], m[None], h, lam, mu, 30000, relax=1.0)
+    assert np.sqrt(np.mean((x1[0] - x) ** 2)) < 1e-7
+
+
+def test_vectorial_tv_couples_channels():
+    # With identical channels, vectorial TV over 3 channels equals isotropic TV
+    # with lambda scaled by 1/sqrt(3) per channel (the norm of 3 equal vectors).
+    x_true, y, m, h, lam, mu = small_problem(8, M=12, N=12, K=3, frac=0.0)
+    y3 = np.repeat(y[None], 3, 0)
+    m3 = np.repeat(m[None], 3, 0)
+    x3, _, _ = oracle.admm(y3, m3, h, lam, mu, 40)
+    x1, _, _ = oracle.admm(y[None], m[None], h, lam / np.sqrt(3.0), mu, 40)
+    for c in range(3):
+        assert np.max(np.abs(x3[c] - x1[0])) < 1e-12
