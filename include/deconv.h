@@ -1,0 +1,134 @@
+/*
+ * deconv.h -- C ABI of the GB300 partial-ADMM deconvolution library
+ * (libdeconv.so).
+ *
+ * Method: "A Framework for Fast Image Deconvolution with Incomplete
+ * Observations" (Simoes, Almeida, Bioucas-Dias, Chanussot, arXiv:1602.01410).
+ * The library minimises, over the extended sharp image x and the unobserved
+ * blurred pixels z,
+ *     1/2 || [y; z] - P T~ x ||^2 + lambda * TV(x)            (Eq. (problem_xz))
+ * with the partial ADMM of Eqs. (admm_aprox_1)-(admm_aprox_4): one
+ * block-Gauss-Seidel pass per iteration, the FFT-diagonalised x-step
+ * (Eq. (dual_x_iter_resolved_boundaries)), the over-relaxed z-step
+ * (Sec. II-B, coefficient `relax`, 2 in the paper), the isotropic TV
+ * vector soft-threshold (Sec. III-B) or its vectorial form over 3 channels
+ * (Sec. III-C, demosaicing) and the dual update.
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: each image is the extended M x N grid of the unknown x
+ *     (M = m + 2b, N = n + 2b, Sec. I-A).  Pixels are row-major; an image
+ *     of C channels is stored [C][M][N]; a batch is the concatenation of
+ *     its images in order (image j starts at sum_{i<j} C*M_i*N_i elements).
+ *   - Kernel h: (2b+1) x (2b+1), row-major, origin at h[b][b]; the blur is a
+ *     true circular convolution on the extended grid (Eq. (4)).
+ *   - Element type: float or double for every real array, chosen by
+ *     deconv_dims.dtype; the FP64 reductions for statistics are double.
+ *   - Memory: every array argument is DEVICE memory unless the name ends in
+ *     _host.  The caller owns all memory, including the plan workspace; the
+ *     library never allocates or frees device memory and never frees a
+ *     caller pointer.
+ *   - Streams: all device work is issued on the stream given at plan
+ *     creation (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream).  Calls are stream-ordered and asynchronous unless stated.
+ *   - Errors: functions return a deconv_status and never abort.  Argument
+ *     errors are found on the host before any launch.  Errors that only the
+ *     device can see (non-finite values) are recorded in the workspace and
+ *     returned by deconv_sync.
+ *   - Threads: a plan may be used by one host thread at a time.
+ */
+#ifndef DECONV_H
+#define DECONV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct deconv_plan_s *deconv_plan; /* opaque; destroy with deconv_plan_destroy */
+
+typedef enum {
+  DECONV_OK = 0,
+  DECONV_EINVAL = 1,       /* bad argument: sizes, kernel, lambda/mu, pointer, alignment */
+  DECONV_EUNSUPPORTED = 2, /* a length with a prime factor > 5, or above the largest schedule */
+  DECONV_ENOMEM = 3,       /* workspace smaller than deconv_workspace_size() */
+  DECONV_ECUDA = 4,        /* a CUDA runtime call failed */
+  DECONV_ETIMEOUT = 5,     /* a bounded device wait expired */
+  DECONV_ENONFINITE = 6    /* a NaN or Inf reached the iterate */
+} deconv_status;
+
+enum { DECONV_F32 = 0, DECONV_F64 = 1 };
+
+/* Problem geometry.  rows/cols are HOST arrays of `batch` entries (the
+ * extended sizes M_j, N_j); every M_j, N_j must factor into 2, 3 and 5 and
+ * be >= ksize.  channels is 1, or 3 for the vectorial TV of Sec. III-C.
+ * ksize = 2b+1 is odd (Sec. I-A).  kernel_per_image = 0 shares one h across
+ * the batch, 1 reads batch consecutive kernels.  relax is the z
+ * over-relaxation coefficient (2 in Sec. II-B; 1 gives
+ * Eq. (dual_z_iter_resolved_boundaries), the form Theorem 1 covers); it must
+ * lie in [1, 2]. */
+typedef struct {
+  int32_t batch;
+  int32_t channels;
+  const int32_t *rows;
+  const int32_t *cols;
+  int32_t ksize;
+  int32_t kernel_per_image;
+  int32_t dtype; /* DECONV_F32 or DECONV_F64 */
+  float relax;
+} deconv_dims;
+
+/* Bytes of device workspace a plan for `dims` needs.  Host only. */
+deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes);
+
+/* Create a plan (Sec. II-B, the precomputation of the FFT-diagonalised
+ * operators).  h: device, ksize*ksize elements (times batch when
+ * kernel_per_image), dtype elements; the DC gain sum(h) must be non-zero,
+ * which makes the solution unique (Sec. III-B, null spaces of H and D).
+ * mask: device, one byte per pixel in the batch layout (C planes per image),
+ * nonzero = observed.  The boundary band of width b should be unobserved for
+ * the model of Eq. (4); the library does not require it.  lambda >= 0 is the
+ * TV weight, mu > 0 the ADMM penalty.  workspace: device, 256-byte aligned,
+ * at least deconv_workspace_size() bytes; the plan borrows it until
+ * destroyed.  stream: cudaStream_t as void*.  Synchronises the stream once
+ * (it reads h back to validate the DC gain). */
+deconv_status deconv_plan_create(deconv_plan *out, const deconv_dims *dims, const void *h,
+                                 const uint8_t *mask, double lambda, double mu, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+
+/* Run `iters` >= 0 partial-ADMM iterations.  y: device, batch layout, dtype;
+ * values at unobserved pixels are ignored.  warm = 0 initialises the state
+ * from y (border padding of Sec. III-B, unobserved interior pixels set to the
+ * mean of the observed ones); warm = 1 continues from the plan's state (y is
+ * then unused and may be NULL).  x: device output, batch layout, receives
+ * x^{iters} (may be NULL when iters == 0).  stats: NULL, or device
+ * [batch][iters][3] doubles receiving per iteration ||d^{i+1} - d^i||^2,
+ * ||z^{i+1} - z^i||^2 and the objective of Eq. (problem_xz) at x^{i+1}
+ * minimised over z; stats mode launches the iteration kernels one by one
+ * instead of replaying a CUDA graph.  Asynchronous. */
+deconv_status deconv_solve(deconv_plan plan, const void *y, void *x, int32_t iters, int32_t warm,
+                           double *stats);
+
+/* Same as deconv_solve with warm = 0 and no statistics, but y_host and
+ * x_host are HOST buffers (pinned or pageable) in the batch layout: the call
+ * copies y to the device, runs, copies x back and synchronises the stream
+ * before returning.  Uses the workspace as staging; nothing is allocated. */
+deconv_status deconv_solve_host(deconv_plan plan, const void *y_host, void *x_host, int32_t iters);
+
+/* Wait for the plan's stream and report device-side errors recorded since
+ * the last call (DECONV_ENONFINITE, DECONV_ETIMEOUT), then clear them. */
+deconv_status deconv_sync(deconv_plan plan);
+
+/* Release the plan's host resources (and its cached CUDA graph).  The
+ * workspace is the caller's to free. */
+deconv_status deconv_plan_destroy(deconv_plan plan);
+
+/* Static string for a status code. */
+const char *deconv_status_string(deconv_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DECONV_H */

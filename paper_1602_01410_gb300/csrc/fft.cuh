@@ -1,0 +1,234 @@
+// Shared-memory mixed-radix FFT used by the row and column passes.
+//
+// The 2-D DFT that diagonalises T~^T T~ + mu D^T D (Sec. II-B, the paragraph
+// after the over-relaxed z-update) is computed as 1-D transforms along rows
+// and along columns.  Each CTA holds a batch of S signals of length L in
+// shared memory, laid out [position][signal] with an odd leading dimension
+// `ld` (signal index fastest, so consecutive threads touch consecutive
+// addresses and an odd stride avoids bank conflicts on the transposing
+// writes).  The transform is an in-place Stockham auto-sort sequence of
+// radix-R passes (R in {2,3,4,5,8,16}, chosen per length on the host): in
+// pass p with span Ns (the product of the radices already applied), the
+// butterfly j reads elements j + r L/R, multiplies element r by
+// w^(r (j mod Ns)) with w = exp(sign 2 pi i / (Ns R)), applies an R-point
+// DFT in registers and writes element r to (j - j mod Ns) R + j mod Ns +
+// r Ns.  After the last pass the output is in natural order (the Stockham
+// formulation of Govindaraju et al., SC'08, written for [position][signal]
+// storage).  Each thread
+// keeps at most 32 complex values in registers per pass, so a CTA of NT
+// threads can hold S * L <= 30 NT elements.
+//
+// Twiddles come from a table tw[m] = exp(-2 pi i m / L) computed on the host
+// in double precision (cos/sin of the exact rational angle) and rounded once
+// to the element type; the inverse uses the conjugate.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dcv {
+
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+template <typename T> using cx = typename vec2<T>::type;
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// multiply by sign * i
+template <typename T, int SIGN> __device__ __forceinline__ cx<T> mul_si(cx<T> a) {
+  return SIGN > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------------------
+// R-point DFTs in registers: X[q] = sum_r v[r] exp(SIGN 2 pi i r q / R).
+// Constants are the exact values of cos/sin at multiples of 2 pi / R.
+
+template <typename T, int R, int SIGN> struct Dft;
+
+template <typename T, int SIGN> struct Dft<T, 2, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *v) {
+    cx<T> a = v[0], b = v[1];
+    v[0] = cadd<T>(a, b);
+    v[1] = csub<T>(a, b);
+  }
+};
+
+template <typename T, int SIGN> struct Dft<T, 3, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *v) {
+    const T c = T(-0.5), s = T(0.86602540378443864676);  // cos, |sin| of 2 pi / 3
+    cx<T> t1 = cadd<T>(v[1], v[2]), t2 = csub<T>(v[1], v[2]);
+    cx<T> m = mk<T>(v[0].x + c * t1.x, v[0].y + c * t1.y);
+    cx<T> r = mul_si<T, SIGN>(cscale<T>(t2, s));
+    v[0] = cadd<T>(v[0], t1);
+    v[1] = cadd<T>(m, r);
+    v[2] = csub<T>(m, r);
+  }
+};
+
+template <typename T, int SIGN> struct Dft<T, 4, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *v) {
+    cx<T> a = cadd<T>(v[0], v[2]), b = csub<T>(v[0], v[2]);
+    cx<T> c = cadd<T>(v[1], v[3]), d = mul_si<T, SIGN>(csub<T>(v[1], v[3]));
+    v[0] = cadd<T>(a, c);
+    v[2] = csub<T>(a, c);
+    v[1] = cadd<T>(b, d);
+    v[3] = csub<T>(b, d);
+  }
+};
+
+template <typename T, int SIGN> struct Dft<T, 5, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *v) {
+    const T c1 = T(0.30901699437494742410), s1 = T(0.95105651629515357212);   // 2 pi / 5
+    const T c2 = T(-0.80901699437494742410), s2 = T(0.58778525229247312917);  // 4 pi / 5
+    cx<T> a1 = cadd<T>(v[1], v[4]), b1 = csub<T>(v[1], v[4]);
+    cx<T> a2 = cadd<T>(v[2], v[3]), b2 = csub<T>(v[2], v[3]);
+    cx<T> m1 = mk<T>(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+    cx<T> m2 = mk<T>(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+    cx<T> r1 = mul_si<T, SIGN>(mk<T>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+    cx<T> r2 = mul_si<T, SIGN>(mk<T>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+    v[0] = mk<T>(v[0].x + a1.x + a2.x, v[0].y + a1.y + a2.y);
+    v[1] = cadd<T>(m1, r1);
+    v[4] = csub<T>(m1, r1);
+    v[2] = cadd<T>(m2, r2);
+    v[3] = csub<T>(m2, r2);
+  }
+};
+
+// 8 = 2 x 4 (even/odd split), 16 = 2 x 8.
+template <typename T, int SIGN> struct Dft<T, 8, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *v) {
+    const T h = T(0.70710678118654752440);
+    cx<T> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<T, 4, SIGN>::run(e);
+    Dft<T, 4, SIGN>::run(o);
+    // w8^q, q = 0..3, w8 = exp(SIGN i pi / 4)
+    cx<T> t1 = cmul<T>(o[1], mk<T>(h, SIGN * h));
+    cx<T> t2 = mul_si<T, SIGN>(o[2]);
+    cx<T> t3 = cmul<T>(o[3], mk<T>(-h, SIGN * h));
+    v[0] = cadd<T>(e[0], o[0]);
+    v[4] = csub<T>(e[0], o[0]);
+    v[1] = cadd<T>(e[1], t1);
+    v[5] = csub<T>(e[1], t1);
+    v[2] = cadd<T>(e[2], t2);
+    v[6] = csub<T>(e[2], t2);
+    v[3] = cadd<T>(e[3], t3);
+    v[7] = csub<T>(e[3], t3);
+  }
+};
+
+template <typename T, int SIGN> struct Dft<T, 16, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *v) {
+    // cos, sin of q pi / 8 for q = 0..7
+    const T C[8] = {T(1.0), T(0.92387953251128675613), T(0.70710678118654752440), T(0.38268343236508977173),
+                    T(0.0), T(-0.38268343236508977173), T(-0.70710678118654752440), T(-0.92387953251128675613)};
+    const T S[8] = {T(0.0), T(0.38268343236508977173), T(0.70710678118654752440), T(0.92387953251128675613),
+                    T(1.0), T(0.92387953251128675613), T(0.70710678118654752440), T(0.38268343236508977173)};
+    cx<T> e[8], o[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      e[r] = v[2 * r];
+      o[r] = v[2 * r + 1];
+    }
+    Dft<T, 8, SIGN>::run(e);
+    Dft<T, 8, SIGN>::run(o);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      cx<T> t = (q == 0) ? o[0] : cmul<T>(o[q], mk<T>(C[q], SIGN * S[q]));
+      v[q] = cadd<T>(e[q], t);
+      v[q + 8] = csub<T>(e[q], t);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// One radix-R Stockham pass over S signals of length L held in buf.  The
+// host plans S * L <= 30 NT so that every butterfly has a register slot.
+template <typename T, int NT, int R, int SIGN>
+__device__ __forceinline__ void stockham_pass(cx<T> *buf, int L, int S, int ld, int Ns,
+                                              const cx<T> *__restrict__ tw) {
+  constexpr int CM = 32 / R;
+  const int LR = L / R;
+  const int nbf = S * LR;
+  const int tstride = L / (Ns * R);
+  cx<T> v[CM][R];
+#pragma unroll
+  for (int c = 0; c < CM; ++c) {
+    const int b = threadIdx.x + c * NT;
+    if (b < nbf) {
+      const int s = b % S, j = b / S, k = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[c][r] = buf[(j + r * LR) * ld + s];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cx<T> w = __ldg(&tw[k * r * tstride]);
+          if (SIGN > 0) w.y = -w.y;
+          v[c][r] = cmul<T>(v[c][r], w);
+        }
+      }
+      Dft<T, R, SIGN>::run(v[c]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < CM; ++c) {
+    const int b = threadIdx.x + c * NT;
+    if (b < nbf) {
+      const int s = b % S, j = b / S, k = j % Ns;
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[(base + r * Ns) * ld + s] = v[c][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Radix schedule of one length L = 16^n16 * r * 5^n5 * 3^n3 with r in
+// {1, 2, 4, 8}: the passes run in that fixed order.  (A fixed sequence of
+// pass loops, instead of one loop over a runtime radix switch, lets the
+// register allocator treat each pass on its own.)
+struct FftSched {
+  int8_t n16, r, n5, n3;
+};
+
+// Full transform.  buf must be complete (a __syncthreads after it was
+// written) on entry; it is complete on return.
+template <typename T, int NT, int SIGN>
+__device__ __forceinline__ void fft_smem(cx<T> *buf, int L, int S, int ld, FftSched sc,
+                                         const cx<T> *__restrict__ tw) {
+  int Ns = 1;
+  for (int p = 0; p < sc.n16; ++p) {
+    stockham_pass<T, NT, 16, SIGN>(buf, L, S, ld, Ns, tw);
+    Ns *= 16;
+  }
+  if (sc.r == 8) {
+    stockham_pass<T, NT, 8, SIGN>(buf, L, S, ld, Ns, tw);
+    Ns *= 8;
+  } else if (sc.r == 4) {
+    stockham_pass<T, NT, 4, SIGN>(buf, L, S, ld, Ns, tw);
+    Ns *= 4;
+  } else if (sc.r == 2) {
+    stockham_pass<T, NT, 2, SIGN>(buf, L, S, ld, Ns, tw);
+    Ns *= 2;
+  }
+  for (int p = 0; p < sc.n5; ++p) {
+    stockham_pass<T, NT, 5, SIGN>(buf, L, S, ld, Ns, tw);
+    Ns *= 5;
+  }
+  for (int p = 0; p < sc.n3; ++p) {
+    stockham_pass<T, NT, 3, SIGN>(buf, L, S, ld, Ns, tw);
+    Ns *= 3;
+  }
+}
+
+}  // namespace dcv

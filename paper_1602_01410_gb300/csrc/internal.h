@@ -1,0 +1,97 @@
+// Internal types shared by the device kernels and the host plan code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace dcv {
+
+// Per-image geometry and workspace offsets.  Offsets are in elements of the
+// array they index (see Plan in plan.cu for the arrays).
+struct ImageDesc {
+  int M, N, Nh, C;       // extended rows, cols, N/2+1, channels
+  int Rb;                // rows owned by one row-pass CTA
+  int W;                 // spectral columns (k2) per column-pass CTA
+  int row_blocks;        // ceil(M / Rb)
+  int col_tiles;         // ceil(Nh / W) (per channel)
+  int row_begin;         // first row-pass work item of this image
+  int col_begin;         // first column-pass work item (C * col_tiles items)
+  long long px;          // first pixel (real element) of the image, batch layout
+  long long spec;        // first cpair of the image in the spectral buffers
+  long long hhat;        // first complex of the image's H^ half-spectrum
+  long long mask;        // first 32-bit word of the image's packed mask
+  long long mask_plane;  // words per channel plane
+  int tw_row, tw_col;    // twiddle-table offsets for lengths N and M
+  int s2_row, s2_col;    // 4 sin^2(pi k / L) table offsets for N and M
+  FftSched sched_row, sched_col;
+};
+
+// Pair of complex values stored per (row, k2) in the spectral buffers:
+// forward: (Y_row, R_row) = row spectra of y~ and r; inverse: (X_row, HX_row).
+template <typename T> struct alignas(4 * sizeof(T)) cpair { T ar, ai, br, bi; };
+
+enum RowMode { ROW_ITER = 0, ROW_INIT = 1 };
+
+template <typename T> struct RowArgs {
+  const ImageDesc *desc;
+  int nimg;
+  int mode;           // RowMode
+  T *yt;              // y~ (observed: y, unobserved: z), batch layout
+  const T *d_in;      // d_x^i as (d_h, d_v) pairs per pixel; NULL = zero
+  T *d_out;           // d_x^{i+1}
+  const cpair<T> *S_in;   // (X_row, HX_row) from the column pass (ROW_ITER)
+  cpair<T> *S_out;        // (Y_row, R_row) for the next column pass
+  const uint32_t *mask;   // packed observed bits
+  const void *tw;         // twiddle tables (cx<T>)
+  T mu, tau, relax, lambda;
+  T *x_out;               // nullable: x^{i+1} for owned rows
+  double *partials;       // nullable: per work item [3] = sum dd^2, dz^2, J
+  int *err;
+};
+
+template <typename T> struct ColArgs {
+  const ImageDesc *desc;
+  int nimg;
+  const cpair<T> *S_in;
+  cpair<T> *S_out;
+  const void *hhat;   // cx<T>
+  const void *tw;     // cx<T>
+  const T *s2;        // 4 sin^2 tables
+  T mu;
+  int *err;
+};
+
+// Kernel launchers (kernels_*.cu).  nt = threads per CTA (256 or 512).
+template <typename T>
+cudaError_t launch_row(const RowArgs<T> &a, int grid, int nt, int channels, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t launch_col(const ColArgs<T> &a, int grid, int nt, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_kernels(int nt, int channels, size_t row_smem, size_t col_smem);
+
+// Setup kernels (setup.cu).
+struct HhatJob {          // one half-spectrum to compute
+  int M, N, Nh, K;
+  long long out;          // complex offset in hhat
+  long long h;            // element offset of the kernel
+};
+template <typename T>
+cudaError_t launch_hhat(const HhatJob *jobs_dev, int njobs, long long total, const T *h, void *hhat,
+                        const long long *job_begin_dev, cudaStream_t s);
+cudaError_t launch_pack_mask(const ImageDesc *desc_dev, int nimg, long long total_words,
+                             const long long *img_word_begin_dev, const uint8_t *mask, uint32_t *bits,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_means(const ImageDesc *desc_dev, int nplanes, const int *plane_img_dev, const T *y,
+                         const uint32_t *bits, double *means, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init_fill(const ImageDesc *desc_dev, int nimg, long long total_px,
+                             const long long *img_px_begin_dev, const T *y, const uint32_t *bits,
+                             const double *means, int K, T *yt, cudaStream_t s);
+cudaError_t launch_stats_reduce(const ImageDesc *desc_dev, int nimg, const double *partials, double *stats,
+                                int iters, int it, int *err, cudaStream_t s);
+
+}  // namespace dcv

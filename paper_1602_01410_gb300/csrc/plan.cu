@@ -1,0 +1,543 @@
+// Host side of the C ABI declared in include/deconv.h: argument validation,
+// workspace layout, plan setup (H^, packed masks, twiddle tables) and the
+// iteration driver (direct launches, or a cached CUDA graph of a fixed number
+// of iterations replayed on the caller's stream).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "deconv.h"
+#include "internal.h"
+
+using namespace dcv;
+
+namespace {
+
+constexpr int kGraphIters = 20;          // iterations per captured graph (even: d ping-pong returns to 0)
+constexpr int kTargetCtas = 2 * 152;     // aim for two CTAs per SM on a 152-SM GB300
+constexpr size_t kMaxSmem = 227 * 1024 - 2048;  // opt-in dynamic shared memory per CTA, minus static use
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool factor235(int L, FftSched *sc) {
+  if (L < 1) return false;
+  int a = 0, b = 0, c = 0, v = L;
+  while (v % 2 == 0) { v /= 2; ++a; }
+  while (v % 3 == 0) { v /= 3; ++b; }
+  while (v % 5 == 0) { v /= 5; ++c; }
+  if (v != 1) return false;
+  sc->n16 = (int8_t)(a / 4);
+  sc->r = (int8_t)(1 << (a % 4));
+  sc->n5 = (int8_t)c;
+  sc->n3 = (int8_t)b;
+  return true;
+}
+
+int env_int(const char *name, int dflt) {
+  const char *v = std::getenv(name);
+  return v ? std::atoi(v) : dflt;
+}
+
+struct Layout {
+  int B = 0, C = 0, K = 0, dtype = 0, nt = 256, kernel_per_image = 0;
+  size_t esz = 4;
+  std::vector<ImageDesc> desc;
+  long long total_px = 0, total_spec = 0, total_hhat = 0, total_words = 0, total_tw = 0, total_s2 = 0;
+  std::vector<HhatJob> jobs;
+  std::vector<long long> job_begin, img_word_begin, img_px_begin;
+  std::vector<int> plane_img;
+  std::vector<int> lengths;
+  std::map<int, int> tw_off, s2_off;
+  long long hhat_total_elems = 0;
+  int row_grid = 0, col_grid = 0;
+  size_t row_smem = 0, col_smem = 0;
+  size_t o_yt, o_d0, o_d1, o_Sa, o_Sb, o_hhat, o_bits, o_tw, o_s2, o_desc, o_jobs, o_jobbeg, o_wordbeg, o_pxbeg,
+      o_planeimg, o_means, o_partials, o_err, o_xbuf, total;
+};
+
+// Row-block height and column-tile width for one image under CTA size nt.
+bool fit_image(int M, int N, int C, int nt, size_t esz, int rb_pref, int w_pref, int *Rb, int *W) {
+  const int budget = 30 * nt, kmax = 16 / C;
+  int rb = std::min(budget / (C * N) - 2, kmax * nt / N);
+  if (rb < 1) return false;
+  rb = std::min(rb, std::max(1, rb_pref));
+  rb = std::min(rb, M);
+  while (rb >= 1) {
+    size_t ld = (size_t)((C * (rb + 2)) | 1);
+    size_t smem = (size_t)N * ld * 2 * esz + (size_t)(rb + 1) * N * esz;
+    if (smem <= kMaxSmem) break;
+    --rb;
+  }
+  if (rb < 1) return false;
+  const int Nh = N / 2 + 1;
+  int w = std::min(16, budget / (2 * M));
+  if (w < 1) return false;
+  w = std::min(w, std::max(1, w_pref));
+  w = std::min(w, Nh);
+  while (w >= 1 && (size_t)M * (size_t)((2 * w) | 1) * 2 * esz > kMaxSmem) --w;
+  if (w < 1) return false;
+  *Rb = rb;
+  *W = w;
+  return true;
+}
+
+deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
+  if (!d || d->batch < 1 || !d->rows || !d->cols) return DECONV_EINVAL;
+  if (d->channels != 1 && d->channels != 3) return DECONV_EINVAL;
+  if (d->ksize < 1 || d->ksize % 2 == 0) return DECONV_EINVAL;
+  if (d->dtype != DECONV_F32 && d->dtype != DECONV_F64) return DECONV_EINVAL;
+  if (!(d->relax >= 1.0f && d->relax <= 2.0f)) return DECONV_EINVAL;
+  if (d->kernel_per_image != 0 && d->kernel_per_image != 1) return DECONV_EINVAL;
+  Layout &L = *Lo;
+  L.B = d->batch;
+  L.C = d->channels;
+  L.K = d->ksize;
+  L.dtype = d->dtype;
+  L.kernel_per_image = d->kernel_per_image;
+  L.esz = d->dtype == DECONV_F32 ? 4 : 8;
+  long long rows_total = 0, cols_total = 0;
+  for (int j = 0; j < L.B; ++j) {
+    const int M = d->rows[j], N = d->cols[j];
+    if (M < d->ksize || N < d->ksize || M < 2 || N < 2) return DECONV_EINVAL;
+    if ((long long)M * N > (1LL << 30)) return DECONV_EUNSUPPORTED;
+    FftSched s;
+    if (!factor235(M, &s) || !factor235(N, &s)) return DECONV_EUNSUPPORTED;
+    rows_total += M;
+    cols_total += (long long)L.C * (N / 2 + 1);
+  }
+  const int rb_pref = env_int("DECONV_ROW_BLOCK", (int)std::max<long long>(2, (rows_total + kTargetCtas - 1) / kTargetCtas));
+  const int w_pref = env_int("DECONV_COL_TILE", (int)std::max<long long>(1, (cols_total + kTargetCtas - 1) / kTargetCtas));
+  // CTA size: 256 threads when every image fits, else 512 (FP32 only).
+  int nt_req = env_int("DECONV_NT", 0);
+  std::vector<int> cand = nt_req ? std::vector<int>{nt_req} : std::vector<int>{256, 512};
+  bool ok = false;
+  for (int nt : cand) {
+    if (nt != 256 && !(nt == 512 && L.esz == 4)) continue;
+    bool all = true;
+    for (int j = 0; j < L.B && all; ++j) {
+      int rb, w;
+      all = fit_image(d->rows[j], d->cols[j], L.C, nt, L.esz, rb_pref, w_pref, &rb, &w);
+    }
+    if (all) {
+      L.nt = nt;
+      ok = true;
+      break;
+    }
+  }
+  if (!ok) return DECONV_EUNSUPPORTED;
+
+  std::map<std::tuple<int, int, int>, long long> hh;  // (M, N, kernel) -> offset
+  L.desc.resize(L.B);
+  for (int j = 0; j < L.B; ++j) {
+    ImageDesc &D = L.desc[j];
+    std::memset(&D, 0, sizeof(D));
+    D.M = d->rows[j];
+    D.N = d->cols[j];
+    D.Nh = D.N / 2 + 1;
+    D.C = L.C;
+    fit_image(D.M, D.N, L.C, L.nt, L.esz, rb_pref, w_pref, &D.Rb, &D.W);
+    D.row_blocks = (D.M + D.Rb - 1) / D.Rb;
+    D.col_tiles = (D.Nh + D.W - 1) / D.W;
+    D.row_begin = L.row_grid;
+    D.col_begin = L.col_grid;
+    L.row_grid += D.row_blocks;
+    L.col_grid += L.C * D.col_tiles;
+    D.px = L.total_px;
+    L.img_px_begin.push_back(L.total_px);
+    L.total_px += (long long)L.C * D.M * D.N;
+    D.spec = L.total_spec;
+    L.total_spec += (long long)L.C * D.M * D.Nh;
+    D.mask_plane = ((long long)D.M * D.N + 31) / 32;
+    D.mask = L.total_words;
+    L.img_word_begin.push_back(L.total_words);
+    L.total_words += L.C * D.mask_plane;
+    for (int c = 0; c < L.C; ++c) {
+      L.plane_img.push_back(j);
+      L.plane_img.push_back(c);
+    }
+    const int kidx = L.kernel_per_image ? j : 0;
+    auto key = std::make_tuple(D.M, D.N, kidx);
+    auto it = hh.find(key);
+    if (it == hh.end()) {
+      HhatJob job{D.M, D.N, D.Nh, L.K, L.total_hhat, (long long)kidx * L.K * L.K};
+      L.job_begin.push_back(L.hhat_total_elems);
+      L.hhat_total_elems += (long long)D.M * D.Nh;
+      L.jobs.push_back(job);
+      hh[key] = L.total_hhat;
+      D.hhat = L.total_hhat;
+      L.total_hhat += (long long)D.M * D.Nh;
+    } else {
+      D.hhat = it->second;
+    }
+    for (int len : {D.M, D.N})
+      if (!L.tw_off.count(len)) {
+        L.tw_off[len] = (int)L.total_tw;
+        L.s2_off[len] = (int)L.total_s2;
+        L.total_tw += len;
+        L.total_s2 += len;
+        L.lengths.push_back(len);
+      }
+    D.tw_row = L.tw_off[D.N];
+    D.tw_col = L.tw_off[D.M];
+    D.s2_row = L.s2_off[D.N];
+    D.s2_col = L.s2_off[D.M];
+    factor235(D.N, &D.sched_row);
+    factor235(D.M, &D.sched_col);
+    const size_t ldr = (size_t)((L.C * (D.Rb + 2)) | 1), ldc = (size_t)((2 * D.W) | 1);
+    L.row_smem = std::max(L.row_smem, (size_t)D.N * ldr * 2 * L.esz + (size_t)(D.Rb + 1) * D.N * L.esz);
+    L.col_smem = std::max(L.col_smem, (size_t)D.M * ldc * 2 * L.esz);
+  }
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  L.o_yt = take(L.total_px * L.esz);
+  L.o_d0 = take(L.total_px * 2 * L.esz);
+  L.o_d1 = take(L.total_px * 2 * L.esz);
+  L.o_Sa = take(L.total_spec * 4 * L.esz);
+  L.o_Sb = take(L.total_spec * 4 * L.esz);
+  L.o_hhat = take(L.total_hhat * 2 * L.esz);
+  L.o_bits = take(L.total_words * 4);
+  L.o_tw = take(L.total_tw * 2 * L.esz);
+  L.o_s2 = take(L.total_s2 * L.esz);
+  L.o_desc = take(L.desc.size() * sizeof(ImageDesc));
+  L.o_jobs = take(L.jobs.size() * sizeof(HhatJob));
+  L.o_jobbeg = take(L.job_begin.size() * sizeof(long long));
+  L.o_wordbeg = take(L.img_word_begin.size() * sizeof(long long));
+  L.o_pxbeg = take(L.img_px_begin.size() * sizeof(long long));
+  L.o_planeimg = take(L.plane_img.size() * sizeof(int));
+  L.o_means = take(L.plane_img.size() / 2 * sizeof(double));
+  L.o_partials = take((size_t)L.row_grid * 3 * sizeof(double));
+  L.o_err = take(sizeof(int));
+  L.o_xbuf = take(L.total_px * L.esz);
+  L.total = o;
+  return DECONV_OK;
+}
+
+}  // namespace
+
+struct deconv_plan_s {
+  Layout L;
+  cudaStream_t stream = nullptr;
+  char *ws = nullptr;
+  double lambda = 0, mu = 1;
+  float relax = 2.0f;
+  int parity = 0;
+  bool have_state = false;
+  cudaGraphExec_t gexec = nullptr;
+
+  template <typename P> P *at(size_t off) const { return reinterpret_cast<P *>(ws + off); }
+};
+
+namespace {
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return DECONV_ECUDA;  \
+  } while (0)
+
+template <typename T>
+RowArgs<T> row_args(const deconv_plan_s *p, int mode, const T *d_in, T *d_out, T *x_out, double *partials) {
+  const Layout &L = p->L;
+  RowArgs<T> a;
+  a.desc = p->at<ImageDesc>(L.o_desc);
+  a.nimg = L.B;
+  a.mode = mode;
+  a.yt = p->at<T>(L.o_yt);
+  a.d_in = d_in;
+  a.d_out = d_out;
+  a.S_in = p->at<cpair<T>>(L.o_Sb);
+  a.S_out = p->at<cpair<T>>(L.o_Sa);
+  a.mask = p->at<uint32_t>(L.o_bits);
+  a.tw = p->ws + L.o_tw;
+  a.mu = (T)p->mu;
+  a.tau = (T)(p->lambda / p->mu);
+  a.relax = (T)p->relax;
+  a.lambda = (T)p->lambda;
+  a.x_out = x_out;
+  a.partials = partials;
+  a.err = p->at<int>(L.o_err);
+  return a;
+}
+
+template <typename T>
+ColArgs<T> col_args(const deconv_plan_s *p) {
+  const Layout &L = p->L;
+  ColArgs<T> a;
+  a.desc = p->at<ImageDesc>(L.o_desc);
+  a.nimg = L.B;
+  a.S_in = p->at<cpair<T>>(L.o_Sa);
+  a.S_out = p->at<cpair<T>>(L.o_Sb);
+  a.hhat = p->ws + L.o_hhat;
+  a.tw = p->ws + L.o_tw;
+  a.s2 = p->at<T>(L.o_s2);
+  a.mu = (T)p->mu;
+  a.err = p->at<int>(L.o_err);
+  return a;
+}
+
+template <typename T> T *dbuf(deconv_plan_s *p, int which) {
+  return p->at<T>(which ? p->L.o_d1 : p->L.o_d0);
+}
+
+// One iteration (column pass then row pass), d ping-pong by plan parity.
+template <typename T>
+deconv_status iterate(deconv_plan_s *p, cudaStream_t s, T *x_out, double *stats, int iters, int it) {
+  const Layout &L = p->L;
+  CK(launch_col<T>(col_args<T>(p), L.col_grid, L.nt, L.col_smem, s));
+  double *partials = stats ? p->at<double>(L.o_partials) : nullptr;
+  CK(launch_row<T>(row_args<T>(p, ROW_ITER, dbuf<T>(p, p->parity), dbuf<T>(p, p->parity ^ 1), x_out, partials),
+                   L.row_grid, L.nt, L.C, L.row_smem, s));
+  p->parity ^= 1;
+  if (stats) CK(launch_stats_reduce(p->at<ImageDesc>(L.o_desc), L.B, partials, stats, iters, it, p->at<int>(L.o_err), s));
+  return DECONV_OK;
+}
+
+template <typename T>
+deconv_status init_state(deconv_plan_s *p, const T *y, T *x_out) {
+  const Layout &L = p->L;
+  cudaStream_t s = p->stream;
+  const ImageDesc *desc = p->at<ImageDesc>(L.o_desc);
+  CK(launch_means<T>(desc, (int)L.plane_img.size() / 2, p->at<int>(L.o_planeimg), y, p->at<uint32_t>(L.o_bits),
+                     p->at<double>(L.o_means), s));
+  CK(launch_init_fill<T>(desc, L.B, L.total_px, p->at<long long>(L.o_pxbeg), y, p->at<uint32_t>(L.o_bits),
+                         p->at<double>(L.o_means), L.K, p->at<T>(L.o_yt), s));
+  p->parity = 0;
+  CK(launch_row<T>(row_args<T>(p, ROW_INIT, nullptr, dbuf<T>(p, 0), x_out, nullptr), L.row_grid, L.nt, L.C,
+                   L.row_smem, s));
+  p->have_state = true;
+  return DECONV_OK;
+}
+
+template <typename T>
+deconv_status ensure_graph(deconv_plan_s *p) {
+  if (p->gexec) return DECONV_OK;
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const int saved = p->parity;
+  p->parity = 0;
+  deconv_status st = DECONV_OK;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = DECONV_ECUDA;
+  for (int k = 0; k < kGraphIters && st == DECONV_OK; ++k) st = iterate<T>(p, cs, nullptr, nullptr, 0, 0);
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  p->parity = saved;
+  if (st == DECONV_OK && e == cudaSuccess && g) {
+    if (cudaGraphInstantiate(&p->gexec, g, 0) != cudaSuccess) {
+      p->gexec = nullptr;
+      st = DECONV_ECUDA;
+    }
+  } else if (st == DECONV_OK) {
+    st = DECONV_ECUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  return st;
+}
+
+template <typename T>
+deconv_status run_iters(deconv_plan_s *p, T *x, int iters, double *stats) {
+  if (stats) {
+    for (int it = 0; it < iters; ++it) {
+      deconv_status st = iterate<T>(p, p->stream, it == iters - 1 ? x : nullptr, stats, iters, it);
+      if (st != DECONV_OK) return st;
+    }
+    return DECONV_OK;
+  }
+  int remaining = iters;
+  while (remaining > 1) {
+    deconv_status st;
+    if (p->parity == 0 && remaining - 1 >= kGraphIters) {
+      st = ensure_graph<T>(p);
+      if (st != DECONV_OK) return st;
+      CK(cudaGraphLaunch(p->gexec, p->stream));
+      remaining -= kGraphIters;
+    } else {
+      st = iterate<T>(p, p->stream, nullptr, nullptr, 0, 0);
+      if (st != DECONV_OK) return st;
+      --remaining;
+    }
+  }
+  if (remaining == 1) return iterate<T>(p, p->stream, x, nullptr, 0, 0);
+  return DECONV_OK;
+}
+
+template <typename T>
+deconv_status solve_t(deconv_plan_s *p, const void *y, void *x, int iters, int warm, double *stats) {
+  if (!warm) {
+    deconv_status st = init_state<T>(p, static_cast<const T *>(y), iters == 0 ? static_cast<T *>(x) : nullptr);
+    if (st != DECONV_OK) return st;
+  }
+  return run_iters<T>(p, static_cast<T *>(x), iters, stats);
+}
+
+template <typename T>
+deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
+  const Layout &L = p->L;
+  cudaStream_t s = p->stream;
+  // Host tables: twiddles exp(-2 pi i k / L) and 4 sin^2(pi k / L), from
+  // double-precision cos/sin, rounded once to T.
+  std::vector<T> tw(2 * L.total_tw), s2(L.total_s2);
+  for (int len : L.lengths) {
+    const int o = L.tw_off.at(len), o2 = L.s2_off.at(len);
+    for (int k = 0; k < len; ++k) {
+      const double a = 2.0 * M_PI * (double)k / (double)len;
+      tw[2 * (o + k)] = (T)std::cos(a);
+      tw[2 * (o + k) + 1] = (T)(-std::sin(a));
+      const double sn = std::sin(M_PI * (double)k / (double)len);
+      s2[o2 + k] = (T)(4.0 * sn * sn);
+    }
+  }
+  CK(cudaMemcpyAsync(p->ws + L.o_tw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_s2, s2.data(), s2.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_desc, L.desc.data(), L.desc.size() * sizeof(ImageDesc), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_jobs, L.jobs.data(), L.jobs.size() * sizeof(HhatJob), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_jobbeg, L.job_begin.data(), L.job_begin.size() * sizeof(long long),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_wordbeg, L.img_word_begin.data(), L.img_word_begin.size() * sizeof(long long),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_pxbeg, L.img_px_begin.data(), L.img_px_begin.size() * sizeof(long long),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_planeimg, L.plane_img.data(), L.plane_img.size() * sizeof(int),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(p->ws + L.o_err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(p->ws + L.o_d0, 0, L.total_px * 2 * L.esz, s));
+  CK(cudaMemsetAsync(p->ws + L.o_d1, 0, L.total_px * 2 * L.esz, s));
+  CK(launch_hhat<T>(p->at<HhatJob>(L.o_jobs), (int)L.jobs.size(), L.hhat_total_elems, static_cast<const T *>(h),
+                    p->ws + L.o_hhat, p->at<long long>(L.o_jobbeg), s));
+  CK(launch_pack_mask(p->at<ImageDesc>(L.o_desc), L.B, L.total_words, p->at<long long>(L.o_wordbeg), mask,
+                      p->at<uint32_t>(L.o_bits), s));
+  CK(prepare_kernels<T>(L.nt, L.C, L.row_smem, L.col_smem));
+  CK(cudaStreamSynchronize(s));
+  return DECONV_OK;
+}
+
+template <typename T>
+deconv_status check_kernels(const void *h, const Layout &L, cudaStream_t s) {
+  const int nk = L.kernel_per_image ? L.B : 1;
+  std::vector<T> hh((size_t)nk * L.K * L.K);
+  CK(cudaMemcpyAsync(hh.data(), h, hh.size() * sizeof(T), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < nk; ++k) {
+    double sum = 0.0;
+    for (int t = 0; t < L.K * L.K; ++t) {
+      const double v = (double)hh[(size_t)k * L.K * L.K + t];
+      if (!std::isfinite(v)) return DECONV_EINVAL;
+      sum += v;
+    }
+    if (sum == 0.0) return DECONV_EINVAL;  // zero DC gain: H and D share the constant null vector
+  }
+  return DECONV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes) {
+  if (!bytes) return DECONV_EINVAL;
+  Layout L;
+  deconv_status st = build_layout(dims, &L);
+  if (st != DECONV_OK) return st;
+  *bytes = L.total;
+  return DECONV_OK;
+}
+
+deconv_status deconv_plan_create(deconv_plan *out, const deconv_dims *dims, const void *h, const uint8_t *mask,
+                                 double lambda, double mu, void *workspace, size_t workspace_bytes, void *stream) {
+  if (!out) return DECONV_EINVAL;
+  *out = nullptr;
+  if (!h || !mask || !workspace) return DECONV_EINVAL;
+  if (!(std::isfinite(lambda) && lambda >= 0.0) || !(std::isfinite(mu) && mu > 0.0)) return DECONV_EINVAL;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign != 0) return DECONV_EINVAL;
+  deconv_plan_s *p = new (std::nothrow) deconv_plan_s();
+  if (!p) return DECONV_ENOMEM;
+  deconv_status st = build_layout(dims, &p->L);
+  if (st == DECONV_OK && workspace_bytes < p->L.total) st = DECONV_ENOMEM;
+  if (st != DECONV_OK) {
+    delete p;
+    return st;
+  }
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->ws = static_cast<char *>(workspace);
+  p->lambda = lambda;
+  p->mu = mu;
+  p->relax = dims->relax;
+  st = p->L.dtype == DECONV_F32 ? check_kernels<float>(h, p->L, p->stream) : check_kernels<double>(h, p->L, p->stream);
+  if (st == DECONV_OK)
+    st = p->L.dtype == DECONV_F32 ? setup_t<float>(p, h, mask) : setup_t<double>(p, h, mask);
+  if (st != DECONV_OK) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return DECONV_OK;
+}
+
+deconv_status deconv_solve(deconv_plan p, const void *y, void *x, int32_t iters, int32_t warm, double *stats) {
+  if (!p || iters < 0 || (warm != 0 && warm != 1)) return DECONV_EINVAL;
+  if (!warm && !y) return DECONV_EINVAL;
+  if (warm && !p->have_state) return DECONV_EINVAL;
+  if (iters > 0 && !x) return DECONV_EINVAL;
+  if (stats && iters == 0) stats = nullptr;
+  return p->L.dtype == DECONV_F32 ? solve_t<float>(p, y, x, iters, warm, stats)
+                                  : solve_t<double>(p, y, x, iters, warm, stats);
+}
+
+deconv_status deconv_solve_host(deconv_plan p, const void *y_host, void *x_host, int32_t iters) {
+  if (!p || !y_host || !x_host || iters < 0) return DECONV_EINVAL;
+  const Layout &L = p->L;
+  const size_t bytes = L.total_px * L.esz;
+  CK(cudaMemcpyAsync(p->ws + L.o_yt, y_host, bytes, cudaMemcpyHostToDevice, p->stream));
+  // y is staged in the y~ buffer itself: the initial fill only rewrites
+  // unobserved entries and reads observed ones.
+  deconv_status st = p->L.dtype == DECONV_F32
+                         ? solve_t<float>(p, p->ws + L.o_yt, p->ws + L.o_xbuf, iters, 0, nullptr)
+                         : solve_t<double>(p, p->ws + L.o_yt, p->ws + L.o_xbuf, iters, 0, nullptr);
+  if (st != DECONV_OK) return st;
+  CK(cudaMemcpyAsync(x_host, p->ws + L.o_xbuf, bytes, cudaMemcpyDeviceToHost, p->stream));
+  return deconv_sync(p);
+}
+
+deconv_status deconv_sync(deconv_plan p) {
+  if (!p) return DECONV_EINVAL;
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, p->ws + p->L.o_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  if (err) {
+    CK(cudaMemsetAsync(p->ws + p->L.o_err, 0, sizeof(int), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return (err & 2) ? DECONV_ETIMEOUT : DECONV_ENONFINITE;
+  }
+  return DECONV_OK;
+}
+
+deconv_status deconv_plan_destroy(deconv_plan p) {
+  if (!p) return DECONV_EINVAL;
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  delete p;
+  return DECONV_OK;
+}
+
+const char *deconv_status_string(deconv_status s) {
+  switch (s) {
+    case DECONV_OK: return "ok";
+    case DECONV_EINVAL: return "invalid argument";
+    case DECONV_EUNSUPPORTED: return "unsupported size";
+    case DECONV_ENOMEM: return "workspace too small";
+    case DECONV_ECUDA: return "CUDA runtime error";
+    case DECONV_ETIMEOUT: return "device wait timed out";
+    case DECONV_ENONFINITE: return "non-finite value in the iterate";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

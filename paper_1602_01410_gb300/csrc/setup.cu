@@ -1,0 +1,225 @@
+// One-time and per-solve setup kernels.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace dcv {
+
+// H^(k1, k2) = sum_{p,q=-b..b} h[p+b][q+b] exp(-2 pi i (k1 p / M + k2 q / N)),
+// the DFT of the kernel placed with its origin at grid index (0, 0) (the
+// eigenvalues of the BCCB matrix T~ of Eq. (4)).  Evaluated directly in
+// double precision with exact integer phase reduction, then rounded once.
+template <typename T>
+__global__ void hhat_kernel(const HhatJob *jobs, int njobs, const long long *job_begin, long long total,
+                            const T *h, cx<T> *hhat) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (job_begin[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  const HhatJob J = jobs[lo];
+  const long long loc = e - job_begin[lo];
+  const int k1 = (int)(loc / J.Nh), k2 = (int)(loc - (long long)k1 * J.Nh);
+  const int b = J.K / 2;
+  double re = 0.0, im = 0.0;
+  for (int p = -b; p <= b; ++p) {
+    double rr = 0.0, ri = 0.0;
+    for (int q = -b; q <= b; ++q) {
+      const long long ph = ((long long)k2 * q) % J.N;
+      double s, c;
+      sincospi(-2.0 * (double)ph / (double)J.N, &s, &c);
+      const double hv = (double)h[J.h + (long long)(p + b) * J.K + (q + b)];
+      rr += hv * c;
+      ri += hv * s;
+    }
+    const long long ph = ((long long)k1 * p) % J.M;
+    double s, c;
+    sincospi(-2.0 * (double)ph / (double)J.M, &s, &c);
+    re += rr * c - ri * s;
+    im += rr * s + ri * c;
+  }
+  hhat[J.out + loc] = mk<T>((T)re, (T)im);
+}
+
+template <typename T>
+cudaError_t launch_hhat(const HhatJob *jobs_dev, int njobs, long long total, const T *h, void *hhat,
+                        const long long *job_begin_dev, cudaStream_t s) {
+  const int nt = 256;
+  const long long grid = (total + nt - 1) / nt;
+  hhat_kernel<T><<<(unsigned)grid, nt, 0, s>>>(jobs_dev, njobs, job_begin_dev, total, h,
+                                                reinterpret_cast<cx<T> *>(hhat));
+  return cudaGetLastError();
+}
+template cudaError_t launch_hhat<float>(const HhatJob *, int, long long, const float *, void *, const long long *,
+                                        cudaStream_t);
+template cudaError_t launch_hhat<double>(const HhatJob *, int, long long, const double *, void *,
+                                         const long long *, cudaStream_t);
+
+// Packs the byte mask (nonzero = observed) into 32-bit words, one bit per
+// pixel, each channel plane padded to whole words.
+__global__ void pack_mask_kernel(const ImageDesc *desc, int nimg, const long long *img_word_begin,
+                                 long long total_words, const uint8_t *mask, uint32_t *bits) {
+  const long long wd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (wd >= total_words) return;
+  int lo = 0, hi = nimg - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (img_word_begin[mid] <= wd) lo = mid; else hi = mid - 1;
+  }
+  const ImageDesc &D = desc[lo];
+  const long long loc = wd - img_word_begin[lo];
+  const long long ch = loc / D.mask_plane, w = loc - ch * D.mask_plane;
+  const long long P = (long long)D.M * D.N;
+  const uint8_t *src = mask + D.px + ch * P;
+  uint32_t v = 0;
+  for (int b = 0; b < 32; ++b) {
+    const long long p = w * 32 + b;
+    if (p < P && src[p] != 0) v |= 1u << b;
+  }
+  bits[D.mask + loc] = v;
+}
+
+cudaError_t launch_pack_mask(const ImageDesc *desc_dev, int nimg, long long total_words,
+                             const long long *img_word_begin_dev, const uint8_t *mask, uint32_t *bits,
+                             cudaStream_t s) {
+  const int nt = 256;
+  pack_mask_kernel<<<(unsigned)((total_words + nt - 1) / nt), nt, 0, s>>>(desc_dev, nimg, img_word_begin_dev,
+                                                                         total_words, mask, bits);
+  return cudaGetLastError();
+}
+
+// Mean of the observed values of each (image, channel) plane, in double,
+// reduced in a fixed order (one CTA per plane).
+template <typename T>
+__global__ void means_kernel(const ImageDesc *desc, const int *plane_img, const T *y, const uint32_t *bits,
+                             double *means) {
+  const int plane = blockIdx.x;
+  const int img = plane_img[2 * plane], ch = plane_img[2 * plane + 1];
+  const ImageDesc &D = desc[img];
+  const long long P = (long long)D.M * D.N;
+  const T *src = y + D.px + ch * P;
+  const long long w0 = D.mask + ch * D.mask_plane;
+  double s = 0.0, c = 0.0;
+  for (long long p = threadIdx.x; p < P; p += blockDim.x)
+    if ((bits[w0 + (p >> 5)] >> (p & 31)) & 1u) {
+      s += (double)src[p];
+      c += 1.0;
+    }
+  __shared__ double rs[256], rc[256];
+  rs[threadIdx.x] = s;
+  rc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rs[threadIdx.x] += rs[threadIdx.x + o];
+      rc[threadIdx.x] += rc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) means[plane] = rc[0] > 0 ? rs[0] / rc[0] : 0.0;
+}
+
+template <typename T>
+cudaError_t launch_means(const ImageDesc *desc_dev, int nplanes, const int *plane_img_dev, const T *y,
+                         const uint32_t *bits, double *means, cudaStream_t s) {
+  means_kernel<T><<<nplanes, 256, 0, s>>>(desc_dev, plane_img_dev, y, bits, means);
+  return cudaGetLastError();
+}
+template cudaError_t launch_means<float>(const ImageDesc *, int, const int *, const float *, const uint32_t *,
+                                         double *, cudaStream_t);
+template cudaError_t launch_means<double>(const ImageDesc *, int, const int *, const double *,
+                                          const uint32_t *, double *, cudaStream_t);
+
+// y~0 (Sec. III-B: the observed image padded by repeating its border
+// pixels).  Observed pixels take y.  An unobserved pixel of the boundary band
+// takes y at the clamped valid-region index when that pixel is observed;
+// every other unobserved pixel takes the plane's observed mean rounded to T.
+// y may alias yt (observed entries are then left untouched).
+template <typename T>
+__global__ void init_fill_kernel(const ImageDesc *desc, int nimg, const long long *img_px_begin, long long total,
+                                 const T *y, const uint32_t *bits, const double *means, int K, T *yt) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int lo = 0, hi = nimg - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (img_px_begin[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  const ImageDesc &D = desc[lo];
+  const long long P = (long long)D.M * D.N, loc = e - D.px;
+  const int ch = (int)(loc / P);
+  const long long p = loc - ch * P;
+  const int i = (int)(p / D.N), j = (int)(p - (long long)i * D.N);
+  const long long w0 = D.mask + ch * D.mask_plane;
+  const bool obs = (bits[w0 + (p >> 5)] >> (p & 31)) & 1u;
+  if (obs) {
+    if (y != yt) yt[e] = y[e];
+    return;
+  }
+  const int b = K / 2;
+  T v = (T)means[(long long)lo * D.C + ch];  // every image of a plan has the same channel count
+  const bool band = i < b || i >= D.M - b || j < b || j >= D.N - b;
+  if (band) {
+    const int ic = i < b ? b : (i >= D.M - b ? D.M - b - 1 : i);
+    const int jc = j < b ? b : (j >= D.N - b ? D.N - b - 1 : j);
+    const long long pc = (long long)ic * D.N + jc;
+    if ((bits[w0 + (pc >> 5)] >> (pc & 31)) & 1u) v = y[D.px + ch * P + pc];
+  }
+  yt[e] = v;
+}
+
+template <typename T>
+cudaError_t launch_init_fill(const ImageDesc *desc_dev, int nimg, long long total_px,
+                             const long long *img_px_begin_dev, const T *y, const uint32_t *bits,
+                             const double *means, int K, T *yt, cudaStream_t s) {
+  const int nt = 256;
+  init_fill_kernel<T><<<(unsigned)((total_px + nt - 1) / nt), nt, 0, s>>>(desc_dev, nimg, img_px_begin_dev,
+                                                                          total_px, y, bits, means, K, yt);
+  return cudaGetLastError();
+}
+template cudaError_t launch_init_fill<float>(const ImageDesc *, int, long long, const long long *, const float *,
+                                             const uint32_t *, const double *, int, float *, cudaStream_t);
+template cudaError_t launch_init_fill<double>(const ImageDesc *, int, long long, const long long *,
+                                              const double *, const uint32_t *, const double *, int, double *,
+                                              cudaStream_t);
+
+// Per-image sums of the row-pass partials in a fixed order:
+// stats[img][it][0..2] = ||d^{i+1} - d^i||^2, ||z^{i+1} - z^i||^2, J(x^{i+1}).
+__global__ void stats_reduce_kernel(const ImageDesc *desc, const double *partials, double *stats, int iters,
+                                    int it, int *err) {
+  const int img = blockIdx.x;
+  const ImageDesc &D = desc[img];
+  __shared__ double r[3][128];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int q = threadIdx.x; q < D.row_blocks; q += blockDim.x) {
+    const long long o = 3LL * (D.row_begin + q);
+    a += partials[o];
+    b += partials[o + 1];
+    c += partials[o + 2];
+  }
+  r[0][threadIdx.x] = a;
+  r[1][threadIdx.x] = b;
+  r[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 3; ++k) r[k][threadIdx.x] += r[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double *out = stats + 3LL * ((long long)img * iters + it);
+    out[0] = r[0][0];
+    out[1] = r[1][0];
+    out[2] = r[2][0];
+    if (!isfinite(r[2][0])) atomicOr(err, 1);
+  }
+}
+
+cudaError_t launch_stats_reduce(const ImageDesc *desc_dev, int nimg, const double *partials, double *stats,
+                                int iters, int it, int *err, cudaStream_t s) {
+  stats_reduce_kernel<<<nimg, 128, 0, s>>>(desc_dev, partials, stats, iters, it, err);
+  return cudaGetLastError();
+}
+
+}  // namespace dcv

@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances: relative L2 <= 1e-5 after one iteration (FP32), <= 1e-3 and
+|dPSNR| <= 0.01 dB after a full run (FP32); the FP64 instantiation must stay
+within 1e-10.  Masks and indexing are exact (the zero-iteration output is the
+initial fill, compared bit for bit)."""
+import numpy as np
+import pytest
+
+from paper_1602_01410_gb300 import inputs
+
+from gpu_helpers import gpu_solve, oracle_solve, psnr, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_one_iteration_uneven_batch_random_mask():
+    # several row blocks and column tiles per image, ragged last tiles, odd N
+    prob = inputs.random_problem(11, [(96, 160), (120, 90), (45, 75), (64, 64)], 7, mask_kind="random",
+                                 frac=0.4, iters=1)
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    for a, b in zip(xg, xo):
+        assert rel_l2([a], [b]) <= 1e-5
+
+
+def test_one_iteration_vectorial_tv_bayer():
+    prob = inputs.random_problem(12, [(64, 80), (60, 48)], 5, mask_kind="bayer", channels=3, iters=1)
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    for a, b in zip(xg, xo):
+        assert rel_l2([a], [b]) <= 1e-5
+
+
+def test_one_iteration_decimation_and_crop():
+    p1 = inputs.random_problem(13, [(96, 96), (48, 72)], 9, mask_kind="decim4", iters=1, lam=2e-4, mu=1e-3)
+    p2 = inputs.random_problem(14, [(40, 50)], 3, mask_kind="crop", iters=1, psf="uniform")
+    for prob in (p1, p2):
+        xg, _, _ = gpu_solve(prob)
+        xo, _ = oracle_solve(prob)
+        assert rel_l2(xg, xo) <= 1e-5
+
+
+def test_twenty_iterations_motion_blur():
+    prob = inputs.random_problem(15, [(80, 120)], 9, mask_kind="random", frac=0.4, iters=20, psf="motion")
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    assert rel_l2(xg, xo) <= 1e-4
+
+
+def test_zero_iterations_is_the_initial_fill_bit_exact():
+    import oracle
+    prob = inputs.random_problem(16, [(48, 60), (30, 40)], 5, mask_kind="random", frac=0.5, iters=0)
+    xg, _, _ = gpu_solve(prob, iters=0)
+    for j in range(2):
+        want = oracle.init_ytilde(prob.y[j][0], prob.mask[j][0], prob.ksize, round_f32=True)
+        assert np.array_equal(xg[j][0], want.astype(np.float32).astype(np.float64))
+
+
+def test_c1_fp64_full_run():
+    prob = inputs.config_c1("f64")
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    assert rel_l2(xg, xo) <= 1e-10
+
+
+def test_c1_fp32_full_run():
+    prob = inputs.config_c1("f32")
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    assert rel_l2(xg, xo) <= 1e-3
+    xt = prob.x_true[0]
+    assert abs(psnr(xg[0], xt) - psnr(xo[0], xt)) <= 0.01
+
+
+def test_stats_match_oracle():
+    prob = inputs.random_problem(17, [(64, 96), (48, 48)], 5, mask_kind="random", frac=0.3, iters=8)
+    xg, sg, _ = gpu_solve(prob, stats=True)
+    _, so = oracle_solve(prob, stats=True)
+    for j in range(2):
+        o = so[j]
+        # columns: ||dd||^2, ||dz||^2, J  (oracle: dd, dz, mu dv, J)
+        assert np.allclose(sg[j][:, 2], o[:, 3], rtol=1e-4)
+        assert np.allclose(sg[j][1:, 0], o[1:, 0], rtol=2e-3, atol=1e-12)
+        assert np.allclose(sg[j][:, 1], o[:, 1], rtol=2e-3, atol=1e-12)
+
+
+def test_relax_one_matches_oracle():
+    prob = inputs.random_problem(18, [(60, 64)], 5, mask_kind="random", frac=0.3, iters=10)
+    xg, _, _ = gpu_solve(prob, relax=1.0)
+    xo, _ = oracle_solve(prob, relax=1.0)
+    assert rel_l2(xg, xo) <= 1e-4
+
+
+def test_graph_replay_equals_direct_launches_and_is_deterministic():
+    prob = inputs.random_problem(19, [(64, 80)], 5, mask_kind="random", frac=0.3, iters=45)
+    a, _, _ = gpu_solve(prob)                 # graph replays
+    b, _, _ = gpu_solve(prob, stats=True)     # direct launches
+    c, _, _ = gpu_solve(prob)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[0], c[0])
+
+
+def test_warm_continuation():
+    import torch
+    prob = inputs.random_problem(20, [(48, 64)], 5, mask_kind="random", frac=0.3, iters=7)
+    full, _, _ = gpu_solve(prob)
+    _, _, plan = gpu_solve(prob, iters=4)
+    x = plan.solve(None, 3, warm=True)
+    assert plan.sync() == 0
+    assert np.array_equal(x.double().cpu().numpy().reshape(full[0].shape), full[0])
+
+
+def test_solve_host_matches_device():
+    import torch
+    prob = inputs.random_problem(21, [(48, 64), (40, 40)], 5, mask_kind="random", frac=0.3, iters=6)
+    xd, _, plan = gpu_solve(prob)
+    y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=torch.float32).pin_memory()
+    xh = torch.empty_like(y).pin_memory()
+    plan.solve_host(y, xh, prob.iters)
+    assert np.array_equal(xh.double().numpy(), np.concatenate([a.ravel() for a in xd]))
+
+
+def test_nonfinite_input_reported():
+    import paper_1602_01410_gb300 as pkg
+    import torch
+    prob = inputs.random_problem(22, [(32, 40)], 3, mask_kind="crop", iters=2)
+    dev = torch.device("cuda:0")
+    y = torch.tensor(prob.y[0], dtype=torch.float32, device=dev).reshape(-1)
+    y[20 * 40 + 20] = float("nan")
+    plan = pkg.Plan(prob.shapes, torch.tensor(prob.h, dtype=torch.float32, device=dev),
+                    torch.tensor(prob.mask[0], dtype=torch.uint8, device=dev), prob.lam, prob.mu)
+    plan.solve(y, 2)
+    assert plan.sync() == pkg.DECONV_ENONFINITE
+    plan.solve(torch.tensor(prob.y[0], dtype=torch.float32, device=dev).reshape(-1), 2)
+    assert plan.sync() == pkg.DECONV_OK
+
+
+def test_zero_dc_gain_rejected():
+    import paper_1602_01410_gb300 as pkg
+    import torch
+    dev = torch.device("cuda:0")
+    h = torch.zeros((3, 3), dtype=torch.float32, device=dev)
+    h[0, 0], h[2, 2] = 1.0, -1.0
+    mask = torch.ones(32 * 32, dtype=torch.uint8, device=dev)
+    with pytest.raises(pkg.DeconvError) as e:
+        pkg.Plan([(32, 32)], h, mask, 1e-3, 1e-2)
+    assert e.value.status == pkg.DECONV_EINVAL
