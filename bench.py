@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark of the partial-ADMM deconvolution hot path on GB300.
+
+Metric: Mpixel * ADMM-iterations / s (channel-pixels of the extended grid
+times iterations, per second of device time), whole job over all ranks.
+
+A step is one deconv_solve call of the workload: the initial fill (border
+padding) and the workload's full iteration count, inputs resident in HBM.
+Default workload (N = 1): 1024 x 1024 FP32 image, 21 x 21 random-walk motion
+blur, 1004 x 1004 valid crop with 40% of the pixels missing, BSNR 40 dB,
+500 iterations.  Single-image work does not shard: under torchrun every rank
+solves its own replica (weak scaling, no data-path collective).
+
+Timing: W untimed warm-up steps, then K steps, each preceded by an L2 flush
+(a 512 MB device write, outside the timed events) and bracketed by CUDA
+events on the plan's stream; a barrier and a device synchronise on both
+sides; the max over ranks.  `e2e` times the same step through
+deconv_solve_host (pinned host y in, host x out, copies included).
+`roofline` reports the dominant kernel (the row or column pass) from CUDA
+events around its launches (deconv_profile_passes) and its compulsory bytes.
+`cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
+`--impl reference` times the oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "c2": "1024x1024 FP32, 21x21 random-walk motion blur, 1004x1004 valid crop with 40% missing, "
+          "BSNR 40 dB, lambda 2e-6, mu 1e-3, 500 iterations",
+    "c1": "64x64 FP64, 9x9 uniform blur, 56x56 valid crop, BSNR 50 dB, lambda 2e-5, mu 1e-3, 300 iterations",
+    "c3": "16 FP32 images with sides from {256..1024}, 9x9 Gaussian (sigma 2), x4 decimation, "
+          "BSNR 40 dB, lambda 2e-4, mu 1e-3, 300 iterations",
+    "c4": "32 RGB FP32 frames with sides from {512..1536}, 13x13 Gaussian (sigma 2.5), RGGB Bayer, "
+          "vectorial TV, BSNR 45 dB, lambda 1e-5, mu 1e-3, 400 iterations",
+    "c5": "8 FP32 512x512 images, 15x15 Gaussian, 20% missing, BSNR 40 dB, lambda 5e-6, mu 1e-3, "
+          "100 iterations",
+}
+
+
+def make_problem(name: str):
+    from paper_1602_01410_gb300 import inputs
+    return {"c1": lambda: inputs.config_c1("f64"), "c2": inputs.config_c2, "c3": inputs.config_c3,
+            "c4": inputs.config_c4, "c5": inputs.config_c5}[name]()
+
+
+# Compulsory bytes per pixel of one launch of each pass (FP32, two-pass
+# design): column pass = read (Y_row, R_row) 8 + read H^ 4 + write (X_row,
+# HX_row) 8; row pass = read (X_row, HX_row) 8 + y~ 4 + d 8 (read) + d 8
+# (write) + z 4f (write, f = unobserved fraction) + mask 1/8 + write
+# (Y_row, R_row) 8.
+def pass_bytes_per_px(f_unobs: float, esz: int = 4):
+    s = esz / 4.0
+    return {"col": 20.0 * s, "row": (36.0 + 4.0 * f_unobs) * s + 0.125}
+
+
+def algorithmic_bytes_per_px(f_unobs: float, esz: int = 4) -> float:
+    """Bytes one iteration must move by the method itself: y~ 4, z 4f,
+    d read+write 16, H^ half-spectrum 4, mask 1/8 (FP32)."""
+    return (24.0 + 4.0 * f_unobs) * esz / 4.0 + 0.125
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        for s in self.samples:
+            for name, v in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], s[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(name: str, budget_s: float = 20.0):
+    """FP64 oracle on the host cores: a bounded sample of the workload."""
+    import oracle
+    prob = make_problem(name)
+    j = 0
+    y, m = prob.y[j], prob.mask[j]
+    px = prob.channels * y.shape[-2] * y.shape[-1]
+    t0 = time.perf_counter()
+    oracle.admm(y, m, prob.h, prob.lam, prob.mu, 1)
+    t1 = time.perf_counter()
+    per_iter = max(t1 - t0, 1e-3)
+    n = max(2, min(prob.iters, int(budget_s / per_iter)))
+    t0 = time.perf_counter()
+    oracle.admm(y, m, prob.h, prob.lam, prob.mu, n)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": px * n / dt / 1e6, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
+            "sample": f"image 0 of the workload ({y.shape[-2]}x{y.shape[-1]}x{prob.channels}), {n} iterations "
+                      f"incl. setup, FP64 C+OpenMP, {dt:.1f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    prob = make_problem(args.config)
+    y, m = prob.y[0], prob.mask[0]
+    px = prob.channels * y.shape[-2] * y.shape[-1]
+    sample_iters = max(1, min(prob.iters, args.ref_iters))
+    for _ in range(args.warmup):
+        oracle.admm(y, m, prob.h, prob.lam, prob.mu, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.admm(y, m, prob.h, prob.lam, prob.mu, sample_iters)
+    dt = time.perf_counter() - t0
+    value = px * sample_iters * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": "Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator)",
+           "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}",
+                      "sample": f"image 0, {sample_iters} iterations per step"},
+           "cpu_baseline": {"value": value, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
+                            "sample": f"image 0 of the workload, {sample_iters} iterations per step, "
+                                      f"{args.steps} steps"},
+           "e2e": {"value": value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-iters", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1602_01410_gb300 as pkg
+    from paper_1602_01410_gb300 import build as pkg_build
+
+    pkg_build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    prob = make_problem(args.config)
+    dt = torch.float64 if prob.dtype == "f64" else torch.float32
+    esz = 8 if prob.dtype == "f64" else 4
+    h = torch.tensor(prob.h, dtype=dt, device=dev)
+    mask_np = np.concatenate([m.ravel() for m in prob.mask])
+    y_np = np.concatenate([a.ravel() for a in prob.y])
+    mask = torch.tensor(mask_np, dtype=torch.uint8, device=dev)
+    y = torch.tensor(y_np, dtype=dt, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu, channels=prob.channels, stream=stream)
+    x = torch.empty_like(y)
+    px = prob.pixels()
+    f_unobs = float(1.0 - mask_np.mean())
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        plan.solve(y, prob.iters, x=x)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    status = plan.sync()
+    if status != pkg.DECONV_OK:
+        raise SystemExit(f"solve failed: {pkg.deconv_status_string(status)}")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if plan.sync() != pkg.DECONV_OK:
+        raise SystemExit("solve reported a device error")
+    t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_ms = float(t.item())
+    units = px * prob.iters * args.steps * world
+    value = units / (t_ms / 1e3) / 1e6
+
+    # End to end through the host-buffer entry point.
+    y_host = torch.tensor(y_np, dtype=dt).pin_memory()
+    x_host = torch.empty_like(y_host).pin_memory()
+    plan.solve_host(y_host, x_host, prob.iters)
+    barrier()
+    e2e_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        plan.solve_host(y_host, x_host, prob.iters)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e, op=dist.ReduceOp.MAX)
+    e2e_value = units / (float(e.item()) / 1e3) / 1e6
+
+    # Dominant kernel: per-pass durations from CUDA events around launches.
+    prof_iters = min(prob.iters, 100)
+    ms_col, ms_row = plan.profile_passes(prof_iters)
+    per_px = pass_bytes_per_px(f_unobs, esz)
+    peak, peak_kind = measured_peak_hbm()
+    dom, ms_dom = ("row", ms_row) if ms_row >= ms_col else ("col", ms_col)
+    achieved = per_px[dom] * px / (ms_dom / 1e3) / 1e9
+    launches_per_step = 3 + 2 * prob.iters
+
+    out = {
+        "metric": "Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if esz == 8 else "f32", "data": "synthetic (seeded generator)",
+        "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}",
+                   "pixels_per_iter": px, "iterations": prob.iters,
+                   "l2": "flushed before every timed step (512 MB write); the plan's "
+                         f"{plan.workspace_bytes / 2**20:.0f} MB workspace is reused across the step's iterations",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": e2e_value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": int(y_np.size * esz),
+                "d2h_bytes_per_step": int(y_np.size * esz)},
+        "roofline": {"bound": "hbm", "kernel": f"{dom}_pass", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "ms_per_launch": ms_dom, "bytes_per_px": per_px[dom],
+                     "other_pass_ms": ms_col if dom == "row" else ms_row,
+                     "algorithmic_bytes_per_px_iter": algorithmic_bytes_per_px(f_unobs, esz)},
+        "clocks": clk,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.config)
+    if rank == 0:
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -116,6 +116,14 @@ deconv_status deconv_solve(deconv_plan plan, const void *y, void *x, int32_t ite
  * before returning.  Uses the workspace as staging; nothing is allocated. */
 deconv_status deconv_solve_host(deconv_plan plan, const void *y_host, void *x_host, int32_t iters);
 
+/* Diagnostic timing (no counterpart in the paper): continue from the plan's
+ * state for `iters` >= 1 iterations launched one kernel at a time, with a
+ * CUDA event before and after every launch on the plan's stream, and return
+ * in ms_host[0] / ms_host[1] the mean duration of one column pass / one row
+ * pass (HOST array of 2 floats).  Requires a state (a previous
+ * deconv_solve).  Synchronises the stream. */
+deconv_status deconv_profile_passes(deconv_plan plan, int32_t iters, float *ms_host);
+
 /* Wait for the plan's stream and report device-side errors recorded since
  * the last call (DECONV_ENONFINITE, DECONV_ETIMEOUT), then clear them. */
 deconv_status deconv_sync(deconv_plan plan);

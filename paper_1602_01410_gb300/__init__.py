@@ -27,7 +27,7 @@ DECONV_F32, DECONV_F64 = 0, 1
 
 # Entry points declared in include/deconv.h (checked by the test suite).
 EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "deconv_solve_host",
-           "deconv_sync", "deconv_plan_destroy", "deconv_status_string")
+           "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string")
 
 
 class DeconvError(RuntimeError):
@@ -59,6 +59,7 @@ def load() -> ctypes.CDLL:
                                            vp, ctypes.c_size_t, vp]
         lib.deconv_solve.argtypes = [vp, vp, vp, i32, i32, vp]
         lib.deconv_solve_host.argtypes = [vp, vp, vp, i32]
+        lib.deconv_profile_passes.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         lib.deconv_sync.argtypes = [vp]
         lib.deconv_plan_destroy.argtypes = [vp]
         lib.deconv_status_string.argtypes = [ctypes.c_int]
@@ -114,6 +115,13 @@ def deconv_solve_host(plan: int, y_host_ptr: int, x_host_ptr: int, iters: int) -
     _check(load().deconv_solve_host(plan, y_host_ptr, x_host_ptr, int(iters)), "deconv_solve_host")
 
 
+def deconv_profile_passes(plan: int, iters: int):
+    """Mean (column pass, row pass) kernel durations in ms over `iters` iterations."""
+    out = (ctypes.c_float * 2)()
+    _check(load().deconv_profile_passes(plan, int(iters), out), "deconv_profile_passes")
+    return float(out[0]), float(out[1])
+
+
 def deconv_sync(plan: int) -> int:
     """Returns the device-side status (DECONV_OK, DECONV_ENONFINITE, ...)."""
     return load().deconv_sync(plan)
@@ -167,6 +175,9 @@ class Plan:
 
     def solve_host(self, y_host, x_host, iters: int) -> None:
         deconv_solve_host(self.handle, y_host.data_ptr(), x_host.data_ptr(), iters)
+
+    def profile_passes(self, iters: int):
+        return deconv_profile_passes(self.handle, iters)
 
     def sync(self) -> int:
         return deconv_sync(self.handle)

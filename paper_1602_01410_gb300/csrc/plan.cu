@@ -507,6 +507,52 @@ deconv_status deconv_solve_host(deconv_plan p, const void *y_host, void *x_host,
   return deconv_sync(p);
 }
 
+deconv_status deconv_profile_passes(deconv_plan p, int32_t iters, float *ms_host) {
+  if (!p || iters < 1 || !ms_host || !p->have_state) return DECONV_EINVAL;
+  const Layout &L = p->L;
+  std::vector<cudaEvent_t> ev(4 * (size_t)iters);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  deconv_status st = DECONV_OK;
+  for (int it = 0; it < iters && st == DECONV_OK; ++it) {
+    cudaError_t e = cudaEventRecord(ev[4 * it], p->stream);
+    if (L.dtype == DECONV_F32) {
+      if (e == cudaSuccess) e = launch_col<float>(col_args<float>(p), L.col_grid, L.nt, L.col_smem, p->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 1], p->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 2], p->stream);
+      if (e == cudaSuccess)
+        e = launch_row<float>(row_args<float>(p, ROW_ITER, dbuf<float>(p, p->parity), dbuf<float>(p, p->parity ^ 1),
+                                              nullptr, nullptr),
+                              L.row_grid, L.nt, L.C, L.row_smem, p->stream);
+    } else {
+      if (e == cudaSuccess) e = launch_col<double>(col_args<double>(p), L.col_grid, L.nt, L.col_smem, p->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 1], p->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 2], p->stream);
+      if (e == cudaSuccess)
+        e = launch_row<double>(row_args<double>(p, ROW_ITER, dbuf<double>(p, p->parity),
+                                                dbuf<double>(p, p->parity ^ 1), nullptr, nullptr),
+                               L.row_grid, L.nt, L.C, L.row_smem, p->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 3], p->stream);
+    if (e != cudaSuccess) st = DECONV_ECUDA;
+    p->parity ^= 1;
+  }
+  if (st == DECONV_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) st = DECONV_ECUDA;
+  double col = 0.0, row = 0.0;
+  for (int it = 0; it < iters && st == DECONV_OK; ++it) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, ev[4 * it], ev[4 * it + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, ev[4 * it + 2], ev[4 * it + 3]) != cudaSuccess)
+      st = DECONV_ECUDA;
+    col += a;
+    row += b;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (st != DECONV_OK) return st;
+  ms_host[0] = (float)(col / iters);
+  ms_host[1] = (float)(row / iters);
+  return DECONV_OK;
+}
+
 deconv_status deconv_sync(deconv_plan p) {
   if (!p) return DECONV_EINVAL;
   int err = 0;
