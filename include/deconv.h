@@ -116,6 +116,28 @@ deconv_status deconv_solve(deconv_plan plan, const void *y, void *x, int32_t ite
  * before returning.  Uses the workspace as staging; nothing is allocated. */
 deconv_status deconv_solve_host(deconv_plan plan, const void *y_host, void *x_host, int32_t iters);
 
+/* Allocation-free solve (the paper has no counterpart; this is a service of
+ * the library).  For callers that may not allocate device memory: code
+ * hosted inside a framework that owns the CUDA allocator, latency-critical
+ * paths where an allocation could block, or plugins in a process whose
+ * device memory was reserved up front.  Runs deconv_plan_create +
+ * deconv_solve(warm = 0) + deconv_sync + deconv_plan_destroy with the plan
+ * workspace placed in a 32 MiB array that the library reserves statically on
+ * every GPU that loads it (held until the process exits); it calls no
+ * cudaMalloc, cudaFree or other allocating routine and builds no CUDA graph.
+ * Arguments are those of deconv_plan_create and deconv_solve (device h,
+ * mask, y, x; host dims).  Returns DECONV_ENOMEM, before any launch, when
+ * deconv_workspace_size(dims) exceeds 32 MiB (for example a single FP32
+ * image up to about 700 x 700).  The first call on a device looks up the
+ * array's device address, with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one array
+ * (plan creation clears what must start at zero), so calls whose work
+ * overlaps on the GPU (other threads or streams) race: serialise them.
+ * Synchronises `stream` and returns device-side errors like deconv_sync. */
+deconv_status deconv_solve_noalloc(const deconv_dims *dims, const void *h, const uint8_t *mask,
+                                   const void *y, void *x, double lambda, double mu, int32_t iters,
+                                   void *stream);
+
 /* Diagnostic timing (no counterpart in the paper): continue from the plan's
  * state for `iters` >= 1 iterations launched one kernel at a time, with a
  * CUDA event before and after every launch on the plan's stream, and return

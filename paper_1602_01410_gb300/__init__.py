@@ -27,7 +27,8 @@ DECONV_F32, DECONV_F64 = 0, 1
 
 # Entry points declared in include/deconv.h (checked by the test suite).
 EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "deconv_solve_host",
-           "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string")
+           "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
+           "deconv_solve_noalloc")
 
 
 class DeconvError(RuntimeError):
@@ -61,6 +62,7 @@ def load() -> ctypes.CDLL:
         lib.deconv_solve_host.argtypes = [vp, vp, vp, i32]
         lib.deconv_profile_passes.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         lib.deconv_sync.argtypes = [vp]
+        lib.deconv_solve_noalloc.argtypes = [ctypes.POINTER(deconv_dims), vp, vp, vp, vp, dbl, dbl, i32, vp]
         lib.deconv_plan_destroy.argtypes = [vp]
         lib.deconv_status_string.argtypes = [ctypes.c_int]
         lib.deconv_status_string.restype = ctypes.c_char_p
@@ -125,6 +127,14 @@ def deconv_profile_passes(plan: int, iters: int):
 def deconv_sync(plan: int) -> int:
     """Returns the device-side status (DECONV_OK, DECONV_ENONFINITE, ...)."""
     return load().deconv_sync(plan)
+
+
+def deconv_solve_noalloc(dims: deconv_dims, h_ptr: int, mask_ptr: int, y_ptr: int, x_ptr: int, lam: float,
+                         mu: float, iters: int, stream: int) -> None:
+    """Whole solve with the workspace in the library's static 32 MiB device
+    array (no device allocation); synchronises `stream`."""
+    _check(load().deconv_solve_noalloc(ctypes.byref(dims), h_ptr, mask_ptr, y_ptr, x_ptr, float(lam), float(mu),
+                                       int(iters), stream), "deconv_solve_noalloc")
 
 
 def deconv_plan_destroy(plan: int) -> None:
