@@ -150,6 +150,88 @@ template <typename T, int SIGN> struct Dft<T, 16, SIGN> {
   }
 };
 
+template <typename T, int SIGN> struct Dft<T, 1, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *) {}
+};
+
+// 32 = 2 x 16.
+template <typename T, int SIGN> struct Dft<T, 32, SIGN> {
+  static __device__ __forceinline__ void run(cx<T> *v) {
+    // cos, sin of q pi / 16 for q = 0..15
+    const T C[16] = {T(1.0), T(0.98078528040323044913), T(0.92387953251128675613), T(0.83146961230254523708),
+                     T(0.70710678118654752440), T(0.55557023301960222474), T(0.38268343236508977173),
+                     T(0.19509032201612826785), T(0.0), T(-0.19509032201612826785), T(-0.38268343236508977173),
+                     T(-0.55557023301960222474), T(-0.70710678118654752440), T(-0.83146961230254523708),
+                     T(-0.92387953251128675613), T(-0.98078528040323044913)};
+    const T S[16] = {T(0.0), T(0.19509032201612826785), T(0.38268343236508977173), T(0.55557023301960222474),
+                     T(0.70710678118654752440), T(0.83146961230254523708), T(0.92387953251128675613),
+                     T(0.98078528040323044913), T(1.0), T(0.98078528040323044913), T(0.92387953251128675613),
+                     T(0.83146961230254523708), T(0.70710678118654752440), T(0.55557023301960222474),
+                     T(0.38268343236508977173), T(0.19509032201612826785)};
+    cx<T> e[16], o[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      e[r] = v[2 * r];
+      o[r] = v[2 * r + 1];
+    }
+    Dft<T, 16, SIGN>::run(e);
+    Dft<T, 16, SIGN>::run(o);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      cx<T> t = (q == 0) ? o[0] : (q == 8 ? mul_si<T, SIGN>(o[8]) : cmul<T>(o[q], mk<T>(C[q], SIGN * S[q])));
+      v[q] = cadd<T>(e[q], t);
+      v[q + 16] = csub<T>(e[q], t);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Register-resident transform of length L = 32 TT by a group of TT threads
+// (TT in {1, 2, 4, 8, 16, 32}; a group never spans two warps).  Index split
+// n = t + TT m (t < TT, m < 32), k = k1 + 32 k2 (k1 < 32, k2 < TT):
+//   X[k1 + 32 k2] = sum_t w_TT^(t k2) [ w_L^(t k1) sum_m x[t + TT m] w_32^(m k1) ],
+// the two-factor Cooley-Tukey split.  Thread q of the group enters with
+// v[m] = x[q + TT m] and leaves with v[j TT + k2] = X[q + TT j + 32 k2]
+// (j < 32/TT), i.e. v[r] holds index q + TT * p2_slot(r).  Step 1 is a 32-point
+// DFT in registers, then one twiddle multiply from a table laid out
+// [k1][t] (coalesced), one transpose through the group's shared tile, and
+// TT-point DFTs in registers.  The tile is padded (row stride TT+1, group
+// stride p2_group_stride) so the transposing accesses are free of bank
+// conflicts.
+template <int TT> __host__ __device__ constexpr int p2_group_stride() {
+  return 32 * (TT + 1) + (TT < 16 ? TT : 0);
+}
+
+// Position index m of register r after the transform (see above).
+template <int TT> __device__ __forceinline__ constexpr int p2_slot(int r) {
+  return (r / TT) + (32 / TT) * (r % TT);
+}
+
+template <typename T, int TT, int SIGN>
+__device__ __forceinline__ void fft_p2(cx<T> (&v)[32], cx<T> *tile, int q, unsigned gmask,
+                                       const cx<T> *__restrict__ tw2) {
+  Dft<T, 32, SIGN>::run(v);
+  if constexpr (TT > 1) {
+#pragma unroll
+    for (int k1 = 1; k1 < 32; ++k1) {
+      cx<T> w = __ldg(&tw2[k1 * TT + q]);
+      if (SIGN > 0) w.y = -w.y;
+      v[k1] = cmul<T>(v[k1], w);
+    }
+    constexpr int LD = TT + 1;
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) tile[k1 * LD + q] = v[k1];
+    __syncwarp(gmask);
+#pragma unroll
+    for (int j = 0; j < 32 / TT; ++j) {
+#pragma unroll
+      for (int t = 0; t < TT; ++t) v[j * TT + t] = tile[(q + TT * j) * LD + t];
+      Dft<T, TT, SIGN>::run(&v[j * TT]);
+    }
+    __syncwarp(gmask);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // One radix-R Stockham pass over S signals of length L held in buf.  The
 // host plans S * L <= 30 NT so that every butterfly has a register slot.

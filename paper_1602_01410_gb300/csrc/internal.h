@@ -17,8 +17,9 @@ struct ImageDesc {
   int W;                 // spectral columns (k2) per column-pass CTA
   int row_blocks;        // ceil(M / Rb)
   int col_tiles;         // ceil(Nh / W) (per channel)
-  int row_begin;         // first row-pass work item of this image
-  int col_begin;         // first column-pass work item (C * col_tiles items)
+  int row_begin;         // first row-pass work item of this image within its kernel class
+  int col_begin;         // first column-pass work item (C * col_tiles items) within its class
+  int row_pbase;         // first row-pass work item over the whole plan (statistics partials)
   long long px;          // first pixel (real element) of the image, batch layout
   long long spec;        // first cpair of the image in the spectral buffers
   long long hhat;        // first complex of the image's H^ half-spectrum
@@ -26,6 +27,7 @@ struct ImageDesc {
   long long mask_plane;  // words per channel plane
   int tw_row, tw_col;    // twiddle-table offsets for lengths N and M
   int s2_row, s2_col;    // 4 sin^2(pi k / L) table offsets for N and M
+  int tw2_row, tw2_col;  // [k1][t] twiddle-table offsets (power-of-two lengths), -1 if none
   FftSched sched_row, sched_col;
 };
 
@@ -37,7 +39,8 @@ enum RowMode { ROW_ITER = 0, ROW_INIT = 1 };
 
 template <typename T> struct RowArgs {
   const ImageDesc *desc;
-  int nimg;
+  const int *cls_imgs;    // images of the launched kernel class, by increasing row_begin
+  int nimg;               // entries of cls_imgs
   int mode;           // RowMode
   T *yt;              // y~ (observed: y, unobserved: z), batch layout
   const T *d_in;      // d_x^i as (d_h, d_v) pairs per pixel; NULL = zero
@@ -46,6 +49,7 @@ template <typename T> struct RowArgs {
   cpair<T> *S_out;        // (Y_row, R_row) for the next column pass
   const uint32_t *mask;   // packed observed bits
   const void *tw;         // twiddle tables (cx<T>)
+  const void *tw2;        // [k1][t] twiddle tables of the power-of-two transforms (cx<T>)
   T mu, tau, relax, lambda;
   T *x_out;               // nullable: x^{i+1} for owned rows
   double *partials;       // nullable: per work item [3] = sum dd^2, dz^2, J
@@ -54,23 +58,38 @@ template <typename T> struct RowArgs {
 
 template <typename T> struct ColArgs {
   const ImageDesc *desc;
+  const int *cls_imgs;
   int nimg;
   const cpair<T> *S_in;
   cpair<T> *S_out;
   const void *hhat;   // cx<T>
   const void *tw;     // cx<T>
+  const void *tw2;    // cx<T>, [k1][t] layout
   const T *s2;        // 4 sin^2 tables
   T mu;
   int *err;
 };
 
-// Kernel launchers (kernels_*.cu).  nt = threads per CTA (256 or 512).
+// One launch of a pass over the images of one kernel class.
+enum KernelKind { KIND_GENERIC = 0, KIND_P2 = 1 };
+struct LaunchCfg {
+  int kind;      // KernelKind
+  int tt;        // KIND_P2: threads per transform (length / 32)
+  int nt;        // threads per CTA
+  int channels;  // 1 or 3
+  int grid;      // CTAs
+  size_t smem;   // dynamic shared memory per CTA
+};
+
+// Kernel launchers (kernels_*.cu).
 template <typename T>
-cudaError_t launch_row(const RowArgs<T> &a, int grid, int nt, int channels, size_t smem, cudaStream_t s);
+cudaError_t launch_row(const RowArgs<T> &a, const LaunchCfg &c, cudaStream_t s);
 template <typename T>
-cudaError_t launch_col(const ColArgs<T> &a, int grid, int nt, size_t smem, cudaStream_t s);
+cudaError_t launch_col(const ColArgs<T> &a, const LaunchCfg &c, cudaStream_t s);
 template <typename T>
-cudaError_t prepare_kernels(int nt, int channels, size_t row_smem, size_t col_smem);
+cudaError_t prepare_row(const LaunchCfg &c);
+template <typename T>
+cudaError_t prepare_col(const LaunchCfg &c);
 
 // Setup kernels (setup.cu).
 struct HhatJob {          // one half-spectrum to compute
@@ -84,9 +103,10 @@ cudaError_t launch_hhat(const HhatJob *jobs_dev, int njobs, long long total, con
 cudaError_t launch_pack_mask(const ImageDesc *desc_dev, int nimg, long long total_words,
                              const long long *img_word_begin_dev, const uint8_t *mask, uint32_t *bits,
                              cudaStream_t s);
+constexpr int kMeanBlocks = 64;  // CTAs per plane in the observed-mean reduction
 template <typename T>
 cudaError_t launch_means(const ImageDesc *desc_dev, int nplanes, const int *plane_img_dev, const T *y,
-                         const uint32_t *bits, double *means, cudaStream_t s);
+                         const uint32_t *bits, double *partial, double *means, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init_fill(const ImageDesc *desc_dev, int nimg, long long total_px,
                              const long long *img_px_begin_dev, const T *y, const uint32_t *bits,

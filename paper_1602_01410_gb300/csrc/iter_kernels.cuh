@@ -44,14 +44,43 @@ __device__ __forceinline__ bool mask_bit(const uint32_t *bits, long long word0, 
   return (__ldg(&bits[word0 + (idx >> 5)]) >> (idx & 31)) & 1u;
 }
 
-__device__ __forceinline__ int find_item(const ImageDesc *desc, int n, int wi, bool row) {
+// Image of work item wi within a kernel class (its images in order of
+// increasing first work item).
+__device__ __forceinline__ int find_item(const ImageDesc *desc, const int *imgs, int n, int wi, bool row) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    int beg = row ? desc[mid].row_begin : desc[mid].col_begin;
-    if (beg <= wi) lo = mid; else hi = mid - 1;
+    const ImageDesc &D = desc[imgs[mid]];
+    if ((row ? D.row_begin : D.col_begin) <= wi) lo = mid; else hi = mid - 1;
   }
-  return lo;
+  return imgs[lo];
+}
+
+// Deterministic CTA reduction of three doubles for any block size that is a
+// multiple of 32 (at most 1024); result valid in thread 0.
+__device__ __forceinline__ void block_sum3_dyn(double &a, double &b, double &c) {
+  __shared__ double red[3][32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+    red[2][w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = b = c = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a += red[0][i];
+      b += red[1][i];
+      c += red[2][i];
+    }
+  }
 }
 
 // Deterministic CTA reduction of three doubles; result valid in thread 0.
@@ -90,7 +119,7 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
   constexpr int KMAX = 16 / C;  // owned pixels per thread (host guarantees C*Rb*N <= 16 NT)
 
   const int wi = blockIdx.x;
-  const ImageDesc *Dp = &a.desc[find_item(a.desc, a.nimg, wi, true)];
+  const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh;
   const int r0 = (wi - Dp->row_begin) * Dp->Rb;
   const int nr = min(Dp->Rb, M - r0);
@@ -250,9 +279,10 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
     double fit = 0.5 * s_fit + double(a.lambda) * s_tv;
     block_sum3<NT>(s_dd, s_dz, fit);
     if (threadIdx.x == 0) {
-      a.partials[3 * (long long)wi + 0] = s_dd;
-      a.partials[3 * (long long)wi + 1] = s_dz;
-      a.partials[3 * (long long)wi + 2] = fit;
+      double *o = a.partials + 3 * (long long)(Dp->row_pbase + wi - Dp->row_begin);
+      o[0] = s_dd;
+      o[1] = s_dz;
+      o[2] = fit;
     }
   }
 }
@@ -263,7 +293,7 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) col_pass_kernel(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wi = blockIdx.x;
-  const ImageDesc *Dp = &a.desc[find_item(a.desc, a.nimg, wi, false)];
+  const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, false)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh;
   const int local = wi - Dp->col_begin;
   const int ch = local / Dp->col_tiles, t = local - ch * Dp->col_tiles;

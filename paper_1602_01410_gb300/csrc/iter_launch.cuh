@@ -1,55 +1,86 @@
-// Launch wrappers for the iteration kernels: dispatch on CTA size (256 or
-// 512 threads) and channel count (1, or 3 for vectorial TV).
+// Launch wrappers for the iteration kernels: resolve the kernel of a
+// LaunchCfg (generic Stockham passes by CTA size and channel count, or the
+// power-of-two passes by threads per transform and channel count).
 #pragma once
 
 #include "iter_kernels.cuh"
+#include "iter_p2.cuh"
 
 namespace dcv {
 
-template <typename T, int NT, int C>
-static cudaError_t row_launch_nt(const RowArgs<T> &a, int grid, size_t smem, cudaStream_t s) {
-  row_pass_kernel<T, NT, C><<<grid, NT, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-// 512-thread CTAs exist for FP32 only (FP64 registers would spill).
+// 512-thread generic CTAs exist for FP32 only (FP64 registers would spill).
 template <typename T> constexpr int kMaxNt = sizeof(T) == 4 ? 512 : 256;
 
-template <typename T>
-cudaError_t launch_row(const RowArgs<T> &a, int grid, int nt, int channels, size_t smem, cudaStream_t s) {
-  if (grid <= 0) return cudaSuccess;
-  if (nt == 512 && kMaxNt<T> == 512)
-    return channels == 3 ? row_launch_nt<T, kMaxNt<T>, 3>(a, grid, smem, s) : row_launch_nt<T, kMaxNt<T>, 1>(a, grid, smem, s);
-  if (nt != 256) return cudaErrorInvalidValue;
-  return channels == 3 ? row_launch_nt<T, 256, 3>(a, grid, smem, s) : row_launch_nt<T, 256, 1>(a, grid, smem, s);
-}
-
-template <typename T>
-cudaError_t launch_col(const ColArgs<T> &a, int grid, int nt, size_t smem, cudaStream_t s) {
-  if (grid <= 0) return cudaSuccess;
-  if (nt == 512 && kMaxNt<T> == 512) col_pass_kernel<T, kMaxNt<T>><<<grid, kMaxNt<T>, smem, s>>>(a);
-  else if (nt == 256) col_pass_kernel<T, 256><<<grid, 256, smem, s>>>(a);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
-}
-
-// Opt in to the dynamic shared memory the plan needs (above 48 KB).
-template <typename T>
-cudaError_t prepare_kernels(int nt, int channels, size_t row_smem, size_t col_smem) {
-  cudaError_t e;
-  const int rs = (int)row_smem, cs = (int)col_smem;
-  if (nt == 512 && kMaxNt<T> == 512) {
-    constexpr int NT = kMaxNt<T>;
-    e = channels == 3 ? cudaFuncSetAttribute(row_pass_kernel<T, NT, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)
-                      : cudaFuncSetAttribute(row_pass_kernel<T, NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(col_pass_kernel<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs);
+template <typename T, int C>
+static const void *row_p2_ptr(int tt) {
+  switch (tt) {
+    case 2: return (const void *)row_pass_p2_kernel<T, 2, C>;
+    case 4: return (const void *)row_pass_p2_kernel<T, 4, C>;
+    case 8: return (const void *)row_pass_p2_kernel<T, 8, C>;
+    case 16: return (const void *)row_pass_p2_kernel<T, 16, C>;
+    case 32: return (const void *)row_pass_p2_kernel<T, 32, C>;
   }
-  if (nt != 256) return cudaErrorInvalidValue;
-  e = channels == 3 ? cudaFuncSetAttribute(row_pass_kernel<T, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs)
-                    : cudaFuncSetAttribute(row_pass_kernel<T, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(col_pass_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs);
+  return nullptr;
+}
+
+template <typename T>
+static const void *row_ptr(const LaunchCfg &c) {
+  if (c.kind == KIND_P2) return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt) : row_p2_ptr<T, 1>(c.tt);
+  if (c.nt == 512 && kMaxNt<T> == 512)
+    return c.channels == 3 ? (const void *)row_pass_kernel<T, kMaxNt<T>, 3> : (const void *)row_pass_kernel<T, kMaxNt<T>, 1>;
+  if (c.nt == 256)
+    return c.channels == 3 ? (const void *)row_pass_kernel<T, 256, 3> : (const void *)row_pass_kernel<T, 256, 1>;
+  return nullptr;
+}
+
+template <typename T>
+static const void *col_ptr(const LaunchCfg &c) {
+  if (c.kind == KIND_P2) {
+    switch (c.tt) {
+      case 2: return (const void *)col_pass_p2_kernel<T, 2>;
+      case 4: return (const void *)col_pass_p2_kernel<T, 4>;
+      case 8: return (const void *)col_pass_p2_kernel<T, 8>;
+      case 16: return (const void *)col_pass_p2_kernel<T, 16>;
+      case 32: return (const void *)col_pass_p2_kernel<T, 32>;
+    }
+    return nullptr;
+  }
+  if (c.nt == 512 && kMaxNt<T> == 512) return (const void *)col_pass_kernel<T, kMaxNt<T>>;
+  if (c.nt == 256) return (const void *)col_pass_kernel<T, 256>;
+  return nullptr;
+}
+
+template <typename A>
+static cudaError_t launch_ptr(const void *fn, const A &a, const LaunchCfg &c, cudaStream_t s) {
+  if (!fn) return cudaErrorInvalidValue;
+  if (c.grid <= 0) return cudaSuccess;
+  void *args[] = {const_cast<A *>(&a)};
+  return cudaLaunchKernel(fn, dim3(c.grid), dim3(c.nt), args, c.smem, s);
+}
+
+template <typename T>
+cudaError_t launch_row(const RowArgs<T> &a, const LaunchCfg &c, cudaStream_t s) {
+  return launch_ptr(row_ptr<T>(c), a, c, s);
+}
+
+template <typename T>
+cudaError_t launch_col(const ColArgs<T> &a, const LaunchCfg &c, cudaStream_t s) {
+  return launch_ptr(col_ptr<T>(c), a, c, s);
+}
+
+// Opt in to the dynamic shared memory a class needs (above 48 KB).
+template <typename T>
+cudaError_t prepare_row(const LaunchCfg &c) {
+  const void *fn = row_ptr<T>(c);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+}
+
+template <typename T>
+cudaError_t prepare_col(const LaunchCfg &c) {
+  const void *fn = col_ptr<T>(c);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
 }
 
 }  // namespace dcv

@@ -2,7 +2,8 @@
 #include "iter_launch.cuh"
 
 namespace dcv {
-template cudaError_t launch_row<float>(const RowArgs<float> &, int, int, int, size_t, cudaStream_t);
-template cudaError_t launch_col<float>(const ColArgs<float> &, int, int, size_t, cudaStream_t);
-template cudaError_t prepare_kernels<float>(int, int, size_t, size_t);
+template cudaError_t launch_row<float>(const RowArgs<float> &, const LaunchCfg &, cudaStream_t);
+template cudaError_t launch_col<float>(const ColArgs<float> &, const LaunchCfg &, cudaStream_t);
+template cudaError_t prepare_row<float>(const LaunchCfg &);
+template cudaError_t prepare_col<float>(const LaunchCfg &);
 }  // namespace dcv

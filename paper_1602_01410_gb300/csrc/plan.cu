@@ -43,8 +43,19 @@ int env_int(const char *name, int dflt) {
   return v ? std::atoi(v) : dflt;
 }
 
+// One kernel class of a pass: the images launched together with one kernel.
+struct Cls {
+  LaunchCfg cfg;
+  std::vector<int> imgs;
+  size_t o_imgs = 0;  // workspace offset of the image list
+};
+
 struct Layout {
   int B = 0, C = 0, K = 0, dtype = 0, nt = 256, kernel_per_image = 0;
+  std::vector<Cls> row_cls, col_cls;
+  std::map<int, int> tw2_off;
+  long long total_tw2 = 0;
+  int total_row_items = 0;
   size_t esz = 4;
   std::vector<ImageDesc> desc;
   long long total_px = 0, total_spec = 0, total_hhat = 0, total_words = 0, total_tw = 0, total_s2 = 0;
@@ -56,9 +67,34 @@ struct Layout {
   long long hhat_total_elems = 0;
   int row_grid = 0, col_grid = 0;
   size_t row_smem = 0, col_smem = 0;
-  size_t o_yt, o_d0, o_d1, o_Sa, o_Sb, o_hhat, o_bits, o_tw, o_s2, o_desc, o_jobs, o_jobbeg, o_wordbeg, o_pxbeg,
-      o_planeimg, o_means, o_partials, o_err, o_xbuf, total;
+  size_t o_yt, o_d0, o_d1, o_Sa, o_Sb, o_hhat, o_bits, o_tw, o_tw2, o_s2, o_desc, o_jobs, o_jobbeg, o_wordbeg,
+      o_pxbeg, o_planeimg, o_meanpart, o_means, o_partials, o_err, o_xbuf, o_clsimgs, total;
 };
+
+bool is_pow2_32(int L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
+
+size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz) {
+  const int groups_raw = C * (rb + 2), per_warp = 32 / tt > 0 ? 32 / tt : 1;
+  const int groups = (groups_raw + per_warp - 1) / per_warp * per_warp;
+  const size_t tiles = (size_t)groups * (32 * (tt + 1) + (tt < 16 ? tt : 0)) * 2 * esz;
+  const size_t arrays = (size_t)(C * (rb + 2) + C * rb + rb + 1) * N * esz;
+  return std::max(tiles, arrays);
+}
+
+int p2_row_threads(int C, int rb, int tt) {
+  const int groups_raw = C * (rb + 2), per_warp = 32 / tt;
+  return (groups_raw + per_warp - 1) / per_warp * per_warp * tt;
+}
+
+size_t p2_col_smem(int M, int w, int tt, size_t esz) {
+  const int per_warp = 32 / tt, groups = (2 * w + per_warp - 1) / per_warp * per_warp;
+  return (size_t)M * ((2 * w) | 1) * 2 * esz + (size_t)groups * (32 * (tt + 1) + (tt < 16 ? tt : 0)) * 2 * esz;
+}
+
+int p2_col_threads(int w, int tt) {
+  const int per_warp = 32 / tt;
+  return (2 * w + per_warp - 1) / per_warp * per_warp * tt;
+}
 
 // Row-block height and column-tile width for one image under CTA size nt.
 bool fit_image(int M, int N, int C, int nt, size_t esz, int rb_pref, int w_pref, int *Rb, int *W) {
@@ -110,9 +146,31 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     rows_total += M;
     cols_total += (long long)L.C * (N / 2 + 1);
   }
-  const int rb_pref = env_int("DECONV_ROW_BLOCK", (int)std::max<long long>(2, (rows_total + kTargetCtas - 1) / kTargetCtas));
-  const int w_pref = env_int("DECONV_COL_TILE", (int)std::max<long long>(1, (cols_total + kTargetCtas - 1) / kTargetCtas));
-  // CTA size: 256 threads when every image fits, else 512 (FP32 only).
+  const int maxthr = L.esz == 4 ? 512 : 256;
+  const bool allow_p2 = env_int("DECONV_GENERIC", 0) == 0;
+  // Kernel class of every image and pass: the power-of-two passes for lengths
+  // 64..1024 that fit, the generic Stockham passes otherwise.
+  std::vector<int> row_tt(L.B, 0), col_tt(L.B, 0);
+  long long g_rows = 0, g_cols = 0, p2_rows[33] = {0}, p2_cols[33] = {0};
+  for (int j = 0; j < L.B; ++j) {
+    const int M = d->rows[j], N = d->cols[j];
+    if (allow_p2 && is_pow2_32(N) && N / 32 * L.C * 3 <= maxthr && p2_row_smem(L.C, N, 1, N / 32, L.esz) <= kMaxSmem) {
+      row_tt[j] = N / 32;
+      p2_rows[N / 32] += M;
+    } else {
+      g_rows += M;
+    }
+    if (allow_p2 && is_pow2_32(M) && p2_col_smem(M, 1, M / 32, L.esz) <= kMaxSmem) {
+      col_tt[j] = M / 32;
+      p2_cols[M / 32] += (long long)L.C * (N / 2 + 1);
+    } else {
+      g_cols += (long long)L.C * (N / 2 + 1);
+    }
+  }
+  const int target = env_int("DECONV_TARGET_CTAS", kTargetCtas);
+  const int rb_pref = env_int("DECONV_ROW_BLOCK", (int)std::max<long long>(2, (g_rows + target - 1) / target));
+  const int w_pref = env_int("DECONV_COL_TILE", (int)std::max<long long>(1, (g_cols + target - 1) / target));
+  // Generic CTA size: 256 threads when every generic image fits, else 512 (FP32 only).
   int nt_req = env_int("DECONV_NT", 0);
   std::vector<int> cand = nt_req ? std::vector<int>{nt_req} : std::vector<int>{256, 512};
   bool ok = false;
@@ -120,6 +178,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     if (nt != 256 && !(nt == 512 && L.esz == 4)) continue;
     bool all = true;
     for (int j = 0; j < L.B && all; ++j) {
+      if (row_tt[j] && col_tt[j]) continue;
       int rb, w;
       all = fit_image(d->rows[j], d->cols[j], L.C, nt, L.esz, rb_pref, w_pref, &rb, &w);
     }
@@ -130,6 +189,42 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     }
   }
   if (!ok) return DECONV_EUNSUPPORTED;
+  // Class parameters: rows per CTA / columns per CTA aiming at `target` CTAs.
+  int p2_rb[33] = {0}, p2_w[33] = {0};
+  for (int tt = 2; tt <= 32; tt *= 2) {
+    const int N = 32 * tt;
+    if (p2_rows[tt]) {
+      int rb = (int)std::max<long long>(1, (p2_rows[tt] + target - 1) / target);
+      rb = env_int("DECONV_P2_ROW_BLOCK", rb);
+      while (rb > 1 && (p2_row_threads(L.C, rb, tt) > maxthr || p2_row_smem(L.C, N, rb, tt, L.esz) > kMaxSmem)) --rb;
+      p2_rb[tt] = rb;
+    }
+  }
+  int p2w_all = 1;
+  {
+    long long tot = 0;
+    for (int tt = 2; tt <= 32; tt *= 2) tot += p2_cols[tt];
+    p2w_all = (int)std::max<long long>(1, (tot + target - 1) / target);
+    p2w_all = env_int("DECONV_P2_COL_TILE", p2w_all);
+  }
+  for (int tt = 2; tt <= 32; tt *= 2) {
+    if (!p2_cols[tt]) continue;
+    int w = std::min(p2w_all, 16);
+    while (w > 1 && (p2_col_threads(w, tt) > maxthr || p2_col_smem(32 * tt, w, tt, L.esz) > kMaxSmem)) --w;
+    p2_w[tt] = w;
+  }
+
+  // Class lists (generic first, then by threads per transform).
+  auto class_index = [](std::vector<Cls> &v, int kind, int tt) {
+    for (size_t k = 0; k < v.size(); ++k)
+      if (v[k].cfg.kind == kind && v[k].cfg.tt == tt) return (int)k;
+    Cls c;
+    std::memset(&c.cfg, 0, sizeof(c.cfg));
+    c.cfg.kind = kind;
+    c.cfg.tt = tt;
+    v.push_back(c);
+    return (int)v.size() - 1;
+  };
 
   std::map<std::tuple<int, int, int>, long long> hh;  // (M, N, kernel) -> offset
   L.desc.resize(L.B);
@@ -140,13 +235,40 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     D.N = d->cols[j];
     D.Nh = D.N / 2 + 1;
     D.C = L.C;
-    fit_image(D.M, D.N, L.C, L.nt, L.esz, rb_pref, w_pref, &D.Rb, &D.W);
+    int grb = 0, gw = 0;
+    if (!(row_tt[j] && col_tt[j])) fit_image(D.M, D.N, L.C, L.nt, L.esz, rb_pref, w_pref, &grb, &gw);
+    D.Rb = row_tt[j] ? p2_rb[row_tt[j]] : grb;
+    D.W = col_tt[j] ? p2_w[col_tt[j]] : gw;
     D.row_blocks = (D.M + D.Rb - 1) / D.Rb;
     D.col_tiles = (D.Nh + D.W - 1) / D.W;
-    D.row_begin = L.row_grid;
-    D.col_begin = L.col_grid;
+    Cls &rc = L.row_cls[class_index(L.row_cls, row_tt[j] ? KIND_P2 : KIND_GENERIC, row_tt[j])];
+    Cls &cc = L.col_cls[class_index(L.col_cls, col_tt[j] ? KIND_P2 : KIND_GENERIC, col_tt[j])];
+    D.row_begin = rc.cfg.grid;
+    D.col_begin = cc.cfg.grid;
+    rc.cfg.grid += D.row_blocks;
+    cc.cfg.grid += L.C * D.col_tiles;
+    rc.imgs.push_back(j);
+    cc.imgs.push_back(j);
+    D.row_pbase = L.total_row_items;
+    L.total_row_items += D.row_blocks;
     L.row_grid += D.row_blocks;
     L.col_grid += L.C * D.col_tiles;
+    if (row_tt[j]) {
+      rc.cfg.nt = p2_row_threads(L.C, D.Rb, row_tt[j]);
+      rc.cfg.smem = std::max(rc.cfg.smem, p2_row_smem(L.C, D.N, D.Rb, row_tt[j], L.esz));
+    } else {
+      rc.cfg.nt = L.nt;
+      const size_t ldr = (size_t)((L.C * (D.Rb + 2)) | 1);
+      rc.cfg.smem = std::max(rc.cfg.smem, (size_t)D.N * ldr * 2 * L.esz + (size_t)(D.Rb + 1) * D.N * L.esz);
+    }
+    if (col_tt[j]) {
+      cc.cfg.nt = p2_col_threads(D.W, col_tt[j]);
+      cc.cfg.smem = std::max(cc.cfg.smem, p2_col_smem(D.M, D.W, col_tt[j], L.esz));
+    } else {
+      cc.cfg.nt = L.nt;
+      cc.cfg.smem = std::max(cc.cfg.smem, (size_t)D.M * (size_t)((2 * D.W) | 1) * 2 * L.esz);
+    }
+    rc.cfg.channels = cc.cfg.channels = L.C;
     D.px = L.total_px;
     L.img_px_begin.push_back(L.total_px);
     L.total_px += (long long)L.C * D.M * D.N;
@@ -186,12 +308,20 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     D.tw_col = L.tw_off[D.M];
     D.s2_row = L.s2_off[D.N];
     D.s2_col = L.s2_off[D.M];
+    D.tw2_row = D.tw2_col = -1;
+    for (int len : {D.M, D.N})
+      if (is_pow2_32(len) && !L.tw2_off.count(len)) {
+        L.tw2_off[len] = (int)L.total_tw2;
+        L.total_tw2 += len;
+      }
+    if (L.tw2_off.count(D.N)) D.tw2_row = L.tw2_off[D.N];
+    if (L.tw2_off.count(D.M)) D.tw2_col = L.tw2_off[D.M];
     factor235(D.N, &D.sched_row);
     factor235(D.M, &D.sched_col);
-    const size_t ldr = (size_t)((L.C * (D.Rb + 2)) | 1), ldc = (size_t)((2 * D.W) | 1);
-    L.row_smem = std::max(L.row_smem, (size_t)D.N * ldr * 2 * L.esz + (size_t)(D.Rb + 1) * D.N * L.esz);
-    L.col_smem = std::max(L.col_smem, (size_t)D.M * ldc * 2 * L.esz);
   }
+  for (auto &c : L.row_cls) L.row_smem = std::max(L.row_smem, c.cfg.smem);
+  for (auto &c : L.col_cls) L.col_smem = std::max(L.col_smem, c.cfg.smem);
+  if (L.row_smem > kMaxSmem || L.col_smem > kMaxSmem) return DECONV_EUNSUPPORTED;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t r = o;
@@ -206,6 +336,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   L.o_hhat = take(L.total_hhat * 2 * L.esz);
   L.o_bits = take(L.total_words * 4);
   L.o_tw = take(L.total_tw * 2 * L.esz);
+  L.o_tw2 = take(L.total_tw2 * 2 * L.esz);
   L.o_s2 = take(L.total_s2 * L.esz);
   L.o_desc = take(L.desc.size() * sizeof(ImageDesc));
   L.o_jobs = take(L.jobs.size() * sizeof(HhatJob));
@@ -213,10 +344,13 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   L.o_wordbeg = take(L.img_word_begin.size() * sizeof(long long));
   L.o_pxbeg = take(L.img_px_begin.size() * sizeof(long long));
   L.o_planeimg = take(L.plane_img.size() * sizeof(int));
+  L.o_meanpart = take(L.plane_img.size() / 2 * kMeanBlocks * 2 * sizeof(double));
   L.o_means = take(L.plane_img.size() / 2 * sizeof(double));
-  L.o_partials = take((size_t)L.row_grid * 3 * sizeof(double));
+  L.o_partials = take((size_t)L.total_row_items * 3 * sizeof(double));
   L.o_err = take(sizeof(int));
   L.o_xbuf = take(L.total_px * L.esz);
+  for (auto *v : {&L.row_cls, &L.col_cls})
+    for (auto &c : *v) c.o_imgs = take(c.imgs.size() * sizeof(int));
   L.total = o;
   return DECONV_OK;
 }
@@ -245,11 +379,13 @@ namespace {
   } while (0)
 
 template <typename T>
-RowArgs<T> row_args(const deconv_plan_s *p, int mode, const T *d_in, T *d_out, T *x_out, double *partials) {
+RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_in, T *d_out, T *x_out,
+                    double *partials) {
   const Layout &L = p->L;
   RowArgs<T> a;
   a.desc = p->at<ImageDesc>(L.o_desc);
-  a.nimg = L.B;
+  a.cls_imgs = p->at<int>(c.o_imgs);
+  a.nimg = (int)c.imgs.size();
   a.mode = mode;
   a.yt = p->at<T>(L.o_yt);
   a.d_in = d_in;
@@ -258,6 +394,7 @@ RowArgs<T> row_args(const deconv_plan_s *p, int mode, const T *d_in, T *d_out, T
   a.S_out = p->at<cpair<T>>(L.o_Sa);
   a.mask = p->at<uint32_t>(L.o_bits);
   a.tw = p->ws + L.o_tw;
+  a.tw2 = p->ws + L.o_tw2;
   a.mu = (T)p->mu;
   a.tau = (T)(p->lambda / p->mu);
   a.relax = (T)p->relax;
@@ -269,15 +406,17 @@ RowArgs<T> row_args(const deconv_plan_s *p, int mode, const T *d_in, T *d_out, T
 }
 
 template <typename T>
-ColArgs<T> col_args(const deconv_plan_s *p) {
+ColArgs<T> col_args(const deconv_plan_s *p, const Cls &c) {
   const Layout &L = p->L;
   ColArgs<T> a;
   a.desc = p->at<ImageDesc>(L.o_desc);
-  a.nimg = L.B;
+  a.cls_imgs = p->at<int>(c.o_imgs);
+  a.nimg = (int)c.imgs.size();
   a.S_in = p->at<cpair<T>>(L.o_Sa);
   a.S_out = p->at<cpair<T>>(L.o_Sb);
   a.hhat = p->ws + L.o_hhat;
   a.tw = p->ws + L.o_tw;
+  a.tw2 = p->ws + L.o_tw2;
   a.s2 = p->at<T>(L.o_s2);
   a.mu = (T)p->mu;
   a.err = p->at<int>(L.o_err);
@@ -290,12 +429,30 @@ template <typename T> T *dbuf(deconv_plan_s *p, int which) {
 
 // One iteration (column pass then row pass), d ping-pong by plan parity.
 template <typename T>
+cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s) {
+  for (const Cls &c : p->L.col_cls) {
+    cudaError_t e = launch_col<T>(col_args<T>(p, c), c.cfg, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, T *d_out, T *x_out,
+                     double *partials) {
+  for (const Cls &c : p->L.row_cls) {
+    cudaError_t e = launch_row<T>(row_args<T>(p, c, mode, d_in, d_out, x_out, partials), c.cfg, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
 deconv_status iterate(deconv_plan_s *p, cudaStream_t s, T *x_out, double *stats, int iters, int it) {
   const Layout &L = p->L;
-  CK(launch_col<T>(col_args<T>(p), L.col_grid, L.nt, L.col_smem, s));
+  CK(col_pass<T>(p, s));
   double *partials = stats ? p->at<double>(L.o_partials) : nullptr;
-  CK(launch_row<T>(row_args<T>(p, ROW_ITER, dbuf<T>(p, p->parity), dbuf<T>(p, p->parity ^ 1), x_out, partials),
-                   L.row_grid, L.nt, L.C, L.row_smem, s));
+  CK(row_pass<T>(p, s, ROW_ITER, dbuf<T>(p, p->parity), dbuf<T>(p, p->parity ^ 1), x_out, partials));
   p->parity ^= 1;
   if (stats) CK(launch_stats_reduce(p->at<ImageDesc>(L.o_desc), L.B, partials, stats, iters, it, p->at<int>(L.o_err), s));
   return DECONV_OK;
@@ -307,12 +464,11 @@ deconv_status init_state(deconv_plan_s *p, const T *y, T *x_out) {
   cudaStream_t s = p->stream;
   const ImageDesc *desc = p->at<ImageDesc>(L.o_desc);
   CK(launch_means<T>(desc, (int)L.plane_img.size() / 2, p->at<int>(L.o_planeimg), y, p->at<uint32_t>(L.o_bits),
-                     p->at<double>(L.o_means), s));
+                     p->at<double>(L.o_meanpart), p->at<double>(L.o_means), s));
   CK(launch_init_fill<T>(desc, L.B, L.total_px, p->at<long long>(L.o_pxbeg), y, p->at<uint32_t>(L.o_bits),
                          p->at<double>(L.o_means), L.K, p->at<T>(L.o_yt), s));
   p->parity = 0;
-  CK(launch_row<T>(row_args<T>(p, ROW_INIT, nullptr, dbuf<T>(p, 0), x_out, nullptr), L.row_grid, L.nt, L.C,
-                   L.row_smem, s));
+  CK(row_pass<T>(p, s, ROW_INIT, nullptr, dbuf<T>(p, 0), x_out, nullptr));
   p->have_state = true;
   return DECONV_OK;
 }
@@ -396,7 +552,23 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
       s2[o2 + k] = (T)(4.0 * sn * sn);
     }
   }
+  // [k1][t] tables of the power-of-two transforms: tw2[k1 TT + t] = exp(-2 pi i t k1 / L).
+  std::vector<T> tw2(2 * L.total_tw2);
+  for (const auto &kv : L.tw2_off) {
+    const int len = kv.first, o = kv.second, tt = len / 32;
+    for (int k1 = 0; k1 < 32; ++k1)
+      for (int t = 0; t < tt; ++t) {
+        const double a = 2.0 * M_PI * (double)(k1 * t) / (double)len;
+        tw2[2 * (o + k1 * tt + t)] = (T)std::cos(a);
+        tw2[2 * (o + k1 * tt + t) + 1] = (T)(-std::sin(a));
+      }
+  }
   CK(cudaMemcpyAsync(p->ws + L.o_tw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  if (!tw2.empty())
+    CK(cudaMemcpyAsync(p->ws + L.o_tw2, tw2.data(), tw2.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  for (const auto *v : {&L.row_cls, &L.col_cls})
+    for (const Cls &c : *v)
+      CK(cudaMemcpyAsync(p->ws + c.o_imgs, c.imgs.data(), c.imgs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(p->ws + L.o_s2, s2.data(), s2.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(p->ws + L.o_desc, L.desc.data(), L.desc.size() * sizeof(ImageDesc), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(p->ws + L.o_jobs, L.jobs.data(), L.jobs.size() * sizeof(HhatJob), cudaMemcpyHostToDevice, s));
@@ -415,7 +587,8 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
                     p->ws + L.o_hhat, p->at<long long>(L.o_jobbeg), s));
   CK(launch_pack_mask(p->at<ImageDesc>(L.o_desc), L.B, L.total_words, p->at<long long>(L.o_wordbeg), mask,
                       p->at<uint32_t>(L.o_bits), s));
-  CK(prepare_kernels<T>(L.nt, L.C, L.row_smem, L.col_smem));
+  for (const Cls &c : L.row_cls) CK(prepare_row<T>(c.cfg));
+  for (const Cls &c : L.col_cls) CK(prepare_col<T>(c.cfg));
   CK(cudaStreamSynchronize(s));
   return DECONV_OK;
 }
@@ -509,29 +682,20 @@ deconv_status deconv_solve_host(deconv_plan p, const void *y_host, void *x_host,
 
 deconv_status deconv_profile_passes(deconv_plan p, int32_t iters, float *ms_host) {
   if (!p || iters < 1 || !ms_host || !p->have_state) return DECONV_EINVAL;
-  const Layout &L = p->L;
   std::vector<cudaEvent_t> ev(4 * (size_t)iters);
   for (auto &e : ev) CK(cudaEventCreate(&e));
   deconv_status st = DECONV_OK;
   for (int it = 0; it < iters && st == DECONV_OK; ++it) {
     cudaError_t e = cudaEventRecord(ev[4 * it], p->stream);
-    if (L.dtype == DECONV_F32) {
-      if (e == cudaSuccess) e = launch_col<float>(col_args<float>(p), L.col_grid, L.nt, L.col_smem, p->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 1], p->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 2], p->stream);
-      if (e == cudaSuccess)
-        e = launch_row<float>(row_args<float>(p, ROW_ITER, dbuf<float>(p, p->parity), dbuf<float>(p, p->parity ^ 1),
-                                              nullptr, nullptr),
-                              L.row_grid, L.nt, L.C, L.row_smem, p->stream);
-    } else {
-      if (e == cudaSuccess) e = launch_col<double>(col_args<double>(p), L.col_grid, L.nt, L.col_smem, p->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 1], p->stream);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 2], p->stream);
-      if (e == cudaSuccess)
-        e = launch_row<double>(row_args<double>(p, ROW_ITER, dbuf<double>(p, p->parity),
-                                                dbuf<double>(p, p->parity ^ 1), nullptr, nullptr),
-                               L.row_grid, L.nt, L.C, L.row_smem, p->stream);
-    }
+    const bool f32 = p->L.dtype == DECONV_F32;
+    if (e == cudaSuccess) e = f32 ? col_pass<float>(p, p->stream) : col_pass<double>(p, p->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 1], p->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 2], p->stream);
+    if (e == cudaSuccess)
+      e = f32 ? row_pass<float>(p, p->stream, ROW_ITER, dbuf<float>(p, p->parity), dbuf<float>(p, p->parity ^ 1),
+                                nullptr, nullptr)
+              : row_pass<double>(p, p->stream, ROW_ITER, dbuf<double>(p, p->parity),
+                                 dbuf<double>(p, p->parity ^ 1), nullptr, nullptr);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4 * it + 3], p->stream);
     if (e != cudaSuccess) st = DECONV_ECUDA;
     p->parity ^= 1;

@@ -89,24 +89,27 @@ cudaError_t launch_pack_mask(const ImageDesc *desc_dev, int nimg, long long tota
   return cudaGetLastError();
 }
 
-// Mean of the observed values of each (image, channel) plane, in double,
-// reduced in a fixed order (one CTA per plane).
+// Mean of the observed values of each (image, channel) plane, in double.
+// kMeanBlocks CTAs per plane write partial (sum, count) pairs; one CTA per
+// plane then adds them in a fixed order.
 template <typename T>
-__global__ void means_kernel(const ImageDesc *desc, const int *plane_img, const T *y, const uint32_t *bits,
-                             double *means) {
-  const int plane = blockIdx.x;
+__global__ void means_partial_kernel(const ImageDesc *desc, const int *plane_img, const T *y, const uint32_t *bits,
+                                     double *partial) {
+  const int plane = blockIdx.x / kMeanBlocks, part = blockIdx.x % kMeanBlocks;
   const int img = plane_img[2 * plane], ch = plane_img[2 * plane + 1];
   const ImageDesc &D = desc[img];
   const long long P = (long long)D.M * D.N;
   const T *src = y + D.px + ch * P;
   const long long w0 = D.mask + ch * D.mask_plane;
-  double s = 0.0, c = 0.0;
-  for (long long p = threadIdx.x; p < P; p += blockDim.x)
+  double s = 0.0;
+  long long c = 0;
+  for (long long p = (long long)part * blockDim.x + threadIdx.x; p < P; p += (long long)kMeanBlocks * blockDim.x)
     if ((bits[w0 + (p >> 5)] >> (p & 31)) & 1u) {
       s += (double)src[p];
-      c += 1.0;
+      ++c;
     }
-  __shared__ double rs[256], rc[256];
+  __shared__ double rs[256];
+  __shared__ long long rc[256];
   rs[threadIdx.x] = s;
   rc[threadIdx.x] = c;
   __syncthreads();
@@ -117,19 +120,36 @@ __global__ void means_kernel(const ImageDesc *desc, const int *plane_img, const 
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) means[plane] = rc[0] > 0 ? rs[0] / rc[0] : 0.0;
+  if (threadIdx.x == 0) {
+    partial[2 * (long long)blockIdx.x] = rs[0];
+    partial[2 * (long long)blockIdx.x + 1] = (double)rc[0];
+  }
+}
+
+__global__ void means_final_kernel(const double *partial, int nplanes, double *means) {
+  const int plane = blockIdx.x * blockDim.x + threadIdx.x;
+  if (plane >= nplanes) return;
+  double s = 0.0, c = 0.0;
+  for (int k = 0; k < kMeanBlocks; ++k) {
+    s += partial[2 * ((long long)plane * kMeanBlocks + k)];
+    c += partial[2 * ((long long)plane * kMeanBlocks + k) + 1];
+  }
+  means[plane] = c > 0 ? s / c : 0.0;
 }
 
 template <typename T>
 cudaError_t launch_means(const ImageDesc *desc_dev, int nplanes, const int *plane_img_dev, const T *y,
-                         const uint32_t *bits, double *means, cudaStream_t s) {
-  means_kernel<T><<<nplanes, 256, 0, s>>>(desc_dev, plane_img_dev, y, bits, means);
+                         const uint32_t *bits, double *partial, double *means, cudaStream_t s) {
+  means_partial_kernel<T><<<nplanes * kMeanBlocks, 256, 0, s>>>(desc_dev, plane_img_dev, y, bits, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  means_final_kernel<<<(nplanes + 127) / 128, 128, 0, s>>>(partial, nplanes, means);
   return cudaGetLastError();
 }
 template cudaError_t launch_means<float>(const ImageDesc *, int, const int *, const float *, const uint32_t *,
-                                         double *, cudaStream_t);
-template cudaError_t launch_means<double>(const ImageDesc *, int, const int *, const double *,
-                                          const uint32_t *, double *, cudaStream_t);
+                                         double *, double *, cudaStream_t);
+template cudaError_t launch_means<double>(const ImageDesc *, int, const int *, const double *, const uint32_t *,
+                                          double *, double *, cudaStream_t);
 
 // y~0 (Sec. III-B: the observed image padded by repeating its border
 // pixels).  Observed pixels take y.  An unobserved pixel of the boundary band
@@ -193,7 +213,7 @@ __global__ void stats_reduce_kernel(const ImageDesc *desc, const double *partial
   __shared__ double r[3][128];
   double a = 0.0, b = 0.0, c = 0.0;
   for (int q = threadIdx.x; q < D.row_blocks; q += blockDim.x) {
-    const long long o = 3LL * (D.row_begin + q);
+    const long long o = 3LL * (D.row_pbase + q);
     a += partials[o];
     b += partials[o + 1];
     c += partials[o + 2];

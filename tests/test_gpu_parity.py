@@ -152,3 +152,30 @@ def test_zero_dc_gain_rejected():
     with pytest.raises(pkg.DeconvError) as e:
         pkg.Plan([(32, 32)], h, mask, 1e-3, 1e-2)
     assert e.value.status == pkg.DECONV_EINVAL
+
+
+def test_pow2_passes_every_group_size():
+    # rows and columns of 64 .. 1024: every threads-per-transform variant
+    prob = inputs.random_problem(23, [(64, 1024), (128, 512), (256, 256), (512, 128), (1024, 64)], 5,
+                                 mask_kind="random", frac=0.3, iters=1)
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    for a, b in zip(xg, xo):
+        assert rel_l2([a], [b]) <= 1e-5
+
+
+def test_pow2_passes_vectorial_tv_and_stats():
+    prob = inputs.random_problem(24, [(64, 64), (128, 256)], 5, mask_kind="bayer", channels=3, iters=3)
+    xg, sg, _ = gpu_solve(prob, stats=True)
+    xo, so = oracle_solve(prob, stats=True)
+    for j in range(2):
+        assert rel_l2([xg[j]], [xo[j]]) <= 3e-5
+        assert np.allclose(sg[j][:, 2], so[j][:, 3], rtol=1e-4)
+
+
+def test_generic_passes_on_pow2_sizes(monkeypatch):
+    monkeypatch.setenv("DECONV_GENERIC", "1")
+    prob = inputs.random_problem(25, [(128, 256), (64, 64)], 7, mask_kind="random", frac=0.4, iters=1)
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    assert rel_l2(xg, xo) <= 1e-5
