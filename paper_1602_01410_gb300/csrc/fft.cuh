@@ -201,6 +201,7 @@ template <typename T, int SIGN> struct Dft<T, 32, SIGN> {
 template <int TT> __host__ __device__ constexpr int p2_group_stride() {
   return 32 * (TT + 1) + (TT < 16 ? TT : 0);
 }
+__host__ __device__ constexpr int p2_group_stride_h(int tt) { return 32 * (tt + 1) + (tt < 16 ? tt : 0); }
 
 // Position index m of register r after the transform (see above).
 template <int TT> __device__ __forceinline__ constexpr int p2_slot(int r) {

@@ -52,6 +52,7 @@ template <typename T> struct RowArgs {
   const void *tw2;        // [k1][t] twiddle tables of the power-of-two transforms (cx<T>)
   T mu, tau, relax, lambda;
   T *x_out;               // nullable: x^{i+1} for owned rows
+  T *xbuf;                // plan's x buffer (power-of-two row passes: written by the inverse half)
   double *partials;       // nullable: per work item [3] = sum dd^2, dz^2, J
   int *err;
 };

@@ -163,7 +163,10 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
 
   // 2. z-update, a = D x + d, g, d^{i+1} (rows r0-1 .. r1-1; updates only on owned rows).
   const T tau = a.tau, tau2 = a.tau * a.tau, relax = a.relax;
-  double s_dd = 0.0, s_dz = 0.0, s_fit = 0.0, s_tv = 0.0;
+  // Statistics: per-thread partials in the working precision, only when
+  // requested (the FP64 pipe is slow); FP64 for the CTA and plan reductions.
+  const bool stats = a.partials != nullptr;
+  T s_dd = T(0), s_dz = T(0), s_fit = T(0), s_tv = T(0);
   for (int e = threadIdx.x; e < (nr + 1) * N; e += NT) {
     const int h = e / N, n = e - h * N, i = wrapi(r0 - 1 + h, M);
     const int n1 = (n + 1 == N) ? 0 : n + 1;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
         const long long o = px0 + ch * P + (long long)i * N + n;
         const T dnh = (T(1) - g) * ah[ch], dnv = (T(1) - g) * av[ch];
         dout[o] = mk<T>(dnh, dnv);
-        s_dd += double(dnh - dh0[ch]) * double(dnh - dh0[ch]) + double(dnv - dv0[ch]) * double(dnv - dv0[ch]);
+        if (stats) s_dd += (dnh - dh0[ch]) * (dnh - dh0[ch]) + (dnv - dv0[ch]) * (dnv - dv0[ch]);
         const T yo = a.yt[o];
         T yn = yo;
         if (!init) {
@@ -199,15 +202,15 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
           if (!mask_bit(a.mask, mword + ch * mplane, (long long)i * N + n)) {
             yn = relax * t - (relax - T(1)) * yo;
             a.yt[o] = yn;
-            s_dz += double(yn - yo) * double(yn - yo);
-          } else {
-            s_fit += double(yo - t) * double(yo - t);
+            if (stats) s_dz += (yn - yo) * (yn - yo);
+          } else if (stats) {
+            s_fit += (yo - t) * (yo - t);
           }
         }
         if (a.x_out) a.x_out[o] = bufr[2 * (n * ld + sg)];
         bufr[2 * (n * ld + sg) + 1] = yn;  // second slot now holds y~^{i+1}
       }
-      s_tv += sqrt(double(tv));
+      if (stats) s_tv += sqrt(tv);
     }
   }
   __syncthreads();
@@ -275,13 +278,13 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
     }
   }
 
-  if (a.partials) {
-    double fit = 0.5 * s_fit + double(a.lambda) * s_tv;
-    block_sum3<NT>(s_dd, s_dz, fit);
+  if (stats) {
+    double fit = 0.5 * double(s_fit) + double(a.lambda) * double(s_tv), dd = double(s_dd), dz = double(s_dz);
+    block_sum3<NT>(dd, dz, fit);
     if (threadIdx.x == 0) {
       double *o = a.partials + 3 * (long long)(Dp->row_pbase + wi - Dp->row_begin);
-      o[0] = s_dd;
-      o[1] = s_dz;
+      o[0] = dd;
+      o[1] = dz;
       o[2] = fit;
     }
   }

@@ -11,21 +11,22 @@ namespace dcv {
 // 512-thread generic CTAs exist for FP32 only (FP64 registers would spill).
 template <typename T> constexpr int kMaxNt = sizeof(T) == 4 ? 512 : 256;
 
+// Power-of-two row pass: half 0 = inverse (R1), half 1 = forward (R2).
 template <typename T, int C>
-static const void *row_p2_ptr(int tt) {
+static const void *row_p2_ptr(int tt, int half) {
   switch (tt) {
-    case 2: return (const void *)row_pass_p2_kernel<T, 2, C>;
-    case 4: return (const void *)row_pass_p2_kernel<T, 4, C>;
-    case 8: return (const void *)row_pass_p2_kernel<T, 8, C>;
-    case 16: return (const void *)row_pass_p2_kernel<T, 16, C>;
-    case 32: return (const void *)row_pass_p2_kernel<T, 32, C>;
+    case 2: return half ? (const void *)row_fwd_p2_kernel<T, 2, C> : (const void *)row_inv_p2_kernel<T, 2, C>;
+    case 4: return half ? (const void *)row_fwd_p2_kernel<T, 4, C> : (const void *)row_inv_p2_kernel<T, 4, C>;
+    case 8: return half ? (const void *)row_fwd_p2_kernel<T, 8, C> : (const void *)row_inv_p2_kernel<T, 8, C>;
+    case 16: return half ? (const void *)row_fwd_p2_kernel<T, 16, C> : (const void *)row_inv_p2_kernel<T, 16, C>;
+    case 32: return half ? (const void *)row_fwd_p2_kernel<T, 32, C> : (const void *)row_inv_p2_kernel<T, 32, C>;
   }
   return nullptr;
 }
 
 template <typename T>
-static const void *row_ptr(const LaunchCfg &c) {
-  if (c.kind == KIND_P2) return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt) : row_p2_ptr<T, 1>(c.tt);
+static const void *row_ptr(const LaunchCfg &c, int half = 0) {
+  if (c.kind == KIND_P2) return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt, half) : row_p2_ptr<T, 1>(c.tt, half);
   if (c.nt == 512 && kMaxNt<T> == 512)
     return c.channels == 3 ? (const void *)row_pass_kernel<T, kMaxNt<T>, 3> : (const void *)row_pass_kernel<T, kMaxNt<T>, 1>;
   if (c.nt == 256)
@@ -60,7 +61,9 @@ static cudaError_t launch_ptr(const void *fn, const A &a, const LaunchCfg &c, cu
 
 template <typename T>
 cudaError_t launch_row(const RowArgs<T> &a, const LaunchCfg &c, cudaStream_t s) {
-  return launch_ptr(row_ptr<T>(c), a, c, s);
+  cudaError_t e = launch_ptr(row_ptr<T>(c, 0), a, c, s);
+  if (e != cudaSuccess || c.kind != KIND_P2) return e;
+  return launch_ptr(row_ptr<T>(c, 1), a, c, s);
 }
 
 template <typename T>
@@ -71,9 +74,13 @@ cudaError_t launch_col(const ColArgs<T> &a, const LaunchCfg &c, cudaStream_t s) 
 // Opt in to the dynamic shared memory a class needs (above 48 KB).
 template <typename T>
 cudaError_t prepare_row(const LaunchCfg &c) {
-  const void *fn = row_ptr<T>(c);
-  if (!fn) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  for (int half = 0; half < (c.kind == KIND_P2 ? 2 : 1); ++half) {
+    const void *fn = row_ptr<T>(c, half);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>

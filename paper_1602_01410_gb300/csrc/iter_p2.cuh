@@ -24,161 +24,246 @@ __device__ __forceinline__ unsigned group_mask(int TT) {
   return ((1u << TT) - 1u) << base;
 }
 
-// ------------------------------------------------------------------ row ---
+// Asynchronous global -> shared copies (sm_80+ cp.async), B = 4, 8 or 16 bytes.
+template <int B>
+__device__ __forceinline__ void cp_async(void *sdst, const void *gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Cooperative asynchronous copy of n elements (4, 8 or 16 bytes each) from
+// global to shared memory: 16-byte chunks when both ends are 16-byte aligned.
+template <typename E>
+__device__ __forceinline__ void copy_async(E *sdst, const E *gsrc, int n, int tid, int nthr) {
+  if (sizeof(E) < 16 && (((uintptr_t)gsrc | (uintptr_t)sdst) & 15) == 0 && (n * (int)sizeof(E)) % 16 == 0) {
+    const int n16 = n * (int)sizeof(E) / 16;
+    for (int k = tid; k < n16; k += nthr)
+      cp_async<16>(reinterpret_cast<char *>(sdst) + 16 * k, reinterpret_cast<const char *>(gsrc) + 16 * k);
+  } else {
+    for (int k = tid; k < n; k += nthr) cp_async<sizeof(E)>(sdst + k, gsrc + k);
+  }
+}
+
+// Register r of fft_p2's output holds position q + TT * p2_slot(r); the
+// register holding position q + TT * m is p2_unslot(m).
+template <int TT> __device__ __forceinline__ constexpr int p2_unslot(int m) {
+  return (m % (32 / TT)) * TT + m / (32 / TT);
+}
+
+// ----------------------------------------------------------- row (R1) ---
+// Inverse half of the row pass: one group of TT threads per (channel, row),
+// Rb rows per CTA, no halo.  Inverse row DFT of X + i HX -> x, T~x; z-update
+// of y~; x to the plan's x buffer (read by R2) and optionally to x_out.
+// The CTA's y~ rows and mask words are staged into shared memory
+// asynchronously while the transforms run.  Statistics: ||dz||^2 and the
+// data-fit half of the objective.
+// Shared memory: [transpose tiles][y~ rows C x Rb][mask words C x Rb].
 template <typename T, int TT, int C>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_pass_p2_kernel(RowArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = p2_group_stride<TT>();
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
-  const int M = Dp->M, N = Dp->N, Nh = Dp->Nh;
+  const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb, wpr = N / 32;
   const int blk = wi - Dp->row_begin;
-  const int r0 = blk * Dp->Rb;
-  const int nr = min(Dp->Rb, M - r0), nh = nr + 2;
-  const long long P = (long long)M * N, px0 = Dp->px, spec0 = Dp->spec;
-  const long long mword = Dp->mask, mplane = Dp->mask_plane;
-  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
-  const cx<T> *din = reinterpret_cast<const cx<T> *>(a.d_in);
-  cx<T> *dout = reinterpret_cast<cx<T> *>(a.d_out);
-  const bool init = a.mode == ROW_INIT;
-
+  const int r0 = blk * Rb, nr = min(Rb, M - r0);
+  const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
-  const unsigned gm = group_mask(TT);
-  const int ch = g / (Dp->Rb + 2), h = g - ch * (Dp->Rb + 2);  // this group's (channel, row)
-  const bool active = ch < C && h < nh;
-  const int i = wrapi(r0 - 1 + h, M);
+  const int ngroups = blockDim.x / TT;
+  const int ch = g / Rb, hh = g - ch * Rb;
+  const bool active = ch < C && hh < nr;
+  const int i = r0 + hh;
+  const bool init = a.mode == ROW_INIT;
+  // Distinct buffers (x_out is written only when it is not the x buffer).
+  T *__restrict__ yt = a.yt;
+  T *__restrict__ xbuf = a.xbuf;
+  T *__restrict__ xout = (a.x_out && a.x_out != a.xbuf) ? a.x_out : nullptr;
   cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
-  // After the transforms, the same shared memory holds x, y~^{i+1} and g.
-  T *X = reinterpret_cast<T *>(smem_raw);  // [C][nh][N]
-  T *Yn = X + (size_t)C * nh * N;          // [C][nr][N]
-  T *Gv = Yn + (size_t)C * nr * N;         // [nr+1][N]
+  T *Ys = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)ngroups * GS);  // [C][Rb][N]
+  uint32_t *Ms = reinterpret_cast<uint32_t *>(Ys + (size_t)C * Rb * N);                        // [C][Rb][N/32]
 
+  if (!init) {
+    for (int c = 0; c < C; ++c) {
+      copy_async<T>(Ys + (size_t)c * Rb * N, yt + px0 + c * P + (long long)r0 * N, nr * N, threadIdx.x, blockDim.x);
+      copy_async<uint32_t>(Ms + (size_t)c * Rb * wpr, a.mask + Dp->mask + c * Dp->mask_plane + (long long)r0 * wpr,
+                           nr * wpr, threadIdx.x, blockDim.x);
+    }
+  }
+  cp_async_commit();
+
+  const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
+  T s_dz = T(0), s_fit = T(0);
   cx<T> v[32];
-  // 1. x + i T~x on this group's row (inverse row DFT), or x^0 = y~0.
+  const long long rowp = px0 + ch * P + (long long)i * N;
   if (active) {
-    const long long rowp = px0 + ch * P + (long long)i * N;
     if (init) {
 #pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = mk<T>(a.yt[rowp + q + TT * p2_slot<TT>(r)], T(0));
+      for (int r = 0; r < 32; ++r) v[r] = mk<T>(yt[rowp + q + TT * p2_slot<TT>(r)], T(0));
     } else {
-      const cpair<T> *src = a.S_in + spec0 + ((long long)ch * M + i) * Nh;
+      const cpair<T> *src = a.S_in + Dp->spec + ((long long)ch * M + i) * Nh;
 #pragma unroll
       for (int m = 0; m < 32; ++m) {
         const int n = q + TT * m;
-        if (2 * n <= N) {
-          const cpair<T> c = src[n];
-          v[m] = mk<T>(c.ar - c.bi, c.ai + c.br);
-        } else {
-          const cpair<T> c = src[N - n];
-          v[m] = mk<T>(c.ar + c.bi, c.br - c.ai);
-        }
+        const cpair<T> c = src[2 * n <= N ? n : N - n];
+        v[m] = 2 * n <= N ? mk<T>(c.ar - c.bi, c.ai + c.br) : mk<T>(c.ar + c.bi, c.br - c.ai);
       }
-      fft_p2<T, TT, +1>(v, tile, q, gm, tw2);
+      fft_p2<T, TT, +1>(v, tile, q, group_mask(TT), reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
-
-  // 2. x to shared memory; z-update on owned rows.
-  const T relax = a.relax;
-  double s_dd = 0.0, s_dz = 0.0, s_fit = 0.0, s_tv = 0.0;
   if (active) {
-    const long long rowp = px0 + ch * P + (long long)i * N;
-    const bool owned = h >= 1 && h <= nr;
+    const T relax = a.relax;
+    const T *yrow = Ys + ((size_t)ch * Rb + hh) * N;
+    const uint32_t *mrow = Ms + ((size_t)ch * Rb + hh) * wpr;
 #pragma unroll
     for (int r = 0; r < 32; ++r) {
       const int p = q + TT * p2_slot<TT>(r);
-      X[((size_t)ch * nh + h) * N + p] = v[r].x;
-      if (owned) {
-        const T yo = a.yt[rowp + p];
-        T yn = yo;
-        if (!init) {
-          if (!mask_bit(a.mask, mword + ch * mplane, (long long)i * N + p)) {
-            yn = relax * v[r].y - (relax - T(1)) * yo;
-            a.yt[rowp + p] = yn;
-            s_dz += double(yn - yo) * double(yn - yo);
-          } else {
-            s_fit += double(yo - v[r].y) * double(yo - v[r].y);
-          }
+      xbuf[rowp + p] = v[r].x;
+      if (xout) xout[rowp + p] = v[r].x;
+      if (!init) {
+        const T yo = yrow[p];
+        if (!((mrow[p >> 5] >> (p & 31)) & 1u)) {
+          const T yn = relax * v[r].y - (relax - T(1)) * yo;
+          yt[rowp + p] = yn;
+          if (stats) s_dz += (yn - yo) * (yn - yo);
+        } else if (stats) {
+          s_fit += (yo - v[r].y) * (yo - v[r].y);
         }
-        Yn[((size_t)ch * nr + h - 1) * N + p] = yn;
-        if (a.x_out) a.x_out[rowp + p] = v[r].x;
       }
     }
   }
+  if (stats) {
+    double fit = 0.5 * double(s_fit), z = 0.0, dz = double(s_dz);
+    block_sum3_dyn(z, dz, fit);
+    if (threadIdx.x == 0) {
+      double *o = a.partials + 3 * (long long)(Dp->row_pbase + blk);
+      o[1] = dz;
+      o[2] = fit;
+    }
+  }
+}
+
+// ----------------------------------------------------------- row (R2) ---
+// Forward half: one group per (channel, row).  The CTA stages x (rows
+// r0-1 .. r1), d (rows r0-1 .. r1-1) and y~ (rows r0 .. r1-1) of every
+// channel into shared memory with one batch of asynchronous copies.  From
+// them: the prox factor g at (i,p), (i,p-1), (i-1,p) (norm over channels),
+// d^{i+1} = (1-g) a, r = mu D^T (v - d^{i+1}) with v - d^{i+1} = (2g - 1) a;
+// then the forward row DFT of y~ + i r, split into (Y_row, R_row).
+// Statistics: ||dd||^2 and the TV half of the objective.
+// Shared memory: [x C x (Rb+2) rows][d C x (Rb+1) rows][y~ C x Rb rows] (the
+// transpose tiles reuse it after a barrier), then one row of y~ + i r per
+// group.
+template <typename T, int TT, int C>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(RowArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int GS = p2_group_stride<TT>();
+  const int wi = blockIdx.x;
+  const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
+  const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb;
+  const int blk = wi - Dp->row_begin;
+  const int r0 = blk * Rb, nr = min(Rb, M - r0);
+  const long long P = (long long)M * N, px0 = Dp->px;
+  const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int ch = g / Rb, hh = g - ch * Rb;
+  const bool active = ch < C && hh < nr;
+  const int i = r0 + hh;
+  const bool init = a.mode == ROW_INIT;
+  cx<T> *__restrict__ dout = reinterpret_cast<cx<T> *>(a.d_out);
+  T *Xs = reinterpret_cast<T *>(smem_raw);                      // [C][Rb+2][N]
+  cx<T> *Ds = reinterpret_cast<cx<T> *>(Xs + (size_t)C * (Rb + 2) * N);  // [C][Rb+1][N]
+  T *Ys = reinterpret_cast<T *>(Ds + (size_t)C * (Rb + 1) * N);           // [C][Rb][N]
+  const size_t staged = (size_t)C * ((Rb + 2) + 2 * (Rb + 1) + Rb) * N * sizeof(T);
+  const size_t tiles = (size_t)(blockDim.x / TT) * GS * sizeof(cx<T>);
+  cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)g * N;
+
+  for (int c = 0; c < C; ++c) {
+    for (int k = 0; k < nr + 2; ++k)
+      copy_async<T>(Xs + ((size_t)c * (Rb + 2) + k) * N, a.xbuf + px0 + c * P + (long long)wrapi(r0 - 1 + k, M) * N,
+                    N, threadIdx.x, blockDim.x);
+    if (!init)
+      for (int k = 0; k < nr + 1; ++k)
+        copy_async<cx<T>>(Ds + ((size_t)c * (Rb + 1) + k) * N,
+                          reinterpret_cast<const cx<T> *>(a.d_in) + px0 + c * P + (long long)wrapi(r0 - 1 + k, M) * N,
+                          N, threadIdx.x, blockDim.x);
+    copy_async<T>(Ys + (size_t)c * Rb * N, a.yt + px0 + c * P + (long long)r0 * N, nr * N, threadIdx.x, blockDim.x);
+  }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
 
-  // 3. g = max(1 - tau/||a||, 0) on rows r0-1 .. r1-1 (one group per row,
-  //    all channels), d^{i+1} = (1 - g) a on owned rows.
   const T tau = a.tau, tau2 = a.tau * a.tau;
-  if (g <= nr) {
-    const int hh = g, ii = wrapi(r0 - 1 + hh, M);
-#pragma unroll 4
-    for (int m = 0; m < 32; ++m) {
-      const int p = q + TT * m, p1 = (p + 1 == N) ? 0 : p + 1;
-      T ah[C], av[C], dh0[C], dv0[C];
-      T s = T(0), tv = T(0);
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const T *Xr = X + ((size_t)c * nh + hh) * N;
-        const T x0 = Xr[p], gh = Xr[p1] - x0, gv = Xr[N + p] - x0;
-        const cx<T> dold = din ? din[px0 + c * P + (long long)ii * N + p] : mk<T>(T(0), T(0));
-        dh0[c] = dold.x;
-        dv0[c] = dold.y;
-        ah[c] = gh + dold.x;
-        av[c] = gv + dold.y;
-        s += ah[c] * ah[c] + av[c] * av[c];
-        tv += gh * gh + gv * gv;
-      }
-      const T gg = init ? T(1) : (s > tau2 ? T(1) - tau * rsqrt_t<T>(s) : T(0));
-      Gv[(size_t)hh * N + p] = gg;
-      if (hh >= 1) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const T dnh = (T(1) - gg) * ah[c], dnv = (T(1) - gg) * av[c];
-          dout[px0 + c * P + (long long)ii * N + p] = mk<T>(dnh, dnv);
-          s_dd += double(dnh - dh0[c]) * double(dnh - dh0[c]) + double(dnv - dv0[c]) * double(dnv - dv0[c]);
-        }
-        s_tv += sqrt(double(tv));
-      }
-    }
-  }
-  __syncthreads();
-
-  // 4. r = mu D^T (v - d^{i+1}) on owned rows; v <- y~^{i+1} + i r.
-  const bool fwd = active && h >= 1 && h <= nr;
+  const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
+  T s_dd = T(0), s_tv = T(0);
   bool finite = true;
-  if (fwd) {
-    const T *Xr = X + ((size_t)ch * nh + h) * N;
-    const T *Gr = Gv + (size_t)h * N;
-    const long long dro = px0 + ch * P;
-    const int iu = wrapi(i - 1, M);
-#pragma unroll
+  if (active) {
+#pragma unroll 4
     for (int m = 0; m < 32; ++m) {
       const int p = q + TT * m;
       const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
-      const T x0 = Xr[p], xl = Xr[pm], xr = Xr[p1], xd = Xr[N + p], xu = Xr[p - N];
-      const T g0 = T(2) * Gr[p] - T(1), gl = T(2) * Gr[pm] - T(1), gu = T(2) * Gr[p - N] - T(1);
-      const cx<T> d0 = din ? din[dro + (long long)i * N + p] : mk<T>(T(0), T(0));
-      const cx<T> dl = din ? din[dro + (long long)i * N + pm] : mk<T>(T(0), T(0));
-      const cx<T> du = din ? din[dro + (long long)iu * N + p] : mk<T>(T(0), T(0));
-      const T uh0 = g0 * (xr - x0 + d0.x), uhl = gl * (x0 - xl + dl.x);
-      const T uv0 = g0 * (xd - x0 + d0.y), uvu = gu * (x0 - xu + du.y);
-      const T r = a.mu * ((uhl - uh0) + (uvu - uv0));
-      const T yv = Yn[((size_t)ch * nr + h - 1) * N + p];
+      T s0 = T(0), sl = T(0), su = T(0), tv = T(0);
+      T ah0 = T(0), av0 = T(0), ahl = T(0), avu = T(0), dh0 = T(0), dv0 = T(0);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T *xr = Xs + ((size_t)c * (Rb + 2) + hh + 1) * N;  // row i; xr - N: i-1, xr + N: i+1
+        const T x0 = xr[p], xl = xr[pm], xrr = xr[p1], xdn = xr[N + p], xdl = xr[N + pm], xup = xr[p - N],
+                xul = xr[p1 - N];
+        const cx<T> *dr = Ds + ((size_t)c * (Rb + 1) + hh + 1) * N;  // row i; dr - N: i-1
+        const cx<T> d0 = init ? mk<T>(T(0), T(0)) : dr[p];
+        const cx<T> dl = init ? mk<T>(T(0), T(0)) : dr[pm];
+        const cx<T> du = init ? mk<T>(T(0), T(0)) : dr[p - N];
+        const T gh = xrr - x0, gv = xdn - x0;
+        const T a_h = gh + d0.x, a_v = gv + d0.y;
+        s0 += a_h * a_h + a_v * a_v;
+        tv += gh * gh + gv * gv;
+        const T a_hl = (x0 - xl) + dl.x, a_vl = (xdl - xl) + dl.y;
+        sl += a_hl * a_hl + a_vl * a_vl;
+        const T a_hu = (xul - xup) + du.x, a_vu = (x0 - xup) + du.y;
+        su += a_hu * a_hu + a_vu * a_vu;
+        if (c == ch) {
+          ah0 = a_h;
+          av0 = a_v;
+          ahl = a_hl;
+          avu = a_vu;
+          dh0 = d0.x;
+          dv0 = d0.y;
+        }
+      }
+      const T g0 = init ? T(1) : (s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0));
+      const T gl = init ? T(1) : (sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0));
+      const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
+      const T dnh = (T(1) - g0) * ah0, dnv = (T(1) - g0) * av0;
+      dout[px0 + ch * P + (long long)i * N + p] = mk<T>(dnh, dnv);
+      if (stats) {
+        s_dd += (dnh - dh0) * (dnh - dh0) + (dnv - dv0) * (dnv - dv0);
+        if (ch == 0) s_tv += sqrt(tv);
+      }
+      const T r = a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
+                          ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
+      const T yv = Ys[((size_t)ch * Rb + hh) * N + p];
       finite = finite && isfinite(r) && isfinite(yv);
-      v[m] = mk<T>(yv, r);
+      Cs[p] = mk<T>(yv, r);
     }
   }
   if (!finite) atomicOr(a.err, 1);
-  __syncthreads();
-
-  // 5. Forward row DFT of y~ + i r, then split C = Y + i R and store.
-  if (fwd) {
-    fft_p2<T, TT, -1>(v, tile, q, gm, tw2);
+  __syncthreads();  // the transpose tiles below reuse the staged rows
+  if (active) {
+    cx<T> v[32];
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = Cs[q + TT * m];
+    cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
+    const unsigned gm = group_mask(TT);
+    fft_p2<T, TT, -1>(v, tile, q, gm, reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row);
 #pragma unroll
     for (int r = 0; r < 32; ++r) tile[q + TT * p2_slot<TT>(r)] = v[r];
     __syncwarp(gm);
-    cpair<T> *dst = a.S_out + spec0 + ((long long)ch * M + i) * Nh;
+    cpair<T> *__restrict__ dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
     for (int k = q; k < Nh; k += TT) {
       const cx<T> c1 = tile[k], c2 = tile[k == 0 ? 0 : N - k];
       cpair<T> o;
@@ -189,15 +274,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_pass_p2_kernel
       dst[k] = o;
     }
   }
-
-  if (a.partials) {
-    double fit = 0.5 * s_fit + double(a.lambda) * s_tv;
-    block_sum3_dyn(s_dd, s_dz, fit);
+  if (stats) {
+    double tvl = double(a.lambda) * double(s_tv), z = 0.0, dd = double(s_dd);
+    block_sum3_dyn(dd, z, tvl);
     if (threadIdx.x == 0) {
       double *o = a.partials + 3 * (long long)(Dp->row_pbase + blk);
-      o[0] = s_dd;
-      o[1] = s_dz;
-      o[2] = fit;
+      o[0] = dd;
+      o[2] += tvl;
     }
   }
 }
@@ -220,16 +303,28 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   cx<T> *st = reinterpret_cast<cx<T> *>(smem_raw);  // [M][SL]
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
   const unsigned gm = group_mask(TT);
+  const int ngroups = blockDim.x / TT;
   cx<T> *tile = st + (size_t)M * SL + (size_t)g * GS;
+  cx<T> *Hs = st + (size_t)M * SL + (size_t)ngroups * GS;  // [M][W] H^ tile
+  T *S2s = reinterpret_cast<T *>(Hs + (size_t)M * Dp->W);  // [M] column sin^2, then [W] row sin^2
   const long long base = Dp->spec + (long long)ch * M * Nh + k20;
   const int nthr = blockDim.x;
 
-  for (int e = threadIdx.x; e < M * w; e += nthr) {
-    const int ii = e / w, ww = e - ii * w;
-    const cpair<T> c = a.S_in[base + (long long)ii * Nh + ww];
-    st[ii * SL + 2 * ww] = mk<T>(c.ar, c.ai);
-    st[ii * SL + 2 * ww + 1] = mk<T>(c.br, c.bi);
-  }
+  // Loops below give each thread one signal column s of the tile (s < 2W) and
+  // rows r0t, r0t + rstep, ... (nthr is a multiple of 2W), avoiding division.
+  const int S2 = 2 * Dp->W, scol = threadIdx.x % S2, r0t = threadIdx.x / S2, rstep = nthr / S2;
+  const bool lane_ok = threadIdx.x < rstep * S2;  // threads beyond whole column sets stay idle here
+  const bool scol_on = lane_ok && scol < 2 * w;
+  if (scol_on)
+    for (int ii = r0t; ii < M; ii += rstep)
+      cp_async<sizeof(cx<T>)>(&st[ii * SL + scol],
+                              reinterpret_cast<const cx<T> *>(&a.S_in[base + (long long)ii * Nh]) + scol);
+  if (lane_ok && scol < w)
+    for (int k1 = r0t; k1 < M; k1 += rstep) cp_async<sizeof(cx<T>)>(&Hs[k1 * w + scol], &H[(long long)k1 * Nh + k20 + scol]);
+  for (int e = threadIdx.x; e < M + w; e += nthr)
+    cp_async<sizeof(T)>(&S2s[e], e < M ? &s2c[e] : &s2r[k20 + e - M]);
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
   cx<T> v[32];
   const bool active = g < 2 * w;
@@ -242,15 +337,18 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   }
   __syncthreads();
   const T mu = a.mu, scale = T(1) / (T(M) * T(N));
-  for (int e = threadIdx.x; e < M * w; e += nthr) {
-    const int k1 = e / w, ww = e - k1 * w, k2 = k20 + ww;
-    const cx<T> hv = __ldg(&H[(long long)k1 * Nh + k2]);
-    const T den = hv.x * hv.x + hv.y * hv.y + mu * (__ldg(&s2c[k1]) + __ldg(&s2r[k2]));
-    const T inv = scale / den;
-    const cx<T> Y = st[k1 * SL + 2 * ww], R = st[k1 * SL + 2 * ww + 1];
-    const cx<T> Xv = cscale<T>(cadd<T>(cmulc<T>(hv, Y), R), inv);
-    st[k1 * SL + 2 * ww] = Xv;
-    st[k1 * SL + 2 * ww + 1] = cmul<T>(hv, Xv);
+  if (lane_ok && scol < w) {
+    const int ww = scol;
+    const T s2w = S2s[M + ww];
+    for (int k1 = r0t; k1 < M; k1 += rstep) {
+      const cx<T> hv = Hs[k1 * w + ww];
+      const T den = hv.x * hv.x + hv.y * hv.y + mu * (S2s[k1] + s2w);
+      const T inv = scale / den;
+      const cx<T> Y = st[k1 * SL + 2 * ww], R = st[k1 * SL + 2 * ww + 1];
+      const cx<T> Xv = cscale<T>(cadd<T>(cmulc<T>(hv, Y), R), inv);
+      st[k1 * SL + 2 * ww] = Xv;
+      st[k1 * SL + 2 * ww + 1] = cmul<T>(hv, Xv);
+    }
   }
   __syncthreads();
   if (active) {
@@ -261,15 +359,17 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     for (int r = 0; r < 32; ++r) st[(q + TT * p2_slot<TT>(r)) * SL + g] = v[r];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < M * w; e += nthr) {
-    const int ii = e / w, ww = e - ii * w;
-    const cx<T> Xv = st[ii * SL + 2 * ww], HX = st[ii * SL + 2 * ww + 1];
-    cpair<T> c;
-    c.ar = Xv.x;
-    c.ai = Xv.y;
-    c.br = HX.x;
-    c.bi = HX.y;
-    a.S_out[base + (long long)ii * Nh + ww] = c;
+  if (lane_ok && scol < w) {
+    const int ww = scol;
+    for (int ii = r0t; ii < M; ii += rstep) {
+      const cx<T> Xv = st[ii * SL + 2 * ww], HX = st[ii * SL + 2 * ww + 1];
+      cpair<T> c;
+      c.ar = Xv.x;
+      c.ai = Xv.y;
+      c.br = HX.x;
+      c.bi = HX.y;
+      a.S_out[base + (long long)ii * Nh + ww] = c;
+    }
   }
 }
 

@@ -73,22 +73,27 @@ struct Layout {
 
 bool is_pow2_32(int L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
 
-size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz) {
-  const int groups_raw = C * (rb + 2), per_warp = 32 / tt > 0 ? 32 / tt : 1;
-  const int groups = (groups_raw + per_warp - 1) / per_warp * per_warp;
-  const size_t tiles = (size_t)groups * (32 * (tt + 1) + (tt < 16 ? tt : 0)) * 2 * esz;
-  const size_t arrays = (size_t)(C * (rb + 2) + C * rb + rb + 1) * N * esz;
-  return std::max(tiles, arrays);
-}
-
+// Power-of-two row passes (inverse and forward halves): rb rows per CTA, one
+// group of tt threads per (channel, row), rounded up to whole warps; shared
+// memory holds one transpose tile per group.
 int p2_row_threads(int C, int rb, int tt) {
-  const int groups_raw = C * (rb + 2), per_warp = 32 / tt;
-  return (groups_raw + per_warp - 1) / per_warp * per_warp * tt;
+  const int per_warp = 32 / tt;
+  return (C * rb + per_warp - 1) / per_warp * per_warp * tt;
 }
 
+size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz) {
+  const size_t tiles = (size_t)(p2_row_threads(C, rb, tt) / tt) * p2_group_stride_h(tt) * 2 * esz;
+  const size_t inv = tiles + (size_t)C * rb * N * esz + (size_t)C * rb * (N / 32) * 4;            // inverse half
+  const size_t fwd = std::max((size_t)C * ((rb + 2) + 2 * (rb + 1) + rb) * N * esz, tiles) +
+                     (size_t)(p2_row_threads(C, rb, tt) / tt) * N * 2 * esz;                     // forward half
+  return std::max(inv, fwd);
+}
+
+// Column pass (power of two): staging tile + transpose tiles + H^ tile + sin^2 tables.
 size_t p2_col_smem(int M, int w, int tt, size_t esz) {
   const int per_warp = 32 / tt, groups = (2 * w + per_warp - 1) / per_warp * per_warp;
-  return (size_t)M * ((2 * w) | 1) * 2 * esz + (size_t)groups * (32 * (tt + 1) + (tt < 16 ? tt : 0)) * 2 * esz;
+  return (size_t)M * ((2 * w) | 1) * 2 * esz + (size_t)groups * p2_group_stride_h(tt) * 2 * esz +
+         (size_t)M * w * 2 * esz + (size_t)(M + w) * esz;
 }
 
 int p2_col_threads(int w, int tt) {
@@ -154,7 +159,8 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   long long g_rows = 0, g_cols = 0, p2_rows[33] = {0}, p2_cols[33] = {0};
   for (int j = 0; j < L.B; ++j) {
     const int M = d->rows[j], N = d->cols[j];
-    if (allow_p2 && is_pow2_32(N) && N / 32 * L.C * 3 <= maxthr && p2_row_smem(L.C, N, 1, N / 32, L.esz) <= kMaxSmem) {
+    if (allow_p2 && is_pow2_32(N) && p2_row_threads(L.C, 1, N / 32) <= maxthr &&
+        p2_row_smem(L.C, N, 1, N / 32, L.esz) <= kMaxSmem) {
       row_tt[j] = N / 32;
       p2_rows[N / 32] += M;
     } else {
@@ -194,7 +200,8 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   for (int tt = 2; tt <= 32; tt *= 2) {
     const int N = 32 * tt;
     if (p2_rows[tt]) {
-      int rb = (int)std::max<long long>(1, (p2_rows[tt] + target - 1) / target);
+      const int rtarget = env_int("DECONV_P2_ROW_CTAS", 152);
+      int rb = (int)std::max<long long>(1, (p2_rows[tt] + rtarget - 1) / rtarget);
       rb = env_int("DECONV_P2_ROW_BLOCK", rb);
       while (rb > 1 && (p2_row_threads(L.C, rb, tt) > maxthr || p2_row_smem(L.C, N, rb, tt, L.esz) > kMaxSmem)) --rb;
       p2_rb[tt] = rb;
@@ -204,7 +211,8 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   {
     long long tot = 0;
     for (int tt = 2; tt <= 32; tt *= 2) tot += p2_cols[tt];
-    p2w_all = (int)std::max<long long>(1, (tot + target - 1) / target);
+    const int ctarget = env_int("DECONV_P2_COL_CTAS", 152);
+    p2w_all = (int)std::max<long long>(1, (tot + ctarget - 1) / ctarget);
     p2w_all = env_int("DECONV_P2_COL_TILE", p2w_all);
   }
   for (int tt = 2; tt <= 32; tt *= 2) {
@@ -400,6 +408,7 @@ RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_i
   a.relax = (T)p->relax;
   a.lambda = (T)p->lambda;
   a.x_out = x_out;
+  a.xbuf = p->at<T>(L.o_xbuf);
   a.partials = partials;
   a.err = p->at<int>(L.o_err);
   return a;
