@@ -53,6 +53,8 @@ def _load():
         lib.or_init_ytilde.argtypes = [_D, _U8, i, i, i, i, _D]
         lib.or_admm.argtypes = [i, i, i, i, _D, _D, _U8, d, d, d, i, i, i, _D, _D, _D, _D, _D]
         lib.or_admm.restype = i
+        lib.or_admm_grad.argtypes = [i, i, i, i, _D, _D, _U8, d, d, d, i, i, _D, _D, _D, _D, _D]
+        lib.or_admm_grad.restype = i
         _lib = lib
     return _lib
 
@@ -195,3 +197,31 @@ def admm(y: np.ndarray, mask: np.ndarray, h: np.ndarray, lam: float, mu: float, 
     if rc != 0:
         raise RuntimeError(f"or_admm failed: {rc}")
     return x, st, (s[:iters] if stats else None)
+
+
+def admm_grad(y: np.ndarray, mask: np.ndarray, h: np.ndarray, lam: float, mu: float, iters: int,
+              x_true: np.ndarray, relax: float = 2.0, round_f32: bool = True):
+    """Loss L = mean((x^{iters} - x_true)^2) over the C x M x N image and its
+    gradients: returns (L, dL/dlambda, dL/dh (K x K), x^{iters})."""
+    y = _c(y)
+    if y.ndim == 2:
+        y = y[None]
+    C, M, N = y.shape
+    m = np.ascontiguousarray(mask, np.uint8).reshape(C, M, N)
+    h = _c(h)
+    xt = _c(x_true).reshape(C, M, N)
+    loss = np.zeros(1)
+    dlam = np.zeros(1)
+    dh = np.zeros_like(h)
+    x = np.zeros((C, M, N))
+    rc = _load().or_admm_grad(C, M, N, h.shape[0], _p(h), _p(y), m.ctypes.data_as(_U8), float(lam), float(mu),
+                              float(relax), int(iters), int(round_f32), _p(xt), _p(loss), _p(dlam), _p(dh), _p(x))
+    if rc != 0:
+        raise RuntimeError(f"or_admm_grad failed: {rc}")
+    return float(loss[0]), float(dlam[0]), dh, x
+
+
+def loss_only(y, mask, h, lam, mu, iters, x_true, relax=2.0, round_f32=True) -> float:
+    """L = mean((x^{iters} - x_true)^2) from the forward oracle (for finite differences)."""
+    x, _, _ = admm(y, mask, h, lam, mu, iters, relax=relax, round_f32=round_f32)
+    return float(np.mean((x - np.asarray(x_true).reshape(x.shape)) ** 2))

@@ -406,3 +406,137 @@ int or_admm(int C, int M, int N, int K, const double *h, const double *y, const 
   free(den); free(rhs); free(tmp); free(dx); free(a); free(vn); free(work);
   return 0;
 }
+
+/* --------------------------------------------------- reverse pass (grad) ---
+ * Gradient of L = mean over all C*M*N pixels of (x^{iters} - x_true)^2 with
+ * respect to lambda and the kernel taps h, through `iters` iterations of
+ * or_admm (from the initial fill, relax as given).  Reverse-mode
+ * differentiation of the steps of Eqs. (admm_aprox_1)-(admm_aprox_4) as
+ * written above, in reverse order; every forward quantity is stored (this is
+ * a small-size reference, not a checkpointed implementation).
+ * Per step i (a = D x^{i+1} + d^i, adjoints carried: yb, vb, db):
+ *   w = vb - db;  ab = db + J(a) w   (J the Jacobian of vector-soft, Sec. III-B)
+ *   taub -= sum_j a_j^T w_j / ||a_j||  over pixels with ||a_j|| > tau
+ *   tb = relax M_u yb;  yb' = (M_o - (relax-1) M_u) yb;  xb = D^T ab (+ dL/dx)
+ *   bb = (T~^T T~ + mu D^T D)^{-1} (xb + T~^T tb)
+ *   hb += corr(bb, y~^i - T~x^{i+1}) + corr(x^{i+1}, tb - T~ bb)
+ *   yb = yb' + T~ bb;  vb = mu D bb;  db = ab - mu D bb
+ * with corr(u, w)[m] = sum_n u[n - m] w[n] at the kernel offsets m.
+ * dlambda = taub / mu (tau = lambda / mu).  dh is K*K, row-major like h.
+ */
+static void corr_taps(const double *u, const double *w, int M, int N, int K, double *acc) {
+  int b = K / 2;
+  for (int p = -b; p <= b; ++p)
+    for (int q = -b; q <= b; ++q) {
+      double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < N; ++j) s += u[(size_t)wrap(i - p, M) * N + wrap(j - q, N)] * w[(size_t)i * N + j];
+      acc[(p + b) * K + (q + b)] += s;
+    }
+}
+
+int or_admm_grad(int C, int M, int N, int K, const double *h, const double *y, const uint8_t *mask, double lambda,
+                 double mu, double relax, int iters, int round_f32, const double *x_true, double *loss,
+                 double *dlambda, double *dh, double *x_out) {
+  size_t P = (size_t)M * N, CP = (size_t)C * P;
+  double tau = lambda / mu;
+  double *den = solve_denominator(M, N, h, K, mu);
+  cplx *work = malloc(sizeof(cplx) * P);
+  /* stored forward quantities */
+  double *YT = malloc(sizeof(double) * CP * (iters + 1));       /* y~^i */
+  double *X = malloc(sizeof(double) * CP * (iters + 1));        /* x^i (x^0 unused) */
+  double *TX = malloc(sizeof(double) * CP * (iters + 1));       /* T~ x^i */
+  double *A = malloc(sizeof(double) * 2 * CP * (iters + 1));    /* a^i = D x^i + d^{i-1} */
+  double *v = malloc(sizeof(double) * 2 * CP), *d = malloc(sizeof(double) * 2 * CP);
+  double *rhs = malloc(sizeof(double) * P), *tmp = malloc(sizeof(double) * P), *tmp2 = malloc(sizeof(double) * P);
+  double *dx = malloc(sizeof(double) * 2 * CP);
+  for (int c = 0; c < C; ++c) {
+    or_init_ytilde(y + c * P, mask + c * P, M, N, K, round_f32, YT + c * P);
+    or_diff_fwd(YT + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P);
+  }
+  memset(d, 0, sizeof(double) * 2 * CP);
+  for (int it = 0; it < iters; ++it) {
+    double *yt = YT + CP * it, *ytn = YT + CP * (it + 1), *x = X + CP * (it + 1), *tx = TX + CP * (it + 1);
+    double *a = A + 2 * CP * (it + 1);
+    for (int c = 0; c < C; ++c) {
+      for (size_t i = 0; i < P; ++i) {
+        tmp[i] = v[2 * c * P + i] - d[2 * c * P + i];
+        tmp2[i] = v[(2 * c + 1) * P + i] - d[(2 * c + 1) * P + i];
+      }
+      or_diff_adj(tmp, tmp2, M, N, rhs);
+      for (size_t i = 0; i < P; ++i) rhs[i] *= mu;
+      or_conv_circ_adj(yt + c * P, M, N, h, K, tmp);
+      for (size_t i = 0; i < P; ++i) rhs[i] += tmp[i];
+      solve_x(rhs, den, M, N, x + c * P, work);
+      or_conv_circ(x + c * P, M, N, h, K, tx + c * P);
+      for (size_t i = 0; i < P; ++i)
+        ytn[c * P + i] = mask[c * P + i] ? yt[c * P + i] : relax * tx[c * P + i] - (relax - 1.0) * yt[c * P + i];
+      or_diff_fwd(x + c * P, M, N, dx + 2 * c * P, dx + (2 * c + 1) * P);
+    }
+    for (size_t i = 0; i < 2 * CP; ++i) a[i] = dx[i] + d[i];
+    or_vsoft(a, (int)P, 2 * C, tau, v);
+    for (size_t i = 0; i < 2 * CP; ++i) d[i] = a[i] - v[i];
+  }
+  double *xK = X + CP * iters;
+  double cnt = (double)CP, L = 0.0;
+  for (size_t i = 0; i < CP; ++i) L += (xK[i] - x_true[i]) * (xK[i] - x_true[i]);
+  *loss = L / cnt;
+  if (x_out) memcpy(x_out, xK, sizeof(double) * CP);
+
+  double *yb = calloc(CP, sizeof(double)), *vb = calloc(2 * CP, sizeof(double)), *db = calloc(2 * CP, sizeof(double));
+  double *ab = malloc(sizeof(double) * 2 * CP), *wv = malloc(sizeof(double) * 2 * CP);
+  double *xb = malloc(sizeof(double) * CP), *tb = malloc(sizeof(double) * CP), *bb = malloc(sizeof(double) * CP);
+  double *tbb = malloc(sizeof(double) * CP), *e = malloc(sizeof(double) * P);
+  double taub = 0.0;
+  for (int t = 0; t < K * K; ++t) dh[t] = 0.0;
+  for (int it = iters - 1; it >= 0; --it) {
+    double *a = A + 2 * CP * (it + 1), *x = X + CP * (it + 1), *tx = TX + CP * (it + 1), *yt = YT + CP * it;
+    for (size_t i = 0; i < 2 * CP; ++i) wv[i] = vb[i] - db[i];
+    for (size_t j = 0; j < P; ++j) {
+      double n2 = 0.0, aw = 0.0;
+      for (int k = 0; k < 2 * C; ++k) {
+        n2 += a[k * P + j] * a[k * P + j];
+        aw += a[k * P + j] * wv[k * P + j];
+      }
+      double n = sqrt(n2);
+      for (int k = 0; k < 2 * C; ++k) {
+        double g = 0.0;
+        if (n > tau) g = (1.0 - tau / n) * wv[k * P + j] + tau * a[k * P + j] * aw / (n2 * n);
+        ab[k * P + j] = db[k * P + j] + g;
+      }
+      if (n > tau) taub -= aw / n;
+    }
+    for (int c = 0; c < C; ++c) {
+      for (size_t i = 0; i < P; ++i) {
+        double yv = yb[c * P + i];
+        int obs = mask[c * P + i] != 0;
+        tb[c * P + i] = obs ? 0.0 : relax * yv;
+        yb[c * P + i] = obs ? yv : -(relax - 1.0) * yv; /* yb' */
+      }
+      or_diff_adj(ab + 2 * c * P, ab + (2 * c + 1) * P, M, N, xb + c * P);
+      if (it == iters - 1)
+        for (size_t i = 0; i < P; ++i) xb[c * P + i] += 2.0 * (xK[c * P + i] - x_true[c * P + i]) / cnt;
+      or_conv_circ_adj(tb + c * P, M, N, h, K, rhs);
+      for (size_t i = 0; i < P; ++i) rhs[i] += xb[c * P + i];
+      solve_x(rhs, den, M, N, bb + c * P, work);
+      or_conv_circ(bb + c * P, M, N, h, K, tbb + c * P);
+      for (size_t i = 0; i < P; ++i) e[i] = yt[c * P + i] - tx[c * P + i];
+      corr_taps(bb + c * P, e, M, N, K, dh);
+      for (size_t i = 0; i < P; ++i) e[i] = tb[c * P + i] - tbb[c * P + i];
+      corr_taps(x + c * P, e, M, N, K, dh);
+      for (size_t i = 0; i < P; ++i) yb[c * P + i] += tbb[c * P + i];
+      or_diff_fwd(bb + c * P, M, N, tmp, tmp2);
+      for (size_t i = 0; i < P; ++i) {
+        vb[2 * c * P + i] = mu * tmp[i];
+        vb[(2 * c + 1) * P + i] = mu * tmp2[i];
+        db[2 * c * P + i] = ab[2 * c * P + i] - mu * tmp[i];
+        db[(2 * c + 1) * P + i] = ab[(2 * c + 1) * P + i] - mu * tmp2[i];
+      }
+    }
+  }
+  *dlambda = taub / mu;
+  free(den); free(work); free(YT); free(X); free(TX); free(A); free(v); free(d); free(rhs); free(tmp); free(tmp2);
+  free(dx); free(yb); free(vb); free(db); free(ab); free(wv); free(xb); free(tb); free(bb); free(tbb); free(e);
+  return 0;
+}
