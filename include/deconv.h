@@ -116,6 +116,25 @@ deconv_status deconv_solve(deconv_plan plan, const void *y, void *x, int32_t ite
  * before returning.  Uses the workspace as staging; nothing is allocated. */
 deconv_status deconv_solve_host(deconv_plan plan, const void *y_host, void *x_host, int32_t iters);
 
+/* Gradient of the unrolled iteration (the differentiable use of the method:
+ * learning lambda or the blur kernel through a fixed number of iterations).
+ * L = mean over every pixel of the batch of (x^{iters} - x_true)^2, with
+ * x^{iters} from deconv_solve(y, iters, warm = 0).  Returns L and dL/dlambda
+ * on the host (loss, dlambda) and dL/dh in dh (device, the layout of h).
+ * Reverse-mode differentiation of Eqs. (admm_aprox_1)-(admm_aprox_4) with
+ * the over-relaxed z-update: the forward pass keeps (y~, d, forward
+ * spectrum) every ckpt_every iterations; the reverse pass recomputes each
+ * segment from its checkpoint and runs the adjoint iteration backwards (the
+ * x-step is self-adjoint; the vector soft-threshold contributes its
+ * Jacobian, zero below the threshold).  grad_ws: device, 256-byte aligned,
+ * at least deconv_grad_workspace_size() bytes.  x_out: NULL or device, the
+ * batch layout, receives x^{iters}.  Power-of-two sizes 64..1024 only
+ * (DECONV_EUNSUPPORTED otherwise).  Synchronises the stream; leaves the plan
+ * state at x^{iters}'s last recomputed segment (use warm = 0 next). */
+deconv_status deconv_grad_workspace_size(deconv_plan plan, int32_t iters, int32_t ckpt_every, size_t *bytes);
+deconv_status deconv_grad(deconv_plan plan, const void *y, const void *x_true, int32_t iters, int32_t ckpt_every,
+                          void *grad_ws, size_t grad_ws_bytes, double *loss, double *dlambda, void *dh, void *x_out);
+
 /* Allocation-free solve (the paper has no counterpart; this is a service of
  * the library).  For callers that may not allocate device memory: code
  * hosted inside a framework that owns the CUDA allocator, latency-critical
@@ -153,6 +172,10 @@ deconv_status deconv_sync(deconv_plan plan);
 /* Release the plan's host resources (and its cached CUDA graph).  The
  * workspace is the caller's to free. */
 deconv_status deconv_plan_destroy(deconv_plan plan);
+
+/* Diagnostic: the last CUDA runtime error seen by this thread in the
+ * library ("" if none), with its name and the library source line. */
+const char *deconv_last_error(void);
 
 /* Static string for a status code. */
 const char *deconv_status_string(deconv_status status);

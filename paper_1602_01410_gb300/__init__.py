@@ -28,12 +28,13 @@ DECONV_F32, DECONV_F64 = 0, 1
 # Entry points declared in include/deconv.h (checked by the test suite).
 EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "deconv_solve_host",
            "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
-           "deconv_solve_noalloc")
+           "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error")
 
 
 class DeconvError(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {deconv_status_string(status)} (status {status})")
+        detail = f" [{deconv_last_error()}]" if status == DECONV_ECUDA else ""
+        super().__init__(f"{where}: {deconv_status_string(status)} (status {status}){detail}")
         self.status = status
 
 
@@ -63,11 +64,16 @@ def load() -> ctypes.CDLL:
         lib.deconv_profile_passes.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         lib.deconv_sync.argtypes = [vp]
         lib.deconv_solve_noalloc.argtypes = [ctypes.POINTER(deconv_dims), vp, vp, vp, vp, dbl, dbl, i32, vp]
+        lib.deconv_grad_workspace_size.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.deconv_grad.argtypes = [vp, vp, vp, i32, i32, vp, ctypes.c_size_t, ctypes.POINTER(dbl),
+                                    ctypes.POINTER(dbl), vp, vp]
         lib.deconv_plan_destroy.argtypes = [vp]
         lib.deconv_status_string.argtypes = [ctypes.c_int]
         lib.deconv_status_string.restype = ctypes.c_char_p
+        lib.deconv_last_error.argtypes = []
+        lib.deconv_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name != "deconv_status_string":
+            if name not in ("deconv_status_string", "deconv_last_error"):
                 getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -92,6 +98,10 @@ def _check(status: int, where: str) -> None:
 
 def deconv_status_string(status: int) -> str:
     return load().deconv_status_string(int(status)).decode()
+
+
+def deconv_last_error() -> str:
+    return load().deconv_last_error().decode()
 
 
 def deconv_workspace_size(dims: deconv_dims) -> int:
@@ -135,6 +145,22 @@ def deconv_solve_noalloc(dims: deconv_dims, h_ptr: int, mask_ptr: int, y_ptr: in
     array (no device allocation); synchronises `stream`."""
     _check(load().deconv_solve_noalloc(ctypes.byref(dims), h_ptr, mask_ptr, y_ptr, x_ptr, float(lam), float(mu),
                                        int(iters), stream), "deconv_solve_noalloc")
+
+
+def deconv_grad_workspace_size(plan: int, iters: int, ckpt_every: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().deconv_grad_workspace_size(plan, int(iters), int(ckpt_every), ctypes.byref(n)),
+           "deconv_grad_workspace_size")
+    return n.value
+
+
+def deconv_grad(plan: int, y_ptr: int, xtrue_ptr: int, iters: int, ckpt_every: int, gws_ptr: int, gws_bytes: int,
+                dh_ptr: int, x_out_ptr: Optional[int] = None):
+    """Returns (loss, dL/dlambda); dL/dh is written to dh_ptr (device)."""
+    loss, dlam = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().deconv_grad(plan, y_ptr, xtrue_ptr, int(iters), int(ckpt_every), gws_ptr, gws_bytes,
+                              ctypes.byref(loss), ctypes.byref(dlam), dh_ptr, x_out_ptr), "deconv_grad")
+    return loss.value, dlam.value
 
 
 def deconv_plan_destroy(plan: int) -> None:
@@ -183,6 +209,17 @@ class Plan:
                      None if stats is None else stats.data_ptr())
         return x
 
+    def grad(self, y, x_true, iters: int, ckpt_every: int = 10, x_out=None):
+        """Loss mean((x^iters - x_true)^2), dL/dlambda and dL/dh (tensor shaped like h)."""
+        torch = self._torch
+        n = deconv_grad_workspace_size(self.handle, iters, ckpt_every)
+        gws = torch.empty(n + 256, dtype=torch.uint8, device=self.workspace.device)
+        gptr = gws.data_ptr() + (-gws.data_ptr()) % 256
+        dh = torch.empty_like(self._h)
+        loss, dlam = deconv_grad(self.handle, y.data_ptr(), x_true.data_ptr(), iters, ckpt_every, gptr, n,
+                                 dh.data_ptr(), None if x_out is None else x_out.data_ptr())
+        return loss, dlam, dh
+
     def solve_host(self, y_host, x_host, iters: int) -> None:
         deconv_solve_host(self.handle, y_host.data_ptr(), x_host.data_ptr(), iters)
 
@@ -202,3 +239,45 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class DeconvLoss:
+    """torch.autograd.Function: L = mean((x^iters - x_true)^2) of the unrolled
+    partial ADMM as a differentiable function of lambda (0-dim tensor) and
+    the blur kernel h; the forward call runs deconv_grad, which returns the
+    loss and both gradients together, and backward scales them by the
+    incoming gradient.  y, mask and x_true are data (no gradient)."""
+
+    @staticmethod
+    def apply(lam, h, y, mask, x_true, shapes, mu: float, iters: int, channels: int = 1, ckpt_every: int = 10,
+              relax: float = 2.0):
+        return _deconv_loss_fn().apply(lam, h, y, mask, x_true, tuple(map(tuple, shapes)), mu, iters, channels,
+                                       ckpt_every, relax)
+
+
+_LOSS_FN = None
+
+
+def _deconv_loss_fn():
+    global _LOSS_FN
+    if _LOSS_FN is None:
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, lam, h, y, mask, x_true, shapes, mu, iters, channels, ckpt_every, relax):
+                plan = Plan(list(shapes), h.detach(), mask, float(lam), mu, channels=channels, relax=relax)
+                try:
+                    loss, dlam, dh = plan.grad(y.detach(), x_true, iters, ckpt_every)
+                finally:
+                    plan.close()
+                ctx.save_for_backward(torch.tensor(dlam, dtype=h.dtype, device=h.device), dh)
+                return torch.tensor(loss, dtype=h.dtype, device=h.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                dlam, dh = ctx.saved_tensors
+                return (g * dlam, g * dh) + (None,) * 9
+
+        _LOSS_FN = _Fn
+    return _LOSS_FN

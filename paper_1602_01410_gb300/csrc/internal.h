@@ -35,7 +35,7 @@ struct ImageDesc {
 // forward: (Y_row, R_row) = row spectra of y~ and r; inverse: (X_row, HX_row).
 template <typename T> struct alignas(4 * sizeof(T)) cpair { T ar, ai, br, bi; };
 
-enum RowMode { ROW_ITER = 0, ROW_INIT = 1 };
+enum RowMode { ROW_ITER = 0, ROW_INIT = 1, ROW_ADJ = 2 };
 
 template <typename T> struct RowArgs {
   const ImageDesc *desc;
@@ -69,6 +69,10 @@ template <typename T> struct ColArgs {
   const T *s2;        // 4 sin^2 tables
   T mu;
   int *err;
+  // Reverse pass only (power-of-two column pass):
+  cpair<T> *spec_store;       // nullable: store (Y^, R^) after the forward column DFTs
+  const cpair<T> *spec_fwd;   // nullable: forward (Y^, R^) of the same step, with gacc
+  void *gacc;                 // cx<T> per (channel, k1, k2): accumulated h-gradient spectrum
 };
 
 // One launch of a pass over the images of one kernel class.
@@ -91,6 +95,45 @@ template <typename T>
 cudaError_t prepare_row(const LaunchCfg &c);
 template <typename T>
 cudaError_t prepare_col(const LaunchCfg &c);
+
+// Reverse pass (adjoint.cu, adjoint.cuh).
+enum AdjMode { ADJ_START = 0, ADJ_STEP = 1 };
+
+template <typename T> struct AdjArgs {
+  const ImageDesc *desc;
+  const int *cls_imgs;
+  int nimg;
+  const int *adj_begin;  // per image: first work item of this launch
+  int rb;                // rows per CTA
+  int mode;              // AdjMode
+  const T *bbuf;         // bb of step j+1 (ADJ_STEP)
+  const T *ab_in;        // ab of step j+1, (h, v) pairs (ADJ_STEP)
+  T *ab_out;             // ab of step j
+  T *ybar;               // in: yb of step j+1 (after C_{j+1}'s T~bb); out: yb'_j
+  const T *xs;           // x_{j+1}
+  const T *ds;           // d_j pairs
+  const T *xtrue;        // ADJ_START: ground truth for dL/dx
+  const uint32_t *mask;
+  const void *tw2;
+  cpair<T> *S_out;       // row spectra of tb + i xb
+  T mu, tau, relax, lscale;  // lscale = 2 / (number of pixels in the loss)
+  double *tpart;         // per work item: partial taub
+};
+
+
+template <typename T>
+cudaError_t launch_adj(const AdjArgs<T> &a, int tt, int C, int grid, int nt, size_t smem, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_adj(int tt, int C, size_t smem);
+template <typename T>
+cudaError_t launch_row_half(const RowArgs<T> &a, const LaunchCfg &c, int half, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sqerr(const T *x, const T *xt, long long n, double *part, int blocks, cudaStream_t s);
+cudaError_t launch_sum(const double *v, int n, double scale, double *out, cudaStream_t s);
+cudaError_t launch_add(double *acc, const double *v, cudaStream_t s);
+template <typename T>
+cudaError_t launch_taps(const ImageDesc *desc, int img, int Nh, int C, int K, const void *G, double *E, void *dh,
+                        int accumulate, cudaStream_t s);
 
 // Setup kernels (setup.cu).
 struct HhatJob {          // one half-spectrum to compute

@@ -71,6 +71,14 @@ cudaError_t launch_col(const ColArgs<T> &a, const LaunchCfg &c, cudaStream_t s) 
   return launch_ptr(col_ptr<T>(c), a, c, s);
 }
 
+// One half of a power-of-two row pass (0: inverse, 1: forward).  Kernels are
+// launched from the translation unit that opted them in to their shared
+// memory (each unit instantiates its own copy of a kernel template).
+template <typename T>
+cudaError_t launch_row_half(const RowArgs<T> &a, const LaunchCfg &c, int half, cudaStream_t s) {
+  return launch_ptr(row_ptr<T>(c, half), a, c, s);
+}
+
 // Opt in to the dynamic shared memory a class needs (above 48 KB).
 template <typename T>
 cudaError_t prepare_row(const LaunchCfg &c) {

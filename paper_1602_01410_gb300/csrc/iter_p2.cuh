@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
   const bool init = a.mode == ROW_INIT;
+  const bool adj = a.mode == ROW_ADJ;  // reverse pass: xbuf <- b, yt <- yt + T~b
   // Distinct buffers (x_out is written only when it is not the x buffer).
   T *__restrict__ yt = a.yt;
   T *__restrict__ xbuf = a.xbuf;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   T *Ys = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)ngroups * GS);  // [C][Rb][N]
   uint32_t *Ms = reinterpret_cast<uint32_t *>(Ys + (size_t)C * Rb * N);                        // [C][Rb][N/32]
 
-  if (!init) {
+  if (!init && !adj) {
     for (int c = 0; c < C; ++c) {
       copy_async<T>(Ys + (size_t)c * Rb * N, yt + px0 + c * P + (long long)r0 * N, nr * N, threadIdx.x, blockDim.x);
       copy_async<uint32_t>(Ms + (size_t)c * Rb * wpr, a.mask + Dp->mask + c * Dp->mask_plane + (long long)r0 * wpr,
@@ -117,7 +118,14 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   }
   cp_async_wait_all();
   __syncthreads();
-  if (active) {
+  if (active && adj) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int p = q + TT * p2_slot<TT>(r);
+      xbuf[rowp + p] = v[r].x;
+      yt[rowp + p] += v[r].y;
+    }
+  } else if (active) {
     const T relax = a.relax;
     const T *yrow = Ys + ((size_t)ch * Rb + hh) * N;
     const uint32_t *mrow = Ms + ((size_t)ch * Rb + hh) * wpr;
@@ -340,12 +348,37 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   if (lane_ok && scol < w) {
     const int ww = scol;
     const T s2w = S2s[M + ww];
+    cx<T> *gacc = a.gacc ? reinterpret_cast<cx<T> *>(a.gacc) + base : nullptr;
     for (int k1 = r0t; k1 < M; k1 += rstep) {
       const cx<T> hv = Hs[k1 * w + ww];
       const T den = hv.x * hv.x + hv.y * hv.y + mu * (S2s[k1] + s2w);
       const T inv = scale / den;
       const cx<T> Y = st[k1 * SL + 2 * ww], R = st[k1 * SL + 2 * ww + 1];
-      const cx<T> Xv = cscale<T>(cadd<T>(cmulc<T>(hv, Y), R), inv);
+      const cx<T> B = cadd<T>(cmulc<T>(hv, Y), R);  // den * (solution spectrum)
+      if (a.spec_store) {
+        cpair<T> o;
+        o.ar = Y.x;
+        o.ai = Y.y;
+        o.br = R.x;
+        o.bi = R.y;
+        a.spec_store[base + (long long)k1 * Nh + ww] = o;
+      }
+      if (gacc) {
+        // Reverse pass of the x-step and of T~x (gradient w.r.t. h): with the
+        // forward spectra Yf, Rf of this step, Xf = (conj(H) Yf + Rf)/den and
+        // the adjoint spectra Tb = Y, Bb = B/den,
+        //   G += conj(Bb) (Yf - H Xf) + conj(Xf) (Tb - H Bb).
+        const cpair<T> f = a.spec_fwd[base + (long long)k1 * Nh + ww];
+        const cx<T> Yf = mk<T>(f.ar, f.ai), Rf = mk<T>(f.br, f.bi);
+        const T rden = T(1) / den;
+        const cx<T> Xf = cscale<T>(cadd<T>(cmulc<T>(hv, Yf), Rf), rden);
+        const cx<T> Bb = cscale<T>(B, rden);
+        const cx<T> e1 = csub<T>(Yf, cmul<T>(hv, Xf)), e2 = csub<T>(Y, cmul<T>(hv, Bb));
+        cx<T> gv = gacc[(long long)k1 * Nh + ww];
+        gv = cadd<T>(gv, cadd<T>(cmulc<T>(Bb, e1), cmulc<T>(Xf, e2)));
+        gacc[(long long)k1 * Nh + ww] = gv;
+      }
+      const cx<T> Xv = cscale<T>(B, inv);
       st[k1 * SL + 2 * ww] = Xv;
       st[k1 * SL + 2 * ww + 1] = cmul<T>(hv, Xv);
     }

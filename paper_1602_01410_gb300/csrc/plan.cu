@@ -3,6 +3,7 @@
 // iteration driver (direct launches, or a cached CUDA graph of a fixed number
 // of iterations replayed on the caller's stream).
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -380,17 +381,26 @@ struct deconv_plan_s {
 
 namespace {
 
-#define CK(call)                                 \
-  do {                                           \
-    cudaError_t e_ = (call);                     \
-    if (e_ != cudaSuccess) return DECONV_ECUDA;  \
+// Last failing CUDA call of this thread, for deconv_last_error().
+thread_local char g_last_error[256] = "";
+
+deconv_status cuda_fail(cudaError_t e, int line) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at plan.cu:%d", cudaGetErrorName(e),
+                cudaGetErrorString(e), line);
+  return DECONV_ECUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, __LINE__);    \
   } while (0)
 
 template <typename T>
 RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_in, T *d_out, T *x_out,
                     double *partials) {
   const Layout &L = p->L;
-  RowArgs<T> a;
+  RowArgs<T> a{};
   a.desc = p->at<ImageDesc>(L.o_desc);
   a.cls_imgs = p->at<int>(c.o_imgs);
   a.nimg = (int)c.imgs.size();
@@ -417,7 +427,7 @@ RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_i
 template <typename T>
 ColArgs<T> col_args(const deconv_plan_s *p, const Cls &c) {
   const Layout &L = p->L;
-  ColArgs<T> a;
+  ColArgs<T> a{};
   a.desc = p->at<ImageDesc>(L.o_desc);
   a.cls_imgs = p->at<int>(c.o_imgs);
   a.nimg = (int)c.imgs.size();
@@ -622,6 +632,248 @@ deconv_status check_kernels(const void *h, const Layout &L, cudaStream_t s) {
 
 }  // namespace
 
+
+// ------------------------------------------------------------------ grad ---
+namespace {
+
+// Reverse-pass workspace (caller-owned, separate from the plan workspace).
+struct GradLayout {
+  int k = 1, nck = 0, items = 0;
+  std::vector<int> rb, grid, nt;      // per row class
+  std::vector<size_t> smem;
+  std::vector<int> adj_begin;         // per image
+  size_t o_ckyt, o_ckd, o_ckS, o_segX, o_segD, o_segSpec, o_bbuf, o_ybar, o_ab0, o_ab1, o_Sr0, o_Sr1, o_G, o_tpart,
+      o_lpart, o_E, o_res, o_xK, o_adjbeg, total;
+};
+
+constexpr int kLossBlocks = 256;
+
+size_t adj_smem(int C, int N, int rb, int tt, size_t esz) {
+  const size_t staged = (size_t)C * (2 * (rb + 2) + 4 * (rb + 1)) * N * esz;
+  const int groups = p2_row_threads(C, rb, tt) / tt;
+  const size_t tiles = (size_t)groups * p2_group_stride_h(tt) * 2 * esz;
+  return std::max(staged, tiles) + (size_t)groups * N * 2 * esz;
+}
+
+deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *G) {
+  const Layout &L = p->L;
+  if (iters < 1 || k < 1) return DECONV_EINVAL;
+  for (const auto *v : {&L.row_cls, &L.col_cls})
+    for (const Cls &c : *v)
+      if (c.cfg.kind != KIND_P2) return DECONV_EUNSUPPORTED;  // reverse pass: power-of-two sizes only
+  G->k = std::min(k, iters);
+  G->nck = (iters + G->k - 1) / G->k;
+  const int maxthr = L.esz == 4 ? 512 : 256;
+  G->adj_begin.assign(L.B, 0);
+  G->items = 0;
+  for (const Cls &c : L.row_cls) {
+    const ImageDesc &D0 = L.desc[c.imgs[0]];
+    const int tt = c.cfg.tt;
+    int rb = D0.Rb;
+    while (rb > 1 && (adj_smem(L.C, D0.N, rb, tt, L.esz) > kMaxSmem || p2_row_threads(L.C, rb, tt) > maxthr)) --rb;
+    if (adj_smem(L.C, D0.N, rb, tt, L.esz) > kMaxSmem) return DECONV_EUNSUPPORTED;
+    int grid = 0;
+    for (int j : c.imgs) {
+      G->adj_begin[j] = grid;
+      grid += (L.desc[j].M + rb - 1) / rb;
+    }
+    G->rb.push_back(rb);
+    G->grid.push_back(grid);
+    G->nt.push_back(p2_row_threads(L.C, rb, tt));
+    G->smem.push_back(adj_smem(L.C, D0.N, rb, tt, L.esz));
+    G->items = std::max(G->items, grid);
+  }
+  const size_t px = L.total_px * L.esz, spec = L.total_spec * 4 * L.esz;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = align_up(o + bytes);
+    return r;
+  };
+  G->o_ckyt = take(px * G->nck);
+  G->o_ckd = take(2 * px * G->nck);
+  G->o_ckS = take(spec * G->nck);
+  G->o_segX = take(px * G->k);
+  G->o_segD = take(2 * px * (G->k + 1));
+  G->o_segSpec = take(spec * G->k);
+  G->o_bbuf = take(px);
+  G->o_ybar = take(px);
+  G->o_ab0 = take(2 * px);
+  G->o_ab1 = take(2 * px);
+  G->o_Sr0 = take(spec);
+  G->o_Sr1 = take(spec);
+  G->o_G = take(L.total_spec * 2 * L.esz);
+  G->o_tpart = take((size_t)G->items * L.row_cls.size() * sizeof(double));
+  G->o_lpart = take(kLossBlocks * sizeof(double));
+  int maxKNh = 0;
+  for (const ImageDesc &D : L.desc) maxKNh = std::max(maxKNh, L.K * D.Nh);
+  G->o_E = take((size_t)maxKNh * 2 * sizeof(double));
+  G->o_res = take(4 * sizeof(double));
+  G->o_xK = take(px);
+  G->o_adjbeg = take(G->adj_begin.size() * sizeof(int));
+  G->total = o;
+  return DECONV_OK;
+}
+
+template <typename T>
+deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int iters, int k, char *gw,
+                     double *loss_h, double *dlambda_h, void *dh, void *x_out) {
+  const Layout &L = p->L;
+  GradLayout G;
+  deconv_status st = grad_layout(p, iters, k, &G);
+  if (st != DECONV_OK) return st;
+  k = G.k;
+  cudaStream_t s = p->stream;
+  const size_t px = L.total_px * sizeof(T), spec = L.total_spec * 4 * sizeof(T);
+  auto at = [&](size_t off) { return gw + off; };
+  CK(cudaMemcpyAsync(at(G.o_adjbeg), G.adj_begin.data(), G.adj_begin.size() * sizeof(int), cudaMemcpyHostToDevice,
+                     s));
+  for (size_t c = 0; c < L.row_cls.size(); ++c) CK(prepare_adj<T>(L.row_cls[c].cfg.tt, L.C, G.smem[c]));
+
+  // 1. Forward with checkpoints of (y~, d, forward spectrum) every k iterations.
+  st = init_state<T>(p, static_cast<const T *>(y), nullptr);
+  if (st != DECONV_OK) return st;
+  for (int c = 0; c < G.nck; ++c) {
+    CK(cudaMemcpyAsync(at(G.o_ckyt) + c * px, p->ws + L.o_yt, px, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(at(G.o_ckd) + 2 * c * px, dbuf<T>(p, p->parity), 2 * px, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(at(G.o_ckS) + c * spec, p->ws + L.o_Sa, spec, cudaMemcpyDeviceToDevice, s));
+    const int n = std::min(k, iters - c * k);
+    for (int it = 0; it < n; ++it) {
+      st = iterate<T>(p, s, nullptr, nullptr, 0, 0);
+      if (st != DECONV_OK) return st;
+    }
+  }
+  // x^{iters} is in the plan's x buffer.
+  CK(cudaMemcpyAsync(at(G.o_xK), p->ws + L.o_xbuf, px, cudaMemcpyDeviceToDevice, s));
+  if (x_out) CK(cudaMemcpyAsync(x_out, p->ws + L.o_xbuf, px, cudaMemcpyDeviceToDevice, s));
+  const long long npx = L.total_px;
+  CK(launch_sqerr<T>(reinterpret_cast<const T *>(at(G.o_xK)), static_cast<const T *>(x_true), npx,
+                     reinterpret_cast<double *>(at(G.o_lpart)), kLossBlocks, s));
+  double *res = reinterpret_cast<double *>(at(G.o_res));
+  CK(launch_sum(reinterpret_cast<const double *>(at(G.o_lpart)), kLossBlocks, 1.0 / (double)npx, res, s));
+
+  // 2. Reverse sweep, one checkpoint segment at a time.
+  CK(cudaMemsetAsync(res + 1, 0, 3 * sizeof(double), s));
+  CK(cudaMemsetAsync(at(G.o_G), 0, L.total_spec * 2 * sizeof(T), s));
+  CK(cudaMemsetAsync(at(G.o_tpart), 0, (size_t)G.items * L.row_cls.size() * sizeof(double), s));
+  int cur = 0;  // ab ping-pong
+  const ImageDesc *desc = p->at<ImageDesc>(L.o_desc);
+  for (int c = G.nck - 1; c >= 0; --c) {
+    const int s0 = c * k, s1 = std::min(s0 + k, iters);
+    CK(cudaMemcpyAsync(p->ws + L.o_yt, at(G.o_ckyt) + c * px, px, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(at(G.o_segD), at(G.o_ckd) + 2 * c * px, 2 * px, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p->ws + L.o_Sa, at(G.o_ckS) + c * spec, spec, cudaMemcpyDeviceToDevice, s));
+    // Forward recompute of the segment, storing x_{j+1}, d_j and the spectra of step j.
+    for (int j = s0; j < s1; ++j) {
+      const int jj = j - s0;
+      for (const Cls &cl : L.col_cls) {
+        ColArgs<T> ca = col_args<T>(p, cl);
+        ca.spec_store = reinterpret_cast<cpair<T> *>(at(G.o_segSpec) + jj * spec);
+        CK(launch_col<T>(ca, cl.cfg, s));
+      }
+      CK(row_pass<T>(p, s, ROW_ITER, reinterpret_cast<const T *>(at(G.o_segD) + 2 * jj * px),
+                     reinterpret_cast<T *>(at(G.o_segD) + 2 * (jj + 1) * px),
+                     reinterpret_cast<T *>(at(G.o_segX) + jj * px), nullptr));
+    }
+    // Reverse through the segment.
+    for (int j = s1 - 1; j >= s0; --j) {
+      const int jj = j - s0;
+      const bool start = (j == iters - 1);
+      if (!start) {
+        // C_{j+1} (first half): inverse row DFT of (bb, T~bb); yb += T~bb.
+        for (const Cls &cl : L.row_cls) {
+          RowArgs<T> ra = row_args<T>(p, cl, ROW_ADJ, nullptr, nullptr, nullptr, nullptr);
+          ra.S_in = reinterpret_cast<const cpair<T> *>(at(G.o_Sr1));
+          ra.xbuf = reinterpret_cast<T *>(at(G.o_bbuf));
+          ra.yt = reinterpret_cast<T *>(at(G.o_ybar));
+          CK(launch_row_half<T>(ra, cl.cfg, 0, s));
+        }
+      }
+      // C_{j+1} (second half) and A_j, forward row DFT of tb + i xb.
+      for (size_t ci = 0; ci < L.row_cls.size(); ++ci) {
+        const Cls &cl = L.row_cls[ci];
+        AdjArgs<T> aa{};
+        aa.desc = desc;
+        aa.cls_imgs = p->at<int>(cl.o_imgs);
+        aa.nimg = (int)cl.imgs.size();
+        aa.adj_begin = reinterpret_cast<const int *>(at(G.o_adjbeg));
+        aa.rb = G.rb[ci];
+        aa.mode = start ? ADJ_START : ADJ_STEP;
+        aa.bbuf = reinterpret_cast<const T *>(at(G.o_bbuf));
+        aa.ab_in = reinterpret_cast<const T *>(at(cur ? G.o_ab1 : G.o_ab0));
+        aa.ab_out = reinterpret_cast<T *>(at(cur ? G.o_ab0 : G.o_ab1));
+        aa.ybar = reinterpret_cast<T *>(at(G.o_ybar));
+        aa.xs = start ? reinterpret_cast<const T *>(at(G.o_xK)) : reinterpret_cast<const T *>(at(G.o_segX) + jj * px);
+        aa.ds = reinterpret_cast<const T *>(at(G.o_segD) + 2 * jj * px);
+        aa.xtrue = static_cast<const T *>(x_true);
+        aa.mask = p->at<uint32_t>(L.o_bits);
+        aa.tw2 = p->ws + L.o_tw2;
+        aa.S_out = reinterpret_cast<cpair<T> *>(at(G.o_Sr0));
+        aa.mu = (T)p->mu;
+        aa.tau = (T)(p->lambda / p->mu);
+        aa.relax = (T)p->relax;
+        aa.lscale = (T)(2.0 / (double)npx);
+        aa.tpart = reinterpret_cast<double *>(at(G.o_tpart)) + ci * G.items;
+        CK(launch_adj<T>(aa, cl.cfg.tt, L.C, G.grid[ci], G.nt[ci], G.smem[ci], s));
+      }
+      cur ^= 1;
+      // taub of this step (all classes; unused partial slots stay zero) into res[1], fixed order.
+      CK(launch_sum(reinterpret_cast<const double *>(at(G.o_tpart)), G.items * (int)L.row_cls.size(), 1.0, res + 2,
+                    s));
+      CK(launch_add(res + 1, res + 2, s));
+      // B_j: the x-step solve of the adjoint pair and the h-gradient spectrum.
+      for (const Cls &cl : L.col_cls) {
+        ColArgs<T> ca = col_args<T>(p, cl);
+        ca.S_in = reinterpret_cast<const cpair<T> *>(at(G.o_Sr0));
+        ca.S_out = reinterpret_cast<cpair<T> *>(at(G.o_Sr1));
+        ca.spec_fwd = reinterpret_cast<const cpair<T> *>(at(G.o_segSpec) + jj * spec);
+        ca.gacc = at(G.o_G);
+        CK(launch_col<T>(ca, cl.cfg, s));
+      }
+    }
+  }
+  // 3. dL/dh from the spectrum, dL/dlambda = taub / mu.
+  const int nk = L.kernel_per_image ? L.B : 1;
+  CK(cudaMemsetAsync(dh, 0, (size_t)nk * L.K * L.K * sizeof(T), s));
+  for (int j = 0; j < L.B; ++j) {
+    T *dhj = static_cast<T *>(dh) + (L.kernel_per_image ? (size_t)j * L.K * L.K : 0);
+    CK(launch_taps<T>(desc, j, L.desc[j].Nh, L.C, L.K, at(G.o_G), reinterpret_cast<double *>(at(G.o_E)), dhj, 1, s));
+  }
+  double hres[2] = {0, 0};
+  CK(cudaMemcpyAsync(hres, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *loss_h = hres[0];
+  *dlambda_h = hres[1] / p->mu;
+  p->have_state = true;
+  return DECONV_OK;
+}
+
+}  // namespace
+
+extern "C" deconv_status deconv_grad_workspace_size(deconv_plan p, int32_t iters, int32_t ckpt_every, size_t *bytes) {
+  if (!p || !bytes) return DECONV_EINVAL;
+  GradLayout G;
+  deconv_status st = grad_layout(p, iters, ckpt_every, &G);
+  if (st != DECONV_OK) return st;
+  *bytes = G.total;
+  return DECONV_OK;
+}
+
+extern "C" deconv_status deconv_grad(deconv_plan p, const void *y, const void *x_true, int32_t iters,
+                                     int32_t ckpt_every, void *grad_ws, size_t grad_ws_bytes, double *loss,
+                                     double *dlambda, void *dh, void *x_out) {
+  if (!p || !y || !x_true || !grad_ws || !loss || !dlambda || !dh) return DECONV_EINVAL;
+  if (reinterpret_cast<uintptr_t>(grad_ws) % kAlign != 0) return DECONV_EINVAL;
+  GradLayout G;
+  deconv_status st = grad_layout(p, iters, ckpt_every, &G);
+  if (st != DECONV_OK) return st;
+  if (grad_ws_bytes < G.total) return DECONV_ENOMEM;
+  return p->L.dtype == DECONV_F32
+             ? grad_t<float>(p, y, x_true, iters, ckpt_every, static_cast<char *>(grad_ws), loss, dlambda, dh, x_out)
+             : grad_t<double>(p, y, x_true, iters, ckpt_every, static_cast<char *>(grad_ws), loss, dlambda, dh,
+                              x_out);
+}
+
 extern "C" {
 
 deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes) {
@@ -745,6 +997,8 @@ deconv_status deconv_plan_destroy(deconv_plan p) {
   delete p;
   return DECONV_OK;
 }
+
+const char *deconv_last_error(void) { return g_last_error; }
 
 const char *deconv_status_string(deconv_status s) {
   switch (s) {

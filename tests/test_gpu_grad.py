@@ -1,0 +1,107 @@
+"""GPU reverse pass (deconv_grad) against the FP64 oracle's reverse pass on
+the same seeded inputs: loss, dL/dlambda and dL/dh (every tap), for one and
+three channels, batches sharing one kernel, and several checkpoint
+intervals; the autograd wrapper; and the full-size differentiation workload
+(512 x 512, 15 x 15 Gaussian, 20% missing, 100 iterations, checkpoints
+every 10) on two images."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_01410_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def gpu_grad(prob, iters, ckpt):
+    import torch
+    import paper_1602_01410_gb300 as pkg
+    dev = torch.device("cuda:0")
+    dt = torch.float32 if prob.dtype == "f32" else torch.float64
+    h = torch.tensor(prob.h, dtype=dt, device=dev)
+    mask = torch.tensor(np.concatenate([m.ravel() for m in prob.mask]), dtype=torch.uint8, device=dev)
+    y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=dt, device=dev)
+    xt = torch.tensor(np.concatenate([a.ravel() for a in prob.x_true]), dtype=dt, device=dev)
+    plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu, channels=prob.channels)
+    loss, dlam, dh = plan.grad(y, xt, iters, ckpt)
+    assert plan.sync() == 0
+    plan.close()
+    return loss, dlam, dh.double().cpu().numpy()
+
+
+def oracle_grad(prob, iters):
+    n = [a.size for a in prob.x_true]
+    tot = float(sum(n))
+    L = dl = 0.0
+    dh = np.zeros_like(prob.h)
+    for j in range(len(prob.shapes)):
+        l, a, g, _ = oracle.admm_grad(prob.y[j], prob.mask[j], prob.h, prob.lam, prob.mu, iters, prob.x_true[j],
+                                      round_f32=prob.dtype == "f32")
+        w = n[j] / tot
+        L += w * l
+        dl += w * a
+        dh += w * g
+    return L, dl, dh
+
+
+def check(prob, iters, ckpt, rtol, ltol=1e-5):
+    """ltol: loss tolerance (1e-5 for a few iterations; the full-run FP32
+    tolerance 1e-3 after 100 iterations).  rtol: gradient tolerance relative
+    to |dL/dlambda| and to max |dL/dh|."""
+    L, dl, dh = gpu_grad(prob, iters, ckpt)
+    Lo, dlo, dho = oracle_grad(prob, iters)
+    el, edl, edh = abs(L - Lo) / abs(Lo), abs(dl - dlo) / abs(dlo), np.max(np.abs(dh - dho)) / np.max(np.abs(dho))
+    print(f"{prob.name} iters {iters}: loss rel {el:.2e}, dlambda rel {edl:.2e}, dh rel {edh:.2e}")
+    assert el <= ltol
+    assert edl <= rtol
+    assert edh <= rtol
+    return L, dl, dh
+
+
+def test_grad_small_one_channel_partial_segment():
+    prob = inputs.random_problem(51, [(64, 64)], 5, mask_kind="random", frac=0.3, iters=7, lam=2e-3, mu=2e-2)
+    check(prob, 7, 3, 2e-3)
+
+
+def test_grad_batch_shared_kernel_and_checkpoint_invariance():
+    prob = inputs.random_problem(52, [(64, 128), (128, 64)], 7, mask_kind="random", frac=0.2, iters=6,
+                                 lam=1e-3, mu=2e-2)
+    a = check(prob, 6, 2, 2e-3)
+    for ck in (1, 6):
+        b = gpu_grad(prob, 6, ck)
+        assert np.isclose(a[0], b[0], rtol=1e-6) and np.isclose(a[1], b[1], rtol=1e-4)
+        assert np.max(np.abs(a[2] - b[2])) <= 1e-4 * np.max(np.abs(a[2]))
+
+
+def test_grad_vectorial_tv():
+    prob = inputs.random_problem(53, [(64, 64)], 5, mask_kind="bayer", channels=3, iters=5, lam=2e-3, mu=2e-2)
+    check(prob, 5, 5, 2e-3)
+
+
+def test_autograd_function():
+    import torch
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(54, [(64, 64)], 5, mask_kind="random", frac=0.3, iters=4, lam=2e-3, mu=2e-2)
+    dev = torch.device("cuda:0")
+    lam = torch.tensor(prob.lam, dtype=torch.float32, device=dev, requires_grad=True)
+    h = torch.tensor(prob.h, dtype=torch.float32, device=dev, requires_grad=True)
+    mask = torch.tensor(prob.mask[0].ravel(), dtype=torch.uint8, device=dev)
+    y = torch.tensor(prob.y[0].ravel(), dtype=torch.float32, device=dev)
+    xt = torch.tensor(prob.x_true[0].ravel(), dtype=torch.float32, device=dev)
+    loss = pkg.DeconvLoss.apply(lam, h, y, mask, xt, prob.shapes, prob.mu, 4)
+    (3.0 * loss).backward()
+    Lo, dlo, dho = oracle_grad(prob, 4)
+    assert abs(float(loss) - Lo) <= 1e-5 * Lo
+    assert abs(float(lam.grad) - 3 * dlo) <= 2e-3 * abs(3 * dlo)
+    assert np.max(np.abs(h.grad.double().cpu().numpy() - 3 * dho)) <= 2e-3 * np.max(np.abs(3 * dho))
+
+
+def test_grad_fullsize_differentiation_workload():
+    prob = inputs.config_c5(count=2)
+    check(prob, prob.iters, 10, 1e-2, ltol=1e-3)
