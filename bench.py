@@ -119,6 +119,113 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+# ----------------------------------------------------------------- plain ---
+# The plain comparison path: one image at a time, cuFFT (torch.fft) for every
+# transform and separate torch elementwise/stencil ops for every step of the
+# iteration (no fusion, no packing of real transforms).  Used only as a timed
+# comparison; the library never calls it.
+
+
+def plain_setup(prob, j, dev, dt):
+    import torch
+    M, N = prob.shapes[j]
+    K = prob.ksize
+    b = K // 2
+    hg = torch.zeros((M, N), dtype=dt, device=dev)
+    hk = torch.tensor(prob.h, dtype=dt, device=dev)
+    for p in range(-b, b + 1):
+        for q in range(-b, b + 1):
+            hg[p % M, q % N] += hk[p + b, q + b]
+    H = torch.fft.rfft2(hg)
+    k1 = torch.arange(M, device=dev, dtype=dt)[:, None]
+    k2 = torch.arange(N // 2 + 1, device=dev, dtype=dt)[None, :]
+    D2 = 4 * torch.sin(torch.pi * k1 / M) ** 2 + 4 * torch.sin(torch.pi * k2 / N) ** 2
+    den = H.real ** 2 + H.imag ** 2 + prob.mu * D2
+    return H, den
+
+
+def plain_init(y, m, K):
+    """Initial fill (border padding, mean of the observed values elsewhere)."""
+    import torch
+    C, M, N = y.shape
+    b = K // 2
+    obs = m != 0
+    mean = (y * obs).sum(dim=(1, 2), keepdim=True) / obs.sum(dim=(1, 2), keepdim=True).clamp(min=1)
+    ii = torch.arange(M, device=y.device).clamp(b, M - b - 1)
+    jj = torch.arange(N, device=y.device).clamp(b, N - b - 1)
+    yc, oc = y[:, ii][:, :, jj], obs[:, ii][:, :, jj]
+    band = torch.ones((M, N), dtype=torch.bool, device=y.device)
+    band[b:M - b, b:N - b] = False
+    fill = torch.where(band[None] & oc, yc, mean.expand_as(y))
+    return torch.where(obs, y, fill)
+
+
+def plain_iterate(yt, d, v, y, m, H, den, lam, mu, relax, iters):
+    import torch
+    obs = m != 0
+    tau = lam / mu
+    x = None
+    for _ in range(iters):
+        u = v - d
+        dtu = (torch.roll(u[:, 0], 1, 2) - u[:, 0]) + (torch.roll(u[:, 1], 1, 1) - u[:, 1])
+        rhs = torch.fft.irfft2(torch.conj(H) * torch.fft.rfft2(yt), s=yt.shape[-2:]) + mu * dtu
+        x = torch.fft.irfft2(torch.fft.rfft2(rhs) / den, s=yt.shape[-2:])
+        t = torch.fft.irfft2(H * torch.fft.rfft2(x), s=yt.shape[-2:])
+        yt = torch.where(obs, yt, relax * t - (relax - 1) * yt)
+        dx = torch.stack([torch.roll(x, -1, 2) - x, torch.roll(x, -1, 1) - x], 1)
+        a = dx + d
+        nrm = torch.sqrt((a * a).sum(dim=(0, 1), keepdim=True))
+        v = a * torch.clamp(1 - tau / torch.clamp(nrm, min=1e-30), min=0)
+        d = a - v
+    return x, yt, d, v
+
+
+def plain_solve(prob, iters, dev, dt):
+    import torch
+    out = []
+    for j in range(len(prob.shapes)):
+        H, den = plain_setup(prob, j, dev, dt)
+        y = torch.tensor(prob.y[j], dtype=dt, device=dev)
+        m = torch.tensor(prob.mask[j], device=dev)
+        yt = plain_init(y, m, prob.ksize)
+        v = torch.stack([torch.roll(yt, -1, 2) - yt, torch.roll(yt, -1, 1) - yt], 1)
+        d = torch.zeros_like(v)
+        x, _, _, _ = plain_iterate(yt, d, v, y, m, H, den, prob.lam, prob.mu, prob.relax, iters)
+        out.append(x)
+    return out
+
+
+def plain_grad(prob, iters, dev, dt):
+    """torch.autograd through the unrolled plain iteration: loss and gradients."""
+    import torch
+    lam = torch.tensor(prob.lam, dtype=dt, device=dev, requires_grad=True)
+    hk = torch.tensor(prob.h, dtype=dt, device=dev, requires_grad=True)
+    n_all = float(sum(a.size for a in prob.x_true))
+    loss = 0.0
+    for j in range(len(prob.shapes)):
+        M, N = prob.shapes[j]
+        K = prob.ksize
+        b = K // 2
+        idx_i = torch.tensor([p % M for p in range(-b, b + 1)], device=dev)
+        idx_j = torch.tensor([q % N for q in range(-b, b + 1)], device=dev)
+        hg = torch.zeros((M, N), dtype=dt, device=dev).index_put((idx_i[:, None], idx_j[None, :]), hk)
+        H = torch.fft.rfft2(hg)
+        k1 = torch.arange(M, device=dev, dtype=dt)[:, None]
+        k2 = torch.arange(N // 2 + 1, device=dev, dtype=dt)[None, :]
+        den = H.real ** 2 + H.imag ** 2 + prob.mu * (4 * torch.sin(torch.pi * k1 / M) ** 2 +
+                                                     4 * torch.sin(torch.pi * k2 / N) ** 2)
+        y = torch.tensor(prob.y[j], dtype=dt, device=dev)
+        m = torch.tensor(prob.mask[j], device=dev)
+        yt = plain_init(y, m, K)
+        v = torch.stack([torch.roll(yt, -1, 2) - yt, torch.roll(yt, -1, 1) - yt], 1)
+        d = torch.zeros_like(v)
+        x, _, _, _ = plain_iterate(yt, d, v, y, m, H, den, lam, prob.mu, prob.relax, iters)
+        xt = torch.tensor(prob.x_true[j], dtype=dt, device=dev)
+        loss = loss + ((x - xt) ** 2).sum() / n_all
+    loss.backward()
+    return float(loss), float(lam.grad), hk.grad.detach()
+
+
 def measured_peak_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -186,6 +293,9 @@ def main():
     ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--ref-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-plain", action="store_true",
+                    help="also time the plain per-image cuFFT path (torch.autograd for c5)")
+    ap.add_argument("--plain-iters", type=int, default=20)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -227,8 +337,20 @@ def main():
     f_unobs = float(1.0 - mask_np.mean())
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    grad_mode = args.config == "c5"
+    if grad_mode:
+        x_true = torch.tensor(np.concatenate([a.ravel() for a in prob.x_true]), dtype=dt, device=dev)
+        gws_n = pkg.deconv_grad_workspace_size(plan.handle, prob.iters, 10)
+        gws = torch.empty(gws_n + 256, dtype=torch.uint8, device=dev)
+        gptr = gws.data_ptr() + (-gws.data_ptr()) % 256
+        dh = torch.empty_like(h)
+
     def step():
-        plan.solve(y, prob.iters, x=x)
+        if grad_mode:
+            pkg.deconv_grad(plan.handle, y.data_ptr(), x_true.data_ptr(), prob.iters, 10, gptr, gws_n, dh.data_ptr(),
+                            x.data_ptr())
+        else:
+            plan.solve(y, prob.iters, x=x)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -263,7 +385,7 @@ def main():
     units = px * prob.iters * args.steps * world
     value = units / (t_ms / 1e3) / 1e6
 
-    # End to end through the host-buffer entry point.
+    # End to end through the host-buffer entry point (forward solve).
     y_host = torch.tensor(y_np, dtype=dt).pin_memory()
     x_host = torch.empty_like(y_host).pin_memory()
     plan.solve_host(y_host, x_host, prob.iters)
@@ -308,6 +430,26 @@ def main():
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
+    if grad_mode:
+        out["config"]["step"] = ("deconv_grad: forward with checkpoints every 10 iterations, loss, reverse pass "
+                                 "(dL/dlambda, dL/dh); value counts forward iterations")
+        out["e2e"]["note"] = "e2e times the forward solve through deconv_solve_host"
+    if args.compare_plain:
+        n_it = min(prob.iters, args.plain_iters)
+        for _ in range(2):
+            (plain_grad(prob, 2, dev, dt) if grad_mode else plain_solve(prob, 2, dev, dt))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        if grad_mode:
+            plain_grad(prob, n_it, dev, dt)
+        else:
+            plain_solve(prob, n_it, dev, dt)
+        torch.cuda.synchronize(dev)
+        pt = time.perf_counter() - t0
+        pv = px * n_it / pt / 1e6
+        out["plain"] = {"value": pv, "unit": "Mpx*iter/s", "iterations": n_it, "speedup": value / pv,
+                        "what": ("torch.autograd through the unrolled per-image torch.fft iteration" if grad_mode
+                                 else "per-image torch.fft (cuFFT) transforms and unfused torch ops")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.config)
     if rank == 0:
