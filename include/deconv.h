@@ -165,6 +165,18 @@ deconv_status deconv_solve_noalloc(const deconv_dims *dims, const void *h, const
  * deconv_solve).  Synchronises the stream. */
 deconv_status deconv_profile_passes(deconv_plan plan, int32_t iters, float *ms_host);
 
+/* Checkpoint / resume of the iteration state (Sec. II-B: the state carried
+ * from one iteration to the next is y~ = [y; z], the scaled dual d_x and the
+ * right-hand side of the next x-step).  The state is exported as an opaque
+ * device blob of deconv_state_bytes() bytes (caller-owned, 16-byte aligned)
+ * holding y~, d_x and the plan's forward row spectra; deconv_state_set
+ * restores it into a plan of the same geometry, after which
+ * deconv_solve(warm = 1) continues exactly where the saved plan stood.
+ * Asynchronous device-to-device copies on the plan's stream. */
+deconv_status deconv_state_bytes(deconv_plan plan, size_t *bytes);
+deconv_status deconv_state_get(deconv_plan plan, void *blob);
+deconv_status deconv_state_set(deconv_plan plan, const void *blob);
+
 /* Wait for the plan's stream and report device-side errors recorded since
  * the last call (DECONV_ENONFINITE, DECONV_ETIMEOUT), then clear them. */
 deconv_status deconv_sync(deconv_plan plan);

@@ -28,7 +28,8 @@ DECONV_F32, DECONV_F64 = 0, 1
 # Entry points declared in include/deconv.h (checked by the test suite).
 EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "deconv_solve_host",
            "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
-           "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error")
+           "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
+           "deconv_state_bytes", "deconv_state_get", "deconv_state_set")
 
 
 class DeconvError(RuntimeError):
@@ -70,6 +71,9 @@ def load() -> ctypes.CDLL:
         lib.deconv_plan_destroy.argtypes = [vp]
         lib.deconv_status_string.argtypes = [ctypes.c_int]
         lib.deconv_status_string.restype = ctypes.c_char_p
+        lib.deconv_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.deconv_state_get.argtypes = [vp, vp]
+        lib.deconv_state_set.argtypes = [vp, vp]
         lib.deconv_last_error.argtypes = []
         lib.deconv_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -163,6 +167,20 @@ def deconv_grad(plan: int, y_ptr: int, xtrue_ptr: int, iters: int, ckpt_every: i
     return loss.value, dlam.value
 
 
+def deconv_state_bytes(plan: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().deconv_state_bytes(plan, ctypes.byref(n)), "deconv_state_bytes")
+    return n.value
+
+
+def deconv_state_get(plan: int, blob_ptr: int) -> None:
+    _check(load().deconv_state_get(plan, blob_ptr), "deconv_state_get")
+
+
+def deconv_state_set(plan: int, blob_ptr: int) -> None:
+    _check(load().deconv_state_set(plan, blob_ptr), "deconv_state_set")
+
+
 def deconv_plan_destroy(plan: int) -> None:
     _check(load().deconv_plan_destroy(plan), "deconv_plan_destroy")
 
@@ -225,6 +243,16 @@ class Plan:
 
     def profile_passes(self, iters: int):
         return deconv_profile_passes(self.handle, iters)
+
+    def state_get(self):
+        """Opaque device checkpoint of the iteration state (uint8 tensor)."""
+        blob = self._torch.empty(deconv_state_bytes(self.handle), dtype=self._torch.uint8,
+                                 device=self.workspace.device)
+        deconv_state_get(self.handle, blob.data_ptr())
+        return blob
+
+    def state_set(self, blob) -> None:
+        deconv_state_set(self.handle, blob.data_ptr())
 
     def sync(self) -> int:
         return deconv_sync(self.handle)

@@ -998,6 +998,45 @@ deconv_status deconv_plan_destroy(deconv_plan p) {
   return DECONV_OK;
 }
 
+static size_t state_parts(const deconv_plan_s *p, size_t *yt, size_t *d, size_t *sa) {
+  *yt = p->L.total_px * p->L.esz;
+  *d = 2 * *yt;
+  *sa = p->L.total_spec * 4 * p->L.esz;
+  return *yt + *d + *sa;
+}
+
+deconv_status deconv_state_bytes(deconv_plan p, size_t *bytes) {
+  if (!p || !bytes) return DECONV_EINVAL;
+  size_t a, b, c;
+  *bytes = state_parts(p, &a, &b, &c);
+  return DECONV_OK;
+}
+
+deconv_status deconv_state_get(deconv_plan p, void *blob) {
+  if (!p || !blob || (reinterpret_cast<uintptr_t>(blob) & 15)) return DECONV_EINVAL;
+  if (!p->have_state) return DECONV_EINVAL;
+  size_t a, b, c;
+  state_parts(p, &a, &b, &c);
+  char *o = static_cast<char *>(blob);
+  CK(cudaMemcpyAsync(o, p->ws + p->L.o_yt, a, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemcpyAsync(o + a, p->ws + (p->parity ? p->L.o_d1 : p->L.o_d0), b, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemcpyAsync(o + a + b, p->ws + p->L.o_Sa, c, cudaMemcpyDeviceToDevice, p->stream));
+  return DECONV_OK;
+}
+
+deconv_status deconv_state_set(deconv_plan p, const void *blob) {
+  if (!p || !blob || (reinterpret_cast<uintptr_t>(blob) & 15)) return DECONV_EINVAL;
+  size_t a, b, c;
+  state_parts(p, &a, &b, &c);
+  const char *o = static_cast<const char *>(blob);
+  CK(cudaMemcpyAsync(p->ws + p->L.o_yt, o, a, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->ws + p->L.o_d0, o + a, b, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->ws + p->L.o_Sa, o + a + b, c, cudaMemcpyDeviceToDevice, p->stream));
+  p->parity = 0;
+  p->have_state = true;
+  return DECONV_OK;
+}
+
 const char *deconv_last_error(void) { return g_last_error; }
 
 const char *deconv_status_string(deconv_status s) {

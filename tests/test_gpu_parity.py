@@ -179,3 +179,21 @@ def test_generic_passes_on_pow2_sizes(monkeypatch):
     xg, _, _ = gpu_solve(prob)
     xo, _ = oracle_solve(prob)
     assert rel_l2(xg, xo) <= 1e-5
+
+
+def test_checkpoint_resume_in_another_plan():
+    import paper_1602_01410_gb300 as pkg
+    import torch
+    prob = inputs.random_problem(26, [(64, 64), (48, 60)], 5, mask_kind="random", frac=0.3, iters=9)
+    full, _, _ = gpu_solve(prob)
+    _, _, plan = gpu_solve(prob, iters=5)
+    blob = plan.state_get()
+    dev = torch.device("cuda:0")
+    plan2 = pkg.Plan(prob.shapes, torch.tensor(prob.h, dtype=torch.float32, device=dev),
+                     torch.tensor(np.concatenate([m.ravel() for m in prob.mask]), dtype=torch.uint8, device=dev),
+                     prob.lam, prob.mu)
+    plan2.state_set(blob)
+    x = plan2.solve(None, 4, warm=True)
+    assert plan2.sync() == 0
+    flat = np.concatenate([a.ravel() for a in full])
+    assert np.array_equal(x.double().cpu().numpy(), flat)
