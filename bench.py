@@ -430,7 +430,7 @@ def main():
     peak, peak_kind = measured_peak_hbm()
     dom, ms_dom = ("row", ms_row) if ms_row >= ms_col else ("col", ms_col)
     achieved = per_px[dom] * px / (ms_dom / 1e3) / 1e9
-    launches_per_step = 3 + 2 * prob.iters
+    launches_per_step = pkg.deconv_kernel_launches(plan.handle, prob.iters, 1 if grad_mode else 0, 10)
 
     out = {
         "metric": "Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": world, "steps": args.steps,

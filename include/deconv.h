@@ -177,6 +177,12 @@ deconv_status deconv_state_bytes(deconv_plan plan, size_t *bytes);
 deconv_status deconv_state_get(deconv_plan plan, void *blob);
 deconv_status deconv_state_set(deconv_plan plan, const void *blob);
 
+/* Diagnostic (no counterpart in the paper): number of kernel launches that
+ * deconv_solve(plan, y, x, iters, warm = 0, NULL) (mode 0) or
+ * deconv_grad(plan, ..., iters, ckpt_every, ...) (mode 1) issues.  Host only. */
+deconv_status deconv_kernel_launches(deconv_plan plan, int32_t iters, int32_t mode, int32_t ckpt_every,
+                                     int64_t *count);
+
 /* Wait for the plan's stream and report device-side errors recorded since
  * the last call (DECONV_ENONFINITE, DECONV_ETIMEOUT), then clear them. */
 deconv_status deconv_sync(deconv_plan plan);

@@ -29,7 +29,7 @@ DECONV_F32, DECONV_F64 = 0, 1
 EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "deconv_solve_host",
            "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
-           "deconv_state_bytes", "deconv_state_get", "deconv_state_set")
+           "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches")
 
 
 class DeconvError(RuntimeError):
@@ -72,6 +72,7 @@ def load() -> ctypes.CDLL:
         lib.deconv_status_string.argtypes = [ctypes.c_int]
         lib.deconv_status_string.restype = ctypes.c_char_p
         lib.deconv_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.deconv_kernel_launches.argtypes = [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_int64)]
         lib.deconv_state_get.argtypes = [vp, vp]
         lib.deconv_state_set.argtypes = [vp, vp]
         lib.deconv_last_error.argtypes = []
@@ -165,6 +166,13 @@ def deconv_grad(plan: int, y_ptr: int, xtrue_ptr: int, iters: int, ckpt_every: i
     _check(load().deconv_grad(plan, y_ptr, xtrue_ptr, int(iters), int(ckpt_every), gws_ptr, gws_bytes,
                               ctypes.byref(loss), ctypes.byref(dlam), dh_ptr, x_out_ptr), "deconv_grad")
     return loss.value, dlam.value
+
+
+def deconv_kernel_launches(plan: int, iters: int, mode: int = 0, ckpt_every: int = 10) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().deconv_kernel_launches(plan, int(iters), int(mode), int(ckpt_every), ctypes.byref(n)),
+           "deconv_kernel_launches")
+    return n.value
 
 
 def deconv_state_bytes(plan: int) -> int:

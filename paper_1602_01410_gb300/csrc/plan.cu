@@ -1037,6 +1037,27 @@ deconv_status deconv_state_set(deconv_plan p, const void *blob) {
   return DECONV_OK;
 }
 
+deconv_status deconv_kernel_launches(deconv_plan p, int32_t iters, int32_t mode, int32_t ckpt_every,
+                                     int64_t *count) {
+  if (!p || !count || iters < 0 || (mode != 0 && mode != 1)) return DECONV_EINVAL;
+  const Layout &L = p->L;
+  long long row = 0, col = (long long)L.col_cls.size();
+  for (const Cls &c : L.row_cls) row += c.cfg.kind == KIND_P2 ? 2 : 1;
+  const long long init = 3 + row;  // observed means (2 kernels), initial fill, initial row pass
+  const long long per_iter = col + row;
+  if (mode == 0) {
+    *count = init + (long long)iters * per_iter;
+    return DECONV_OK;
+  }
+  if (iters < 1 || ckpt_every < 1) return DECONV_EINVAL;
+  const long long nrc = (long long)L.row_cls.size();
+  // forward + loss (2) + recompute (iters steps) + reverse per step:
+  // inverse halves (not on the first), adjoint stencils, 2 reductions, column passes; taps (2 per image).
+  *count = init + (long long)iters * per_iter + 2 + (long long)iters * per_iter +
+           (long long)(iters - 1) * nrc + (long long)iters * (nrc + 2 + col) + 2LL * L.B;
+  return DECONV_OK;
+}
+
 const char *deconv_last_error(void) { return g_last_error; }
 
 const char *deconv_status_string(deconv_status s) {
