@@ -234,6 +234,65 @@ __device__ __forceinline__ void fft_p2(cx<T> (&v)[32], cx<T> *tile, int q, unsig
 }
 
 // ---------------------------------------------------------------------------
+// Mixed transform of length L = R * L2, L2 = 32 TT, R in {1, 3, 5}, by R
+// groups of TT threads (decimation in time: x[R n2 + r] -> F_r).  Group gr
+// enters with v[m] = x[R (q + TT m) + gr] and leaves with
+// v[j] = X[q + TT p2_slot(j) + L2 gr].  Steps: the L2-point transform of its
+// sub-sequence (fft_p2), the twiddle w^(gr k2) (table tw3 laid out [r][k2],
+// w = exp(-2 pi i / L), conjugated for the inverse) into the exchange buffer
+// E (L complex, this transform's), and the R-point combine
+// X[k2 + L2 s] = sum_r E[r][k2] exp(SIGN 2 pi i r s / R) for s = gr.
+// Contains __syncthreads when R > 1: every thread of the CTA must call it
+// (threads of inactive groups with active = false).
+template <typename T, int R, int SIGN> __device__ __forceinline__ cx<T> root_r(int j) {
+  // exp(SIGN 2 pi i j / R) for R = 3, 5 (exact constants)
+  if constexpr (R == 3) {
+    const T s3 = T(0.86602540378443864676);
+    return j == 0 ? mk<T>(T(1), T(0)) : (j == 1 ? mk<T>(T(-0.5), SIGN * s3) : mk<T>(T(-0.5), -SIGN * s3));
+  } else {
+    const T c1 = T(0.30901699437494742410), s1 = T(0.95105651629515357212);
+    const T c2 = T(-0.80901699437494742410), s2 = T(0.58778525229247312917);
+    switch (j) {
+      case 0: return mk<T>(T(1), T(0));
+      case 1: return mk<T>(c1, SIGN * s1);
+      case 2: return mk<T>(c2, SIGN * s2);
+      case 3: return mk<T>(c2, -SIGN * s2);
+      default: return mk<T>(c1, -SIGN * s1);
+    }
+  }
+}
+
+template <typename T, int TT, int R, int SIGN>
+__device__ __forceinline__ void fft_mixed(cx<T> (&v)[32], bool active, cx<T> *tile, int q, unsigned gmask, int gr,
+                                          const cx<T> *__restrict__ tw2, const cx<T> *__restrict__ tw3, cx<T> *E) {
+  constexpr int L2 = 32 * TT;
+  if (active) fft_p2<T, TT, SIGN>(v, tile, q, gmask, tw2);
+  if constexpr (R > 1) {
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int k2 = q + TT * p2_slot<TT>(j);
+        cx<T> w = __ldg(&tw3[gr * L2 + k2]);
+        if (SIGN > 0) w.y = -w.y;
+        E[gr * L2 + k2] = cmul<T>(v[j], w);
+      }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int k2 = q + TT * p2_slot<TT>(j);
+        cx<T> acc = E[k2];
+#pragma unroll
+        for (int r = 1; r < R; ++r) acc = cadd<T>(acc, cmul<T>(E[r * L2 + k2], root_r<T, R, SIGN>((r * gr) % R)));
+        v[j] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // One radix-R Stockham pass over S signals of length L held in buf.  The
 // host plans S * L <= 30 NT so that every butterfly has a register slot.
 template <typename T, int NT, int R, int SIGN>

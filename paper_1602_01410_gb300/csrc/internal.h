@@ -27,7 +27,8 @@ struct ImageDesc {
   long long mask_plane;  // words per channel plane
   int tw_row, tw_col;    // twiddle-table offsets for lengths N and M
   int s2_row, s2_col;    // 4 sin^2(pi k / L) table offsets for N and M
-  int tw2_row, tw2_col;  // [k1][t] twiddle-table offsets (power-of-two lengths), -1 if none
+  int tw2_row, tw2_col;  // [k1][t] twiddle-table offsets of the power-of-two (sub-)length, -1 if none
+  int tw3_row, tw3_col;  // [r][k2] twiddles exp(-2 pi i r k2 / L) of a length R * 2^k, -1 if none
   FftSched sched_row, sched_col;
 };
 
@@ -79,7 +80,8 @@ template <typename T> struct ColArgs {
 enum KernelKind { KIND_GENERIC = 0, KIND_P2 = 1 };
 struct LaunchCfg {
   int kind;      // KernelKind
-  int tt;        // KIND_P2: threads per transform (length / 32)
+  int tt;        // KIND_P2: threads per sub-transform (sub-length / 32)
+  int r;         // KIND_P2: length = r * 32 * tt, r in {1, 3, 5}
   int nt;        // threads per CTA
   int channels;  // 1 or 3
   int grid;      // CTAs

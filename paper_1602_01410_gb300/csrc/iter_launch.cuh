@@ -11,22 +11,41 @@ namespace dcv {
 // 512-thread generic CTAs exist for FP32 only (FP64 registers would spill).
 template <typename T> constexpr int kMaxNt = sizeof(T) == 4 ? 512 : 256;
 
-// Power-of-two row pass: half 0 = inverse (R1), half 1 = forward (R2).
+// Power-of-two and R * 2^k row passes: half 0 = inverse (R1), half 1 = forward (R2).
+template <typename T, int TT, int C, int R>
+static const void *row_p2_one(int half) {
+  return half ? (const void *)row_fwd_p2_kernel<T, TT, C, R> : (const void *)row_inv_p2_kernel<T, TT, C, R>;
+}
+
 template <typename T, int C>
-static const void *row_p2_ptr(int tt, int half) {
-  switch (tt) {
-    case 2: return half ? (const void *)row_fwd_p2_kernel<T, 2, C> : (const void *)row_inv_p2_kernel<T, 2, C>;
-    case 4: return half ? (const void *)row_fwd_p2_kernel<T, 4, C> : (const void *)row_inv_p2_kernel<T, 4, C>;
-    case 8: return half ? (const void *)row_fwd_p2_kernel<T, 8, C> : (const void *)row_inv_p2_kernel<T, 8, C>;
-    case 16: return half ? (const void *)row_fwd_p2_kernel<T, 16, C> : (const void *)row_inv_p2_kernel<T, 16, C>;
-    case 32: return half ? (const void *)row_fwd_p2_kernel<T, 32, C> : (const void *)row_inv_p2_kernel<T, 32, C>;
+static const void *row_p2_ptr(int tt, int r, int half) {
+  if (r == 1) {
+    switch (tt) {
+      case 2: return row_p2_one<T, 2, C, 1>(half);
+      case 4: return row_p2_one<T, 4, C, 1>(half);
+      case 8: return row_p2_one<T, 8, C, 1>(half);
+      case 16: return row_p2_one<T, 16, C, 1>(half);
+      case 32: return row_p2_one<T, 32, C, 1>(half);
+    }
+  } else if (r == 3) {
+    switch (tt) {
+      case 4: return row_p2_one<T, 4, C, 3>(half);
+      case 8: return row_p2_one<T, 8, C, 3>(half);
+      case 16: return row_p2_one<T, 16, C, 3>(half);
+    }
+  } else if (r == 5) {
+    switch (tt) {
+      case 4: return row_p2_one<T, 4, C, 5>(half);
+      case 8: return row_p2_one<T, 8, C, 5>(half);
+      case 16: return row_p2_one<T, 16, C, 5>(half);
+    }
   }
   return nullptr;
 }
 
 template <typename T>
 static const void *row_ptr(const LaunchCfg &c, int half = 0) {
-  if (c.kind == KIND_P2) return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt, half) : row_p2_ptr<T, 1>(c.tt, half);
+  if (c.kind == KIND_P2) return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt, c.r, half) : row_p2_ptr<T, 1>(c.tt, c.r, half);
   if (c.nt == 512 && kMaxNt<T> == 512)
     return c.channels == 3 ? (const void *)row_pass_kernel<T, kMaxNt<T>, 3> : (const void *)row_pass_kernel<T, kMaxNt<T>, 1>;
   if (c.nt == 256)
@@ -37,12 +56,26 @@ static const void *row_ptr(const LaunchCfg &c, int half = 0) {
 template <typename T>
 static const void *col_ptr(const LaunchCfg &c) {
   if (c.kind == KIND_P2) {
-    switch (c.tt) {
-      case 2: return (const void *)col_pass_p2_kernel<T, 2>;
-      case 4: return (const void *)col_pass_p2_kernel<T, 4>;
-      case 8: return (const void *)col_pass_p2_kernel<T, 8>;
-      case 16: return (const void *)col_pass_p2_kernel<T, 16>;
-      case 32: return (const void *)col_pass_p2_kernel<T, 32>;
+    if (c.r == 1) {
+      switch (c.tt) {
+        case 2: return (const void *)col_pass_p2_kernel<T, 2, 1>;
+        case 4: return (const void *)col_pass_p2_kernel<T, 4, 1>;
+        case 8: return (const void *)col_pass_p2_kernel<T, 8, 1>;
+        case 16: return (const void *)col_pass_p2_kernel<T, 16, 1>;
+        case 32: return (const void *)col_pass_p2_kernel<T, 32, 1>;
+      }
+    } else if (c.r == 3) {
+      switch (c.tt) {
+        case 4: return (const void *)col_pass_p2_kernel<T, 4, 3>;
+        case 8: return (const void *)col_pass_p2_kernel<T, 8, 3>;
+        case 16: return (const void *)col_pass_p2_kernel<T, 16, 3>;
+      }
+    } else if (c.r == 5) {
+      switch (c.tt) {
+        case 4: return (const void *)col_pass_p2_kernel<T, 4, 5>;
+        case 8: return (const void *)col_pass_p2_kernel<T, 8, 5>;
+        case 16: return (const void *)col_pass_p2_kernel<T, 16, 5>;
+      }
     }
     return nullptr;
   }

@@ -55,18 +55,24 @@ template <int TT> __device__ __forceinline__ constexpr int p2_unslot(int m) {
   return (m % (32 / TT)) * TT + m / (32 / TT);
 }
 
+// All three kernels below handle L = R * 32 * TT (R in {1, 3, 5}): a
+// transform of length L is done by R groups of TT threads (fft_mixed); with
+// R = 1 it is fft_p2 alone.  Work item layout: group g of a CTA serves
+// (channel ch, row hh) = (g / R) split as ch = (g / R) / Rb, hh = (g / R) % Rb,
+// and sub-transform gr = g % R.
+
 // ----------------------------------------------------------- row (R1) ---
-// Inverse half of the row pass: one group of TT threads per (channel, row),
-// Rb rows per CTA, no halo.  Inverse row DFT of X + i HX -> x, T~x; z-update
-// of y~; x to the plan's x buffer (read by R2) and optionally to x_out.
-// The CTA's y~ rows and mask words are staged into shared memory
-// asynchronously while the transforms run.  Statistics: ||dz||^2 and the
-// data-fit half of the objective.
-// Shared memory: [transpose tiles][y~ rows C x Rb][mask words C x Rb].
-template <typename T, int TT, int C>
+// Inverse half of the row pass: Rb rows per CTA, no halo.  Inverse row DFT
+// of X + i HX -> x, T~x; z-update of y~; x to the plan's x buffer (read by
+// R2) and optionally to x_out.  The CTA's y~ rows and mask words are staged
+// into shared memory asynchronously while the transforms run.  Statistics:
+// ||dz||^2 and the data-fit half of the objective.  ROW_ADJ (reverse pass):
+// xbuf <- b, yt <- yt + T~b instead of the z-update.
+// Shared memory: [transpose tiles][exchange C x Rb x N][y~ C x Rb x N][mask words].
+template <typename T, int TT, int C, int R>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>();
+  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb, wpr = N / 32;
@@ -75,7 +81,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
   const int ngroups = blockDim.x / TT;
-  const int ch = g / Rb, hh = g - ch * Rb;
+  const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
   const bool init = a.mode == ROW_INIT;
@@ -85,8 +91,11 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   T *__restrict__ xbuf = a.xbuf;
   T *__restrict__ xout = (a.x_out && a.x_out != a.xbuf) ? a.x_out : nullptr;
   cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
-  T *Ys = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)ngroups * GS);  // [C][Rb][N]
-  uint32_t *Ms = reinterpret_cast<uint32_t *>(Ys + (size_t)C * Rb * N);                        // [C][Rb][N/32]
+  cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)ngroups * GS;           // [C*Rb][N] exchange
+  T *Ys = reinterpret_cast<T *>(Ex + (R > 1 ? (size_t)C * Rb * N : 0));              // [C][Rb][N]
+  uint32_t *Ms = reinterpret_cast<uint32_t *>(Ys + (size_t)C * Rb * N);              // [C][Rb][N/32]
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
 
   if (!init && !adj) {
     for (int c = 0; c < C; ++c) {
@@ -104,44 +113,44 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   if (active) {
     if (init) {
 #pragma unroll
-      for (int r = 0; r < 32; ++r) v[r] = mk<T>(yt[rowp + q + TT * p2_slot<TT>(r)], T(0));
+      for (int j = 0; j < 32; ++j) v[j] = mk<T>(yt[rowp + q + TT * p2_slot<TT>(j) + L2 * gr], T(0));
     } else {
       const cpair<T> *src = a.S_in + Dp->spec + ((long long)ch * M + i) * Nh;
 #pragma unroll
       for (int m = 0; m < 32; ++m) {
-        const int n = q + TT * m;
+        const int n = R * (q + TT * m) + gr;
         const cpair<T> c = src[2 * n <= N ? n : N - n];
         v[m] = 2 * n <= N ? mk<T>(c.ar - c.bi, c.ai + c.br) : mk<T>(c.ar + c.bi, c.br - c.ai);
       }
-      fft_p2<T, TT, +1>(v, tile, q, group_mask(TT), reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row);
     }
   }
+  if (!init) fft_mixed<T, TT, R, +1>(v, active, tile, q, group_mask(TT), gr, tw2, tw3, Ex + (size_t)row_id * N);
   cp_async_wait_all();
   __syncthreads();
   if (active && adj) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int p = q + TT * p2_slot<TT>(r);
-      xbuf[rowp + p] = v[r].x;
-      yt[rowp + p] += v[r].y;
+    for (int j = 0; j < 32; ++j) {
+      const int p = q + TT * p2_slot<TT>(j) + L2 * gr;
+      xbuf[rowp + p] = v[j].x;
+      yt[rowp + p] += v[j].y;
     }
   } else if (active) {
     const T relax = a.relax;
     const T *yrow = Ys + ((size_t)ch * Rb + hh) * N;
     const uint32_t *mrow = Ms + ((size_t)ch * Rb + hh) * wpr;
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int p = q + TT * p2_slot<TT>(r);
-      xbuf[rowp + p] = v[r].x;
-      if (xout) xout[rowp + p] = v[r].x;
+    for (int j = 0; j < 32; ++j) {
+      const int p = q + TT * p2_slot<TT>(j) + L2 * gr;
+      xbuf[rowp + p] = v[j].x;
+      if (xout) xout[rowp + p] = v[j].x;
       if (!init) {
         const T yo = yrow[p];
         if (!((mrow[p >> 5] >> (p & 31)) & 1u)) {
-          const T yn = relax * v[r].y - (relax - T(1)) * yo;
+          const T yn = relax * v[j].y - (relax - T(1)) * yo;
           yt[rowp + p] = yn;
           if (stats) s_dz += (yn - yo) * (yn - yo);
         } else if (stats) {
-          s_fit += (yo - v[r].y) * (yo - v[r].y);
+          s_fit += (yo - v[j].y) * (yo - v[j].y);
         }
       }
     }
@@ -158,20 +167,20 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
 }
 
 // ----------------------------------------------------------- row (R2) ---
-// Forward half: one group per (channel, row).  The CTA stages x (rows
-// r0-1 .. r1), d (rows r0-1 .. r1-1) and y~ (rows r0 .. r1-1) of every
-// channel into shared memory with one batch of asynchronous copies.  From
-// them: the prox factor g at (i,p), (i,p-1), (i-1,p) (norm over channels),
-// d^{i+1} = (1-g) a, r = mu D^T (v - d^{i+1}) with v - d^{i+1} = (2g - 1) a;
-// then the forward row DFT of y~ + i r, split into (Y_row, R_row).
-// Statistics: ||dd||^2 and the TV half of the objective.
+// Forward half.  The CTA stages x (rows r0-1 .. r1), d (rows r0-1 .. r1-1)
+// and y~ (rows r0 .. r1-1) of every channel into shared memory with one
+// batch of asynchronous copies.  From them: the prox factor g at (i,p),
+// (i,p-1), (i-1,p) (norm over channels), d^{i+1} = (1-g) a,
+// r = mu D^T (v - d^{i+1}) with v - d^{i+1} = (2g - 1) a; then the forward
+// row DFT of y~ + i r, split into (Y_row, R_row).  Statistics: ||dd||^2 and
+// the TV half of the objective.
 // Shared memory: [x C x (Rb+2) rows][d C x (Rb+1) rows][y~ C x Rb rows] (the
-// transpose tiles reuse it after a barrier), then one row of y~ + i r per
-// group.
-template <typename T, int TT, int C>
+// transpose tiles reuse it after a barrier), then per row y~ + i r and the
+// exchange buffer.
+template <typename T, int TT, int C, int R>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>();
+  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb;
@@ -179,17 +188,21 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   const int r0 = blk * Rb, nr = min(Rb, M - r0);
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
-  const int ch = g / Rb, hh = g - ch * Rb;
+  const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
   const bool init = a.mode == ROW_INIT;
   cx<T> *__restrict__ dout = reinterpret_cast<cx<T> *>(a.d_out);
-  T *Xs = reinterpret_cast<T *>(smem_raw);                      // [C][Rb+2][N]
+  T *Xs = reinterpret_cast<T *>(smem_raw);                               // [C][Rb+2][N]
   cx<T> *Ds = reinterpret_cast<cx<T> *>(Xs + (size_t)C * (Rb + 2) * N);  // [C][Rb+1][N]
   T *Ys = reinterpret_cast<T *>(Ds + (size_t)C * (Rb + 1) * N);           // [C][Rb][N]
   const size_t staged = (size_t)C * ((Rb + 2) + 2 * (Rb + 1) + Rb) * N * sizeof(T);
   const size_t tiles = (size_t)(blockDim.x / TT) * GS * sizeof(cx<T>);
-  cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)g * N;
+  cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)row_id * N;
+  cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)C * Rb * N +
+              (size_t)row_id * N;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
 
   for (int c = 0; c < C; ++c) {
     for (int k = 0; k < nr + 2; ++k)
@@ -213,7 +226,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   if (active) {
 #pragma unroll 4
     for (int m = 0; m < 32; ++m) {
-      const int p = q + TT * m;
+      const int p = q + TT * m + L2 * gr;
       const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
       T s0 = T(0), sl = T(0), su = T(0), tv = T(0);
       T ah0 = T(0), av0 = T(0), ahl = T(0), avu = T(0), dh0 = T(0), dv0 = T(0);
@@ -261,19 +274,24 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   }
   if (!finite) atomicOr(a.err, 1);
   __syncthreads();  // the transpose tiles below reuse the staged rows
+  cx<T> v[32];
   if (active) {
-    cx<T> v[32];
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = Cs[q + TT * m];
-    cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
-    const unsigned gm = group_mask(TT);
-    fft_p2<T, TT, -1>(v, tile, q, gm, reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row);
+    for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+  }
+  if (R > 1) __syncthreads();  // every group has read its inputs before outputs overwrite Cs
+  cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
+  const unsigned gm = group_mask(TT);
+  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  if (active) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) tile[q + TT * p2_slot<TT>(r)] = v[r];
-    __syncwarp(gm);
+    for (int j = 0; j < 32; ++j) Cs[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
+  }
+  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  if (active) {
     cpair<T> *__restrict__ dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
-    for (int k = q; k < Nh; k += TT) {
-      const cx<T> c1 = tile[k], c2 = tile[k == 0 ? 0 : N - k];
+    for (int k = q + TT * gr; k < Nh; k += TT * R) {
+      const cx<T> c1 = Cs[k], c2 = Cs[k == 0 ? 0 : N - k];
       cpair<T> o;
       o.ar = T(0.5) * (c1.x + c2.x);
       o.ai = T(0.5) * (c1.y - c2.y);
@@ -294,10 +312,14 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
 }
 
 // --------------------------------------------------------------- column ---
-template <typename T, int TT>
+// One set of R groups per signal (Y or R of one spectral column) of a tile of
+// W columns; the tile, the H^ tile and the sin^2 tables are staged with
+// cp.async.  Shared memory: [staging M x SL][transpose tiles][H^ tile]
+// [sin^2][exchange 2W x M].
+template <typename T, int TT, int R>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>();
+  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, false)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh;
@@ -306,15 +328,18 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   const int k20 = t * Dp->W, w = min(Dp->W, Nh - k20);
   const int SL = (2 * Dp->W) | 1;  // staging row stride (complex)
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_col;
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_col;
   const cx<T> *H = reinterpret_cast<const cx<T> *>(a.hhat) + Dp->hhat;
   const T *s2c = a.s2 + Dp->s2_col, *s2r = a.s2 + Dp->s2_row;
   cx<T> *st = reinterpret_cast<cx<T> *>(smem_raw);  // [M][SL]
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
   const unsigned gm = group_mask(TT);
   const int ngroups = blockDim.x / TT;
+  const int gr = g % R, sig = g / R;
   cx<T> *tile = st + (size_t)M * SL + (size_t)g * GS;
   cx<T> *Hs = st + (size_t)M * SL + (size_t)ngroups * GS;  // [M][W] H^ tile
   T *S2s = reinterpret_cast<T *>(Hs + (size_t)M * Dp->W);  // [M] column sin^2, then [W] row sin^2
+  cx<T> *Ex = reinterpret_cast<cx<T> *>(S2s + ((M + Dp->W + 3) & ~3)) + (size_t)sig * M;
   const long long base = Dp->spec + (long long)ch * M * Nh + k20;
   const int nthr = blockDim.x;
 
@@ -335,13 +360,16 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   cp_async_wait_all();
   __syncthreads();
   cx<T> v[32];
-  const bool active = g < 2 * w;
+  const bool active = sig < 2 * w;
   if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = st[(q + TT * m) * SL + g];
-    fft_p2<T, TT, -1>(v, tile, q, gm, tw2);
+    for (int m = 0; m < 32; ++m) v[m] = st[(R * (q + TT * m) + gr) * SL + sig];
+  }
+  if (R > 1) __syncthreads();
+  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  if (active) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) st[(q + TT * p2_slot<TT>(r)) * SL + g] = v[r];
+    for (int j = 0; j < 32; ++j) st[(q + TT * p2_slot<TT>(j) + L2 * gr) * SL + sig] = v[j];
   }
   __syncthreads();
   const T mu = a.mu, scale = T(1) / (T(M) * T(N));
@@ -353,14 +381,14 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
       const cx<T> hv = Hs[k1 * w + ww];
       const T den = hv.x * hv.x + hv.y * hv.y + mu * (S2s[k1] + s2w);
       const T inv = scale / den;
-      const cx<T> Y = st[k1 * SL + 2 * ww], R = st[k1 * SL + 2 * ww + 1];
-      const cx<T> B = cadd<T>(cmulc<T>(hv, Y), R);  // den * (solution spectrum)
+      const cx<T> Y = st[k1 * SL + 2 * ww], Rv = st[k1 * SL + 2 * ww + 1];
+      const cx<T> B = cadd<T>(cmulc<T>(hv, Y), Rv);  // den * (solution spectrum)
       if (a.spec_store) {
         cpair<T> o;
         o.ar = Y.x;
         o.ai = Y.y;
-        o.br = R.x;
-        o.bi = R.y;
+        o.br = Rv.x;
+        o.bi = Rv.y;
         a.spec_store[base + (long long)k1 * Nh + ww] = o;
       }
       if (gacc) {
@@ -386,10 +414,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   __syncthreads();
   if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = st[(q + TT * m) * SL + g];
-    fft_p2<T, TT, +1>(v, tile, q, gm, tw2);
+    for (int m = 0; m < 32; ++m) v[m] = st[(R * (q + TT * m) + gr) * SL + sig];
+  }
+  if (R > 1) __syncthreads();
+  fft_mixed<T, TT, R, +1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  if (active) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) st[(q + TT * p2_slot<TT>(r)) * SL + g] = v[r];
+    for (int j = 0; j < 32; ++j) st[(q + TT * p2_slot<TT>(j) + L2 * gr) * SL + sig] = v[j];
   }
   __syncthreads();
   if (lane_ok && scol < w) {

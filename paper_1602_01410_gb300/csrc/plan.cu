@@ -74,32 +74,52 @@ struct Layout {
 
 bool is_pow2_32(int L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
 
-// Power-of-two row passes (inverse and forward halves): rb rows per CTA, one
-// group of tt threads per (channel, row), rounded up to whole warps; shared
-// memory holds one transpose tile per group.
-int p2_row_threads(int C, int rb, int tt) {
-  const int per_warp = 32 / tt;
-  return (C * rb + per_warp - 1) / per_warp * per_warp * tt;
+// Register-FFT parameters of a length: L = r * 32 * tt with (tt, r) = (L/32, 1)
+// for powers of two 64..1024, or r in {3, 5} and 32 * tt in {128, 256, 512}.
+bool reg_fft_params(int L, int *tt, int *r) {
+  if (is_pow2_32(L)) {
+    *tt = L / 32;
+    *r = 1;
+    return true;
+  }
+  for (int rr : {3, 5})
+    if (L % rr == 0) {
+      const int L2 = L / rr;
+      if (L2 >= 128 && L2 <= 512 && (L2 & (L2 - 1)) == 0) {
+        *tt = L2 / 32;
+        *r = rr;
+        return true;
+      }
+    }
+  return false;
 }
 
-size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz) {
-  const size_t tiles = (size_t)(p2_row_threads(C, rb, tt) / tt) * p2_group_stride_h(tt) * 2 * esz;
-  const size_t inv = tiles + (size_t)C * rb * N * esz + (size_t)C * rb * (N / 32) * 4;            // inverse half
+// Register-FFT row passes (inverse and forward halves): rb rows per CTA, r
+// groups of tt threads per (channel, row), rounded up to whole warps.
+int p2_row_threads(int C, int rb, int tt, int r = 1) {
+  const int per_warp = 32 / tt;
+  return (C * rb * r + per_warp - 1) / per_warp * per_warp * tt;
+}
+
+size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz, int r = 1) {
+  const size_t tiles = (size_t)(p2_row_threads(C, rb, tt, r) / tt) * p2_group_stride_h(tt) * 2 * esz;
+  const size_t ex = r > 1 ? (size_t)C * rb * N * 2 * esz : 0;
+  const size_t inv = tiles + ex + (size_t)C * rb * N * esz + (size_t)C * rb * (N / 32) * 4;  // inverse half
   const size_t fwd = std::max((size_t)C * ((rb + 2) + 2 * (rb + 1) + rb) * N * esz, tiles) +
-                     (size_t)(p2_row_threads(C, rb, tt) / tt) * N * 2 * esz;                     // forward half
+                     (size_t)C * rb * N * 2 * esz + ex;                                     // forward half
   return std::max(inv, fwd);
 }
 
-// Column pass (power of two): staging tile + transpose tiles + H^ tile + sin^2 tables.
-size_t p2_col_smem(int M, int w, int tt, size_t esz) {
-  const int per_warp = 32 / tt, groups = (2 * w + per_warp - 1) / per_warp * per_warp;
+// Column pass: staging tile + transpose tiles + H^ tile + sin^2 tables + exchange.
+size_t p2_col_smem(int M, int w, int tt, size_t esz, int r = 1) {
+  const int per_warp = 32 / tt, groups = (2 * w * r + per_warp - 1) / per_warp * per_warp;
   return (size_t)M * ((2 * w) | 1) * 2 * esz + (size_t)groups * p2_group_stride_h(tt) * 2 * esz +
-         (size_t)M * w * 2 * esz + (size_t)(M + w) * esz;
+         (size_t)M * w * 2 * esz + (size_t)((M + w + 3) & ~3) * esz + (r > 1 ? (size_t)2 * w * M * 2 * esz : 0);
 }
 
-int p2_col_threads(int w, int tt) {
+int p2_col_threads(int w, int tt, int r = 1) {
   const int per_warp = 32 / tt;
-  return (2 * w + per_warp - 1) / per_warp * per_warp * tt;
+  return (2 * w * r + per_warp - 1) / per_warp * per_warp * tt;
 }
 
 // Row-block height and column-tile width for one image under CTA size nt.
@@ -154,22 +174,26 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   }
   const int maxthr = L.esz == 4 ? 512 : 256;
   const bool allow_p2 = env_int("DECONV_GENERIC", 0) == 0;
-  // Kernel class of every image and pass: the power-of-two passes for lengths
-  // 64..1024 that fit, the generic Stockham passes otherwise.
-  std::vector<int> row_tt(L.B, 0), col_tt(L.B, 0);
-  long long g_rows = 0, g_cols = 0, p2_rows[33] = {0}, p2_cols[33] = {0};
+  // Kernel class of every image and pass: the register-FFT passes for the
+  // lengths reg_fft_params accepts (key tt * 8 + r), the generic Stockham
+  // passes otherwise (key 0).
+  std::vector<int> row_key(L.B, 0), col_key(L.B, 0);
+  long long g_rows = 0, g_cols = 0;
+  std::map<int, long long> p2_rows, p2_cols;
   for (int j = 0; j < L.B; ++j) {
     const int M = d->rows[j], N = d->cols[j];
-    if (allow_p2 && is_pow2_32(N) && p2_row_threads(L.C, 1, N / 32) <= maxthr &&
-        p2_row_smem(L.C, N, 1, N / 32, L.esz) <= kMaxSmem) {
-      row_tt[j] = N / 32;
-      p2_rows[N / 32] += M;
+    int tt, r;
+    if (allow_p2 && reg_fft_params(N, &tt, &r) && p2_row_threads(L.C, 1, tt, r) <= maxthr &&
+        p2_row_smem(L.C, N, 1, tt, L.esz, r) <= kMaxSmem) {
+      row_key[j] = tt * 8 + r;
+      p2_rows[row_key[j]] += M;
     } else {
       g_rows += M;
     }
-    if (allow_p2 && is_pow2_32(M) && p2_col_smem(M, 1, M / 32, L.esz) <= kMaxSmem) {
-      col_tt[j] = M / 32;
-      p2_cols[M / 32] += (long long)L.C * (N / 2 + 1);
+    if (allow_p2 && reg_fft_params(M, &tt, &r) && p2_col_threads(1, tt, r) <= maxthr &&
+        p2_col_smem(M, 1, tt, L.esz, r) <= kMaxSmem) {
+      col_key[j] = tt * 8 + r;
+      p2_cols[col_key[j]] += (long long)L.C * (N / 2 + 1);
     } else {
       g_cols += (long long)L.C * (N / 2 + 1);
     }
@@ -185,7 +209,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     if (nt != 256 && !(nt == 512 && L.esz == 4)) continue;
     bool all = true;
     for (int j = 0; j < L.B && all; ++j) {
-      if (row_tt[j] && col_tt[j]) continue;
+      if (row_key[j] && col_key[j]) continue;
       int rb, w;
       all = fit_image(d->rows[j], d->cols[j], L.C, nt, L.esz, rb_pref, w_pref, &rb, &w);
     }
@@ -196,41 +220,43 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     }
   }
   if (!ok) return DECONV_EUNSUPPORTED;
-  // Class parameters: rows per CTA / columns per CTA aiming at `target` CTAs.
-  int p2_rb[33] = {0}, p2_w[33] = {0};
-  for (int tt = 2; tt <= 32; tt *= 2) {
-    const int N = 32 * tt;
-    if (p2_rows[tt]) {
-      const int rtarget = env_int("DECONV_P2_ROW_CTAS", 152);
-      int rb = (int)std::max<long long>(1, (p2_rows[tt] + rtarget - 1) / rtarget);
-      rb = env_int("DECONV_P2_ROW_BLOCK", rb);
-      while (rb > 1 && (p2_row_threads(L.C, rb, tt) > maxthr || p2_row_smem(L.C, N, rb, tt, L.esz) > kMaxSmem)) --rb;
-      p2_rb[tt] = rb;
-    }
+  // Class parameters: rows per CTA / columns per CTA aiming at one CTA per SM.
+  std::map<int, int> p2_rb, p2_w;
+  for (const auto &kv : p2_rows) {
+    const int tt = kv.first / 8, r = kv.first % 8, N = r * 32 * tt;
+    const int rtarget = env_int("DECONV_P2_ROW_CTAS", 152);
+    int rb = (int)std::max<long long>(1, (kv.second + rtarget - 1) / rtarget);
+    rb = env_int("DECONV_P2_ROW_BLOCK", rb);
+    while (rb > 1 &&
+           (p2_row_threads(L.C, rb, tt, r) > maxthr || p2_row_smem(L.C, N, rb, tt, L.esz, r) > kMaxSmem))
+      --rb;
+    p2_rb[kv.first] = rb;
   }
   int p2w_all = 1;
   {
     long long tot = 0;
-    for (int tt = 2; tt <= 32; tt *= 2) tot += p2_cols[tt];
+    for (const auto &kv : p2_cols) tot += kv.second;
     const int ctarget = env_int("DECONV_P2_COL_CTAS", 152);
     p2w_all = (int)std::max<long long>(1, (tot + ctarget - 1) / ctarget);
     p2w_all = env_int("DECONV_P2_COL_TILE", p2w_all);
   }
-  for (int tt = 2; tt <= 32; tt *= 2) {
-    if (!p2_cols[tt]) continue;
+  for (const auto &kv : p2_cols) {
+    const int tt = kv.first / 8, r = kv.first % 8, M = r * 32 * tt;
     int w = std::min(p2w_all, 16);
-    while (w > 1 && (p2_col_threads(w, tt) > maxthr || p2_col_smem(32 * tt, w, tt, L.esz) > kMaxSmem)) --w;
-    p2_w[tt] = w;
+    while (w > 1 && (p2_col_threads(w, tt, r) > maxthr || p2_col_smem(M, w, tt, L.esz, r) > kMaxSmem)) --w;
+    p2_w[kv.first] = w;
   }
 
-  // Class lists (generic first, then by threads per transform).
-  auto class_index = [](std::vector<Cls> &v, int kind, int tt) {
+  // Class lists (in order of first appearance).
+  auto class_index = [](std::vector<Cls> &v, int kind, int key) {
+    const int tt = key / 8, r = key % 8;
     for (size_t k = 0; k < v.size(); ++k)
-      if (v[k].cfg.kind == kind && v[k].cfg.tt == tt) return (int)k;
+      if (v[k].cfg.kind == kind && v[k].cfg.tt == tt && v[k].cfg.r == r) return (int)k;
     Cls c;
     std::memset(&c.cfg, 0, sizeof(c.cfg));
     c.cfg.kind = kind;
     c.cfg.tt = tt;
+    c.cfg.r = r;
     v.push_back(c);
     return (int)v.size() - 1;
   };
@@ -245,13 +271,13 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     D.Nh = D.N / 2 + 1;
     D.C = L.C;
     int grb = 0, gw = 0;
-    if (!(row_tt[j] && col_tt[j])) fit_image(D.M, D.N, L.C, L.nt, L.esz, rb_pref, w_pref, &grb, &gw);
-    D.Rb = row_tt[j] ? p2_rb[row_tt[j]] : grb;
-    D.W = col_tt[j] ? p2_w[col_tt[j]] : gw;
+    if (!(row_key[j] && col_key[j])) fit_image(D.M, D.N, L.C, L.nt, L.esz, rb_pref, w_pref, &grb, &gw);
+    D.Rb = row_key[j] ? p2_rb[row_key[j]] : grb;
+    D.W = col_key[j] ? p2_w[col_key[j]] : gw;
     D.row_blocks = (D.M + D.Rb - 1) / D.Rb;
     D.col_tiles = (D.Nh + D.W - 1) / D.W;
-    Cls &rc = L.row_cls[class_index(L.row_cls, row_tt[j] ? KIND_P2 : KIND_GENERIC, row_tt[j])];
-    Cls &cc = L.col_cls[class_index(L.col_cls, col_tt[j] ? KIND_P2 : KIND_GENERIC, col_tt[j])];
+    Cls &rc = L.row_cls[class_index(L.row_cls, row_key[j] ? KIND_P2 : KIND_GENERIC, row_key[j])];
+    Cls &cc = L.col_cls[class_index(L.col_cls, col_key[j] ? KIND_P2 : KIND_GENERIC, col_key[j])];
     D.row_begin = rc.cfg.grid;
     D.col_begin = cc.cfg.grid;
     rc.cfg.grid += D.row_blocks;
@@ -262,17 +288,17 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     L.total_row_items += D.row_blocks;
     L.row_grid += D.row_blocks;
     L.col_grid += L.C * D.col_tiles;
-    if (row_tt[j]) {
-      rc.cfg.nt = p2_row_threads(L.C, D.Rb, row_tt[j]);
-      rc.cfg.smem = std::max(rc.cfg.smem, p2_row_smem(L.C, D.N, D.Rb, row_tt[j], L.esz));
+    if (row_key[j]) {
+      rc.cfg.nt = p2_row_threads(L.C, D.Rb, rc.cfg.tt, rc.cfg.r);
+      rc.cfg.smem = std::max(rc.cfg.smem, p2_row_smem(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r));
     } else {
       rc.cfg.nt = L.nt;
       const size_t ldr = (size_t)((L.C * (D.Rb + 2)) | 1);
       rc.cfg.smem = std::max(rc.cfg.smem, (size_t)D.N * ldr * 2 * L.esz + (size_t)(D.Rb + 1) * D.N * L.esz);
     }
-    if (col_tt[j]) {
-      cc.cfg.nt = p2_col_threads(D.W, col_tt[j]);
-      cc.cfg.smem = std::max(cc.cfg.smem, p2_col_smem(D.M, D.W, col_tt[j], L.esz));
+    if (col_key[j]) {
+      cc.cfg.nt = p2_col_threads(D.W, cc.cfg.tt, cc.cfg.r);
+      cc.cfg.smem = std::max(cc.cfg.smem, p2_col_smem(D.M, D.W, cc.cfg.tt, L.esz, cc.cfg.r));
     } else {
       cc.cfg.nt = L.nt;
       cc.cfg.smem = std::max(cc.cfg.smem, (size_t)D.M * (size_t)((2 * D.W) | 1) * 2 * L.esz);
@@ -317,14 +343,25 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     D.tw_col = L.tw_off[D.M];
     D.s2_row = L.s2_off[D.N];
     D.s2_col = L.s2_off[D.M];
-    D.tw2_row = D.tw2_col = -1;
-    for (int len : {D.M, D.N})
-      if (is_pow2_32(len) && !L.tw2_off.count(len)) {
-        L.tw2_off[len] = (int)L.total_tw2;
+    // [k1][t] tables of the power-of-two (sub-)lengths and [r][k2] tables of
+    // the R * 2^k lengths share one array (tw2_off keyed by length, tw3 by -length).
+    D.tw2_row = D.tw2_col = D.tw3_row = D.tw3_col = -1;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int len = pass ? D.M : D.N;
+      int tt, r;
+      if (!reg_fft_params(len, &tt, &r)) continue;
+      const int sub = 32 * tt;
+      if (!L.tw2_off.count(sub)) {
+        L.tw2_off[sub] = (int)L.total_tw2;
+        L.total_tw2 += sub;
+      }
+      if (r > 1 && !L.tw2_off.count(-len)) {
+        L.tw2_off[-len] = (int)L.total_tw2;
         L.total_tw2 += len;
       }
-    if (L.tw2_off.count(D.N)) D.tw2_row = L.tw2_off[D.N];
-    if (L.tw2_off.count(D.M)) D.tw2_col = L.tw2_off[D.M];
+      (pass ? D.tw2_col : D.tw2_row) = L.tw2_off[sub];
+      if (r > 1) (pass ? D.tw3_col : D.tw3_row) = L.tw2_off[-len];
+    }
     factor235(D.N, &D.sched_row);
     factor235(D.M, &D.sched_col);
   }
@@ -571,16 +608,31 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
       s2[o2 + k] = (T)(4.0 * sn * sn);
     }
   }
-  // [k1][t] tables of the power-of-two transforms: tw2[k1 TT + t] = exp(-2 pi i t k1 / L).
+  // [k1][t] tables of the power-of-two transforms: tw2[k1 TT + t] = exp(-2 pi i t k1 / L);
+  // [r][k2] tables of the R * L2 transforms: tw3[r L2 + k2] = exp(-2 pi i r k2 / L).
   std::vector<T> tw2(2 * L.total_tw2);
   for (const auto &kv : L.tw2_off) {
-    const int len = kv.first, o = kv.second, tt = len / 32;
-    for (int k1 = 0; k1 < 32; ++k1)
-      for (int t = 0; t < tt; ++t) {
-        const double a = 2.0 * M_PI * (double)(k1 * t) / (double)len;
-        tw2[2 * (o + k1 * tt + t)] = (T)std::cos(a);
-        tw2[2 * (o + k1 * tt + t) + 1] = (T)(-std::sin(a));
-      }
+    const int o = kv.second;
+    if (kv.first > 0) {
+      const int len = kv.first, tt = len / 32;
+      for (int k1 = 0; k1 < 32; ++k1)
+        for (int t = 0; t < tt; ++t) {
+          const double a = 2.0 * M_PI * (double)(k1 * t) / (double)len;
+          tw2[2 * (o + k1 * tt + t)] = (T)std::cos(a);
+          tw2[2 * (o + k1 * tt + t) + 1] = (T)(-std::sin(a));
+        }
+    } else {
+      const int len = -kv.first;
+      int tt, r;
+      reg_fft_params(len, &tt, &r);
+      const int L2 = 32 * tt;
+      for (int rr = 0; rr < r; ++rr)
+        for (int k2 = 0; k2 < L2; ++k2) {
+          const double a = 2.0 * M_PI * (double)(rr * k2) / (double)len;
+          tw2[2 * (o + rr * L2 + k2)] = (T)std::cos(a);
+          tw2[2 * (o + rr * L2 + k2) + 1] = (T)(-std::sin(a));
+        }
+    }
   }
   CK(cudaMemcpyAsync(p->ws + L.o_tw, tw.data(), tw.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   if (!tw2.empty())
@@ -660,7 +712,7 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
   if (iters < 1 || k < 1) return DECONV_EINVAL;
   for (const auto *v : {&L.row_cls, &L.col_cls})
     for (const Cls &c : *v)
-      if (c.cfg.kind != KIND_P2) return DECONV_EUNSUPPORTED;  // reverse pass: power-of-two sizes only
+      if (c.cfg.kind != KIND_P2 || c.cfg.r != 1) return DECONV_EUNSUPPORTED;  // reverse pass: powers of two only
   G->k = std::min(k, iters);
   G->nck = (iters + G->k - 1) / G->k;
   const int maxthr = L.esz == 4 ? 512 : 256;

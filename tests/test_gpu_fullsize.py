@@ -39,3 +39,31 @@ def test_c2_full_run(c2):
     print(f"c2 full run: rel L2 {err:.3e}, dPSNR {dpsnr:+.4f} dB")
     assert err <= 1e-3
     assert abs(dpsnr) <= 0.01
+
+
+def _sampled_batch_check(prob, iters, tol):
+    # the whole batch runs in one plan (the benchmark's launch configuration);
+    # one image of every distinct size is recomputed by the oracle
+    xg, _, _ = gpu_solve(prob, iters=iters)
+    seen = {}
+    for j, s in enumerate(prob.shapes):
+        seen.setdefault(s, j)
+    import oracle
+    for s, j in sorted(seen.items()):
+        xo, _, _ = oracle.admm(prob.y[j], prob.mask[j], prob.h, prob.lam, prob.mu, iters, relax=prob.relax,
+                               round_f32=True)
+        err = rel_l2([xg[j]], [xo])
+        print(f"{prob.name} image {j} {s}: rel L2 {err:.3e}")
+        assert err <= tol
+
+
+def test_c3_batch_one_iteration_sampled():
+    _sampled_batch_check(inputs.config_c3(), 1, 1e-5)
+
+
+def test_c4_batch_one_iteration_sampled():
+    _sampled_batch_check(inputs.config_c4(), 1, 1e-5)
+
+
+def test_c4_batch_ten_iterations_sampled():
+    _sampled_batch_check(inputs.config_c4(), 10, 1e-4)

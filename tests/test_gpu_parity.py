@@ -197,3 +197,38 @@ def test_checkpoint_resume_in_another_plan():
     assert plan2.sync() == 0
     flat = np.concatenate([a.ravel() for a in full])
     assert np.array_equal(x.double().cpu().numpy(), flat)
+
+
+def test_mixed_radix_passes_every_length():
+    # lengths 3 * 2^k and 5 * 2^k (k = 7..9) through the radix-3/5 register
+    # transforms, beside generic (96, 160) and power-of-two (64) lengths
+    prob = inputs.random_problem(27, [(384, 640), (640, 384), (768, 96), (96, 1280), (1536, 160), (160, 2560),
+                                      (1280, 64)], 7, mask_kind="random", frac=0.3, iters=1)
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    for a, b in zip(xg, xo):
+        assert rel_l2([a], [b]) <= 1e-5
+
+
+def test_mixed_radix_vectorial_tv_and_stats():
+    prob = inputs.random_problem(28, [(384, 384), (640, 768)], 5, mask_kind="bayer", channels=3, iters=3)
+    xg, sg, _ = gpu_solve(prob, stats=True)
+    xo, so = oracle_solve(prob, stats=True)
+    for j in range(2):
+        assert rel_l2([xg[j]], [xo[j]]) <= 3e-5
+        assert np.allclose(sg[j][:, 2], so[j][:, 3], rtol=1e-4)
+
+
+def test_mixed_radix_twenty_iterations():
+    prob = inputs.random_problem(29, [(384, 640)], 9, mask_kind="random", frac=0.4, iters=20, psf="motion")
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    assert rel_l2(xg, xo) <= 1e-4
+
+
+def test_mixed_radix_fp64():
+    prob = inputs.random_problem(30, [(384, 640), (768, 1280)], 5, mask_kind="random", frac=0.3, iters=2,
+                                 dtype="f64")
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    assert rel_l2(xg, xo) <= 1e-10
