@@ -306,6 +306,10 @@ def main():
     ap.add_argument("--compare-plain", action="store_true",
                     help="also time the plain per-image cuFFT path (torch.autograd for c5)")
     ap.add_argument("--plain-iters", type=int, default=20)
+    ap.add_argument("--iters", type=int, default=0,
+                    help="override the workload's iteration count (profiling runs; recorded in config)")
+    ap.add_argument("--timed-only", action="store_true",
+                    help="skip the e2e, per-pass and CPU-baseline legs (profiling runs)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -333,6 +337,8 @@ def main():
             dist.barrier()
 
     prob = make_problem(args.config)
+    if args.iters > 0:
+        prob.iters = args.iters
     total_px_all = prob.pixels()
     sharded = world > 1 and len(prob.shapes) > 1
     if sharded:
@@ -404,6 +410,16 @@ def main():
     t_ms = float(t.item())
     units = (total_px_all if sharded else px * world) * prob.iters * args.steps
     value = units / (t_ms / 1e3) / 1e6
+    if args.timed_only:
+        if rank == 0:
+            print(json.dumps({"metric": "Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+                              "config": {"workload": args.config, "iterations": prob.iters},
+                              "clocks": clk, "timed_only": True}))
+        plan.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # End to end through the host-buffer entry point (forward solve).
     y_host = torch.tensor(y_np, dtype=dt).pin_memory()

@@ -243,7 +243,8 @@ __device__ __forceinline__ void fft_p2(cx<T> (&v)[32], cx<T> *tile, int q, unsig
 // E (L complex, this transform's), and the R-point combine
 // X[k2 + L2 s] = sum_r E[r][k2] exp(SIGN 2 pi i r s / R) for s = gr.
 // Contains __syncthreads when R > 1: every thread of the CTA must call it
-// (threads of inactive groups with active = false).
+// (threads of inactive groups with active = false).  E may share storage
+// with the R groups' transpose tiles (a barrier separates their uses).
 template <typename T, int R, int SIGN> __device__ __forceinline__ cx<T> root_r(int j) {
   // exp(SIGN 2 pi i j / R) for R = 3, 5 (exact constants)
   if constexpr (R == 3) {
@@ -268,6 +269,7 @@ __device__ __forceinline__ void fft_mixed(cx<T> (&v)[32], bool active, cx<T> *ti
   constexpr int L2 = 32 * TT;
   if (active) fft_p2<T, TT, SIGN>(v, tile, q, gmask, tw2);
   if constexpr (R > 1) {
+    __syncthreads();  // E may overlay the transpose tiles of the other groups
     if (active) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {

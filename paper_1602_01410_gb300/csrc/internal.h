@@ -82,10 +82,12 @@ struct LaunchCfg {
   int kind;      // KernelKind
   int tt;        // KIND_P2: threads per sub-transform (sub-length / 32)
   int r;         // KIND_P2: length = r * 32 * tt, r in {1, 3, 5}
+  int stage;     // KIND_P2 rows, one channel: forward half stages its rows in shared memory
   int nt;        // threads per CTA
   int channels;  // 1 or 3
   int grid;      // CTAs
   size_t smem;   // dynamic shared memory per CTA
+  size_t smem_fwd;  // KIND_P2 rows: the forward half's (smem is the inverse half's)
 };
 
 // Kernel launchers (kernels_*.cu).

@@ -12,32 +12,36 @@ namespace dcv {
 template <typename T> constexpr int kMaxNt = sizeof(T) == 4 ? 512 : 256;
 
 // Power-of-two and R * 2^k row passes: half 0 = inverse (R1), half 1 = forward (R2).
+// The staged forward half exists for one channel only.
 template <typename T, int TT, int C, int R>
-static const void *row_p2_one(int half) {
-  return half ? (const void *)row_fwd_p2_kernel<T, TT, C, R> : (const void *)row_inv_p2_kernel<T, TT, C, R>;
+static const void *row_p2_one(int half, int stage) {
+  if (!half) return (const void *)row_inv_p2_kernel<T, TT, C, R>;
+  if constexpr (C == 1)
+    if (stage) return (const void *)row_fwd_p2_staged_kernel<T, TT, C, R>;
+  return (const void *)row_fwd_p2_kernel<T, TT, C, R>;
 }
 
 template <typename T, int C>
-static const void *row_p2_ptr(int tt, int r, int half) {
+static const void *row_p2_ptr(int tt, int r, int half, int stage) {
   if (r == 1) {
     switch (tt) {
-      case 2: return row_p2_one<T, 2, C, 1>(half);
-      case 4: return row_p2_one<T, 4, C, 1>(half);
-      case 8: return row_p2_one<T, 8, C, 1>(half);
-      case 16: return row_p2_one<T, 16, C, 1>(half);
-      case 32: return row_p2_one<T, 32, C, 1>(half);
+      case 2: return row_p2_one<T, 2, C, 1>(half, stage);
+      case 4: return row_p2_one<T, 4, C, 1>(half, stage);
+      case 8: return row_p2_one<T, 8, C, 1>(half, stage);
+      case 16: return row_p2_one<T, 16, C, 1>(half, stage);
+      case 32: return row_p2_one<T, 32, C, 1>(half, stage);
     }
   } else if (r == 3) {
     switch (tt) {
-      case 4: return row_p2_one<T, 4, C, 3>(half);
-      case 8: return row_p2_one<T, 8, C, 3>(half);
-      case 16: return row_p2_one<T, 16, C, 3>(half);
+      case 4: return row_p2_one<T, 4, C, 3>(half, stage);
+      case 8: return row_p2_one<T, 8, C, 3>(half, stage);
+      case 16: return row_p2_one<T, 16, C, 3>(half, stage);
     }
   } else if (r == 5) {
     switch (tt) {
-      case 4: return row_p2_one<T, 4, C, 5>(half);
-      case 8: return row_p2_one<T, 8, C, 5>(half);
-      case 16: return row_p2_one<T, 16, C, 5>(half);
+      case 4: return row_p2_one<T, 4, C, 5>(half, stage);
+      case 8: return row_p2_one<T, 8, C, 5>(half, stage);
+      case 16: return row_p2_one<T, 16, C, 5>(half, stage);
     }
   }
   return nullptr;
@@ -45,7 +49,8 @@ static const void *row_p2_ptr(int tt, int r, int half) {
 
 template <typename T>
 static const void *row_ptr(const LaunchCfg &c, int half = 0) {
-  if (c.kind == KIND_P2) return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt, c.r, half) : row_p2_ptr<T, 1>(c.tt, c.r, half);
+  if (c.kind == KIND_P2)
+    return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt, c.r, half, c.stage) : row_p2_ptr<T, 1>(c.tt, c.r, half, c.stage);
   if (c.nt == 512 && kMaxNt<T> == 512)
     return c.channels == 3 ? (const void *)row_pass_kernel<T, kMaxNt<T>, 3> : (const void *)row_pass_kernel<T, kMaxNt<T>, 1>;
   if (c.nt == 256)
@@ -92,11 +97,18 @@ static cudaError_t launch_ptr(const void *fn, const A &a, const LaunchCfg &c, cu
   return cudaLaunchKernel(fn, dim3(c.grid), dim3(c.nt), args, c.smem, s);
 }
 
+// The configuration of one half of a register-FFT row pass (its own shared memory size).
+static inline LaunchCfg row_half_cfg(const LaunchCfg &c, int half) {
+  LaunchCfg h = c;
+  if (c.kind == KIND_P2 && half == 1) h.smem = c.smem_fwd;
+  return h;
+}
+
 template <typename T>
 cudaError_t launch_row(const RowArgs<T> &a, const LaunchCfg &c, cudaStream_t s) {
   cudaError_t e = launch_ptr(row_ptr<T>(c, 0), a, c, s);
   if (e != cudaSuccess || c.kind != KIND_P2) return e;
-  return launch_ptr(row_ptr<T>(c, 1), a, c, s);
+  return launch_ptr(row_ptr<T>(c, 1), a, row_half_cfg(c, 1), s);
 }
 
 template <typename T>
@@ -109,7 +121,7 @@ cudaError_t launch_col(const ColArgs<T> &a, const LaunchCfg &c, cudaStream_t s) 
 // memory (each unit instantiates its own copy of a kernel template).
 template <typename T>
 cudaError_t launch_row_half(const RowArgs<T> &a, const LaunchCfg &c, int half, cudaStream_t s) {
-  return launch_ptr(row_ptr<T>(c, half), a, c, s);
+  return launch_ptr(row_ptr<T>(c, half), a, row_half_cfg(c, half), s);
 }
 
 // Opt in to the dynamic shared memory a class needs (above 48 KB).
@@ -118,7 +130,7 @@ cudaError_t prepare_row(const LaunchCfg &c) {
   for (int half = 0; half < (c.kind == KIND_P2 ? 2 : 1); ++half) {
     const void *fn = row_ptr<T>(c, half);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_half_cfg(c, half).smem);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

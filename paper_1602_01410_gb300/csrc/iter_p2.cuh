@@ -68,11 +68,12 @@ template <int TT> __device__ __forceinline__ constexpr int p2_unslot(int m) {
 // into shared memory asynchronously while the transforms run.  Statistics:
 // ||dz||^2 and the data-fit half of the objective.  ROW_ADJ (reverse pass):
 // xbuf <- b, yt <- yt + T~b instead of the z-update.
-// Shared memory: [transpose tiles][exchange C x Rb x N][y~ C x Rb x N][mask words].
+// Shared memory: [one region of R transpose tiles per (channel, row), which
+// the R groups also use as their exchange buffer][y~ C x Rb x N][mask words].
 template <typename T, int TT, int C, int R>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT;
+  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, RS = R * GS;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb, wpr = N / 32;
@@ -80,7 +81,6 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   const int r0 = blk * Rb, nr = min(Rb, M - r0);
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
-  const int ngroups = blockDim.x / TT;
   const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   T *__restrict__ yt = a.yt;
   T *__restrict__ xbuf = a.xbuf;
   T *__restrict__ xout = (a.x_out && a.x_out != a.xbuf) ? a.x_out : nullptr;
-  cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
-  cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)ngroups * GS;           // [C*Rb][N] exchange
-  T *Ys = reinterpret_cast<T *>(Ex + (R > 1 ? (size_t)C * Rb * N : 0));              // [C][Rb][N]
+  cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)row_id * RS;  // this row's region
+  cx<T> *tile = Ex + gr * GS;
+  T *Ys = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)C * Rb * RS);  // [C][Rb][N]
   uint32_t *Ms = reinterpret_cast<uint32_t *>(Ys + (size_t)C * Rb * N);              // [C][Rb][N/32]
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
       }
     }
   }
-  if (!init) fft_mixed<T, TT, R, +1>(v, active, tile, q, group_mask(TT), gr, tw2, tw3, Ex + (size_t)row_id * N);
+  if (!init) fft_mixed<T, TT, R, +1>(v, active, tile, q, group_mask(TT), gr, tw2, tw3, Ex);
   cp_async_wait_all();
   __syncthreads();
   if (active && adj) {
@@ -167,7 +167,139 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
 }
 
 // ----------------------------------------------------------- row (R2) ---
-// Forward half.  The CTA stages x (rows r0-1 .. r1), d (rows r0-1 .. r1-1)
+// Forward half.  Each thread reads the x, d and y~ values of its own pixels
+// straight from global memory (the neighbours at p-1, p+1 and in rows i-1,
+// i+1 are read by adjacent lanes and by the CTAs of adjacent rows, so they
+// come from L1/L2).  From them: the prox factor g at (i,p), (i,p-1), (i-1,p)
+// (norm over channels), d^{i+1} = (1-g) a, r = mu D^T (v - d^{i+1}) with
+// v - d^{i+1} = (2g - 1) a; then the forward row DFT of y~ + i r, split into
+// (Y_row, R_row).  Statistics: ||dd||^2 and the TV half of the objective.
+// Shared memory: one region of R transpose tiles per (channel, row); it
+// holds y~ + i r, then the transpose tiles and the exchange buffer, then the
+// transformed row.
+template <typename T, int TT, int C, int R>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(RowArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, RS = R * GS;
+  const int wi = blockIdx.x;
+  const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
+  const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb;
+  const int blk = wi - Dp->row_begin;
+  const int r0 = blk * Rb, nr = min(Rb, M - r0);
+  const long long P = (long long)M * N, px0 = Dp->px;
+  const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
+  const bool active = ch < C && hh < nr;
+  const int i = r0 + hh;
+  const int iu = i == 0 ? M - 1 : i - 1, id = i + 1 == M ? 0 : i + 1;
+  const bool init = a.mode == ROW_INIT;
+  const T *__restrict__ xg = a.xbuf + px0;
+  const cx<T> *__restrict__ dg = reinterpret_cast<const cx<T> *>(a.d_in) + px0;
+  const T *__restrict__ yg = a.yt + px0;
+  cx<T> *__restrict__ dout = reinterpret_cast<cx<T> *>(a.d_out);
+  cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)row_id * RS;  // this row's region
+  cx<T> *tile = Cs + gr * GS;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const unsigned gm = group_mask(TT);
+
+  const T tau = a.tau, tau2 = a.tau * a.tau;
+  const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
+  T s_dd = T(0), s_tv = T(0);
+  bool finite = true;
+  if (active) {
+#pragma unroll 4
+    for (int m = 0; m < 32; ++m) {
+      const int p = q + TT * m + L2 * gr;
+      const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
+      T s0 = T(0), sl = T(0), su = T(0), tv = T(0);
+      T ah0 = T(0), av0 = T(0), ahl = T(0), avu = T(0), dh0 = T(0), dv0 = T(0);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T *xr = xg + c * P + (long long)i * N, *xu = xg + c * P + (long long)iu * N,
+                *xd = xg + c * P + (long long)id * N;
+        const T x0 = xr[p], xl = xr[pm], xrr = xr[p1], xdn = xd[p], xdl = xd[pm], xup = xu[p], xul = xu[p1];
+        cx<T> d0 = mk<T>(T(0), T(0)), dl = d0, du = d0;
+        if (!init) {
+          const cx<T> *dr = dg + c * P + (long long)i * N, *dru = dg + c * P + (long long)iu * N;
+          d0 = dr[p];
+          dl = dr[pm];
+          du = dru[p];
+        }
+        const T gh = xrr - x0, gv = xdn - x0;
+        const T a_h = gh + d0.x, a_v = gv + d0.y;
+        s0 += a_h * a_h + a_v * a_v;
+        tv += gh * gh + gv * gv;
+        const T a_hl = (x0 - xl) + dl.x, a_vl = (xdl - xl) + dl.y;
+        sl += a_hl * a_hl + a_vl * a_vl;
+        const T a_hu = (xul - xup) + du.x, a_vu = (x0 - xup) + du.y;
+        su += a_hu * a_hu + a_vu * a_vu;
+        if (c == ch) {
+          ah0 = a_h;
+          av0 = a_v;
+          ahl = a_hl;
+          avu = a_vu;
+          dh0 = d0.x;
+          dv0 = d0.y;
+        }
+      }
+      const T g0 = init ? T(1) : (s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0));
+      const T gl = init ? T(1) : (sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0));
+      const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
+      const T dnh = (T(1) - g0) * ah0, dnv = (T(1) - g0) * av0;
+      dout[px0 + ch * P + (long long)i * N + p] = mk<T>(dnh, dnv);
+      if (stats) {
+        s_dd += (dnh - dh0) * (dnh - dh0) + (dnv - dv0) * (dnv - dv0);
+        if (ch == 0) s_tv += sqrt(tv);
+      }
+      const T r = a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
+                          ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
+      const T yv = yg[ch * P + (long long)i * N + p];
+      finite = finite && isfinite(r) && isfinite(yv);
+      Cs[p] = mk<T>(yv, r);
+    }
+  }
+  if (!finite) atomicOr(a.err, 1);
+  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  cx<T> v[32];
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+  }
+  // every group of the row has read its inputs before the tiles overwrite them
+  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Cs);
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) Cs[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
+  }
+  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  if (active) {
+    cpair<T> *__restrict__ dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
+    for (int k = q + TT * gr; k < Nh; k += TT * R) {
+      const cx<T> c1 = Cs[k], c2 = Cs[k == 0 ? 0 : N - k];
+      cpair<T> o;
+      o.ar = T(0.5) * (c1.x + c2.x);
+      o.ai = T(0.5) * (c1.y - c2.y);
+      o.br = T(0.5) * (c1.y + c2.y);
+      o.bi = T(0.5) * (c2.x - c1.x);
+      dst[k] = o;
+    }
+  }
+  if (stats) {
+    double tvl = double(a.lambda) * double(s_tv), z = 0.0, dd = double(s_dd);
+    block_sum3_dyn(dd, z, tvl);
+    if (threadIdx.x == 0) {
+      double *o = a.partials + 3 * (long long)(Dp->row_pbase + blk);
+      o[0] = dd;
+      o[2] += tvl;
+    }
+  }
+}
+
+// ------------------------------------------------- row (R2), staged ---
+// Forward half, staged variant (used where the staged rows fit: one
+// channel).  The CTA stages x (rows r0-1 .. r1), d (rows r0-1 .. r1-1)
 // and y~ (rows r0 .. r1-1) of every channel into shared memory with one
 // batch of asynchronous copies.  From them: the prox factor g at (i,p),
 // (i,p-1), (i-1,p) (norm over channels), d^{i+1} = (1-g) a,
@@ -178,7 +310,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
 // transpose tiles reuse it after a barrier), then per row y~ + i r and the
 // exchange buffer.
 template <typename T, int TT, int C, int R>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(RowArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT;
   const int wi = blockIdx.x;
@@ -313,33 +445,33 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
 
 // --------------------------------------------------------------- column ---
 // One set of R groups per signal (Y or R of one spectral column) of a tile of
-// W columns; the tile, the H^ tile and the sin^2 tables are staged with
-// cp.async.  Shared memory: [staging M x SL][transpose tiles][H^ tile]
-// [sin^2][exchange 2W x M].
+// W columns.  The tile is staged with cp.async (coalesced row segments) into
+// one shared-memory column per signal; the signal's R groups transform it in
+// place (their transpose tiles and exchange buffer are that column's
+// storage).  Shared memory: [2W columns of R tiles (+4 elements of padding,
+// which spreads the staging stores over the banks)][H^ tile M x w][sin^2 tables].
 template <typename T, int TT, int R>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT;
+  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, SR = R * GS + 4;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, false)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh;
   const int local = wi - Dp->col_begin;
   const int ch = local / Dp->col_tiles, t = local - ch * Dp->col_tiles;
   const int k20 = t * Dp->W, w = min(Dp->W, Nh - k20);
-  const int SL = (2 * Dp->W) | 1;  // staging row stride (complex)
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_col;
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_col;
-  const cx<T> *H = reinterpret_cast<const cx<T> *>(a.hhat) + Dp->hhat;
+  const cx<T> *__restrict__ H = reinterpret_cast<const cx<T> *>(a.hhat) + Dp->hhat;
   const T *s2c = a.s2 + Dp->s2_col, *s2r = a.s2 + Dp->s2_row;
-  cx<T> *st = reinterpret_cast<cx<T> *>(smem_raw);  // [M][SL]
+  cx<T> *St = reinterpret_cast<cx<T> *>(smem_raw);                  // [2W][SR]
+  cx<T> *Hs = St + (size_t)2 * Dp->W * SR;                           // [M][w] H^ tile
+  T *S2s = reinterpret_cast<T *>(Hs + (size_t)M * Dp->W);            // [M] column sin^2, then [W] row sin^2
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
   const unsigned gm = group_mask(TT);
-  const int ngroups = blockDim.x / TT;
   const int gr = g % R, sig = g / R;
-  cx<T> *tile = st + (size_t)M * SL + (size_t)g * GS;
-  cx<T> *Hs = st + (size_t)M * SL + (size_t)ngroups * GS;  // [M][W] H^ tile
-  T *S2s = reinterpret_cast<T *>(Hs + (size_t)M * Dp->W);  // [M] column sin^2, then [W] row sin^2
-  cx<T> *Ex = reinterpret_cast<cx<T> *>(S2s + ((M + Dp->W + 3) & ~3)) + (size_t)sig * M;
+  cx<T> *col = St + (size_t)sig * SR;  // this signal's column
+  cx<T> *tile = col + gr * GS;
   const long long base = Dp->spec + (long long)ch * M * Nh + k20;
   const int nthr = blockDim.x;
 
@@ -350,7 +482,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   const bool scol_on = lane_ok && scol < 2 * w;
   if (scol_on)
     for (int ii = r0t; ii < M; ii += rstep)
-      cp_async<sizeof(cx<T>)>(&st[ii * SL + scol],
+      cp_async<sizeof(cx<T>)>(&St[scol * SR + ii],
                               reinterpret_cast<const cx<T> *>(&a.S_in[base + (long long)ii * Nh]) + scol);
   if (lane_ok && scol < w)
     for (int k1 = r0t; k1 < M; k1 += rstep) cp_async<sizeof(cx<T>)>(&Hs[k1 * w + scol], &H[(long long)k1 * Nh + k20 + scol]);
@@ -363,13 +495,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   const bool active = sig < 2 * w;
   if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = st[(R * (q + TT * m) + gr) * SL + sig];
+    for (int m = 0; m < 32; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
-  if (R > 1) __syncthreads();
-  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, col);
   if (active) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) st[(q + TT * p2_slot<TT>(j) + L2 * gr) * SL + sig] = v[j];
+    for (int j = 0; j < 32; ++j) col[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
   }
   __syncthreads();
   const T mu = a.mu, scale = T(1) / (T(M) * T(N));
@@ -377,11 +509,12 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     const int ww = scol;
     const T s2w = S2s[M + ww];
     cx<T> *gacc = a.gacc ? reinterpret_cast<cx<T> *>(a.gacc) + base : nullptr;
+    cx<T> *cy = St + (size_t)(2 * ww) * SR, *cr = cy + SR;
     for (int k1 = r0t; k1 < M; k1 += rstep) {
       const cx<T> hv = Hs[k1 * w + ww];
       const T den = hv.x * hv.x + hv.y * hv.y + mu * (S2s[k1] + s2w);
       const T inv = scale / den;
-      const cx<T> Y = st[k1 * SL + 2 * ww], Rv = st[k1 * SL + 2 * ww + 1];
+      const cx<T> Y = cy[k1], Rv = cr[k1];
       const cx<T> B = cadd<T>(cmulc<T>(hv, Y), Rv);  // den * (solution spectrum)
       if (a.spec_store) {
         cpair<T> o;
@@ -407,26 +540,27 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
         gacc[(long long)k1 * Nh + ww] = gv;
       }
       const cx<T> Xv = cscale<T>(B, inv);
-      st[k1 * SL + 2 * ww] = Xv;
-      st[k1 * SL + 2 * ww + 1] = cmul<T>(hv, Xv);
+      cy[k1] = Xv;
+      cr[k1] = cmul<T>(hv, Xv);
     }
   }
   __syncthreads();
   if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = st[(R * (q + TT * m) + gr) * SL + sig];
+    for (int m = 0; m < 32; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
-  if (R > 1) __syncthreads();
-  fft_mixed<T, TT, R, +1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  fft_mixed<T, TT, R, +1>(v, active, tile, q, gm, gr, tw2, tw3, col);
   if (active) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) st[(q + TT * p2_slot<TT>(j) + L2 * gr) * SL + sig] = v[j];
+    for (int j = 0; j < 32; ++j) col[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
   }
   __syncthreads();
   if (lane_ok && scol < w) {
     const int ww = scol;
+    const cx<T> *cx_ = St + (size_t)(2 * ww) * SR, *ch_ = cx_ + SR;
     for (int ii = r0t; ii < M; ii += rstep) {
-      const cx<T> Xv = st[ii * SL + 2 * ww], HX = st[ii * SL + 2 * ww + 1];
+      const cx<T> Xv = cx_[ii], HX = ch_[ii];
       cpair<T> c;
       c.ar = Xv.x;
       c.ai = Xv.y;

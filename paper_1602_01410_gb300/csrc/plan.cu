@@ -101,20 +101,26 @@ int p2_row_threads(int C, int rb, int tt, int r = 1) {
   return (C * rb * r + per_warp - 1) / per_warp * per_warp * tt;
 }
 
-size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz, int r = 1) {
+// Shared memory of one half of a register-FFT row pass (0: inverse, 1: forward).
+size_t p2_row_smem_half(int C, int N, int rb, int tt, size_t esz, int r, int stage, int half) {
+  const size_t region = (size_t)C * rb * r * p2_group_stride_h(tt) * 2 * esz;  // tiles / exchange per row
+  if (half == 0) return region + (size_t)C * rb * N * esz + (size_t)C * rb * (N / 32) * 4;  // + y~ rows, mask
+  if (!stage) return region;
+  // staged forward half: [x (rb+2) rows][d (rb+1) rows][y~ rb rows] (the tiles
+  // reuse them), then y~ + i r and the exchange buffer per row
   const size_t tiles = (size_t)(p2_row_threads(C, rb, tt, r) / tt) * p2_group_stride_h(tt) * 2 * esz;
   const size_t ex = r > 1 ? (size_t)C * rb * N * 2 * esz : 0;
-  const size_t inv = tiles + ex + (size_t)C * rb * N * esz + (size_t)C * rb * (N / 32) * 4;  // inverse half
-  const size_t fwd = std::max((size_t)C * ((rb + 2) + 2 * (rb + 1) + rb) * N * esz, tiles) +
-                     (size_t)C * rb * N * 2 * esz + ex;                                     // forward half
-  return std::max(inv, fwd);
+  return std::max((size_t)C * ((rb + 2) + 2 * (rb + 1) + rb) * N * esz, tiles) + (size_t)C * rb * N * 2 * esz + ex;
 }
 
-// Column pass: staging tile + transpose tiles + H^ tile + sin^2 tables + exchange.
+size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz, int r = 1, int stage = 0) {
+  return std::max(p2_row_smem_half(C, N, rb, tt, esz, r, stage, 0), p2_row_smem_half(C, N, rb, tt, esz, r, stage, 1));
+}
+
+// Column pass: one column of r transpose tiles (+4 padding) per signal, H^ tile, sin^2 tables.
 size_t p2_col_smem(int M, int w, int tt, size_t esz, int r = 1) {
-  const int per_warp = 32 / tt, groups = (2 * w * r + per_warp - 1) / per_warp * per_warp;
-  return (size_t)M * ((2 * w) | 1) * 2 * esz + (size_t)groups * p2_group_stride_h(tt) * 2 * esz +
-         (size_t)M * w * 2 * esz + (size_t)((M + w + 3) & ~3) * esz + (r > 1 ? (size_t)2 * w * M * 2 * esz : 0);
+  return (size_t)2 * w * (r * p2_group_stride_h(tt) + 4) * 2 * esz + (size_t)M * w * 2 * esz +
+         (size_t)((M + w + 3) & ~3) * esz;
 }
 
 int p2_col_threads(int w, int tt, int r = 1) {
@@ -184,7 +190,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     const int M = d->rows[j], N = d->cols[j];
     int tt, r;
     if (allow_p2 && reg_fft_params(N, &tt, &r) && p2_row_threads(L.C, 1, tt, r) <= maxthr &&
-        p2_row_smem(L.C, N, 1, tt, L.esz, r) <= kMaxSmem) {
+        p2_row_smem(L.C, N, 1, tt, L.esz, r, L.C == 1) <= kMaxSmem) {
       row_key[j] = tt * 8 + r;
       p2_rows[row_key[j]] += M;
     } else {
@@ -222,13 +228,20 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   if (!ok) return DECONV_EUNSUPPORTED;
   // Class parameters: rows per CTA / columns per CTA aiming at one CTA per SM.
   std::map<int, int> p2_rb, p2_w;
+  // One channel and one row class: the forward row half stages its rows (x
+  // with halo, d, y~) in shared memory.  Otherwise it reads them through L1:
+  // the staged rows of three channels would leave room for one row per CTA,
+  // and the classes of a batch run concurrently only while their CTAs fit on
+  // the SMs side by side.
+  const int row_stage =
+      (L.C == 1 && p2_rows.size() == 1 && g_rows == 0) ? env_int("DECONV_ROW_STAGE", 1) : env_int("DECONV_ROW_STAGE", 0);
   for (const auto &kv : p2_rows) {
     const int tt = kv.first / 8, r = kv.first % 8, N = r * 32 * tt;
     const int rtarget = env_int("DECONV_P2_ROW_CTAS", 152);
     int rb = (int)std::max<long long>(1, (kv.second + rtarget - 1) / rtarget);
     rb = env_int("DECONV_P2_ROW_BLOCK", rb);
-    while (rb > 1 &&
-           (p2_row_threads(L.C, rb, tt, r) > maxthr || p2_row_smem(L.C, N, rb, tt, L.esz, r) > kMaxSmem))
+    while (rb > 1 && (p2_row_threads(L.C, rb, tt, r) > maxthr ||
+                      p2_row_smem(L.C, N, rb, tt, L.esz, r, row_stage) > kMaxSmem))
       --rb;
     p2_rb[kv.first] = rb;
   }
@@ -289,8 +302,11 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
     L.row_grid += D.row_blocks;
     L.col_grid += L.C * D.col_tiles;
     if (row_key[j]) {
+      rc.cfg.stage = row_stage;
       rc.cfg.nt = p2_row_threads(L.C, D.Rb, rc.cfg.tt, rc.cfg.r);
-      rc.cfg.smem = std::max(rc.cfg.smem, p2_row_smem(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r));
+      rc.cfg.smem = std::max(rc.cfg.smem, p2_row_smem_half(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r, row_stage, 0));
+      rc.cfg.smem_fwd =
+          std::max(rc.cfg.smem_fwd, p2_row_smem_half(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r, row_stage, 1));
     } else {
       rc.cfg.nt = L.nt;
       const size_t ldr = (size_t)((L.C * (D.Rb + 2)) | 1);
@@ -412,6 +428,12 @@ struct deconv_plan_s {
   int parity = 0;
   bool have_state = false;
   cudaGraphExec_t gexec = nullptr;
+  // While a graph is captured: the kernel classes of one pass (disjoint sets
+  // of images) fan out over side streams, so their launches run concurrently.
+  cudaStream_t fan_main = nullptr;
+  std::vector<cudaStream_t> fan_side;
+  cudaEvent_t fan_fork = nullptr;
+  std::vector<cudaEvent_t> fan_join;
 
   template <typename P> P *at(size_t off) const { return reinterpret_cast<P *>(ws + off); }
 };
@@ -483,24 +505,53 @@ template <typename T> T *dbuf(deconv_plan_s *p, int which) {
   return p->at<T>(which ? p->L.o_d1 : p->L.o_d0);
 }
 
+// Launches fn(class k, stream) for every class of a pass: on s in order, or,
+// while a graph is captured on fan_main, class k > 0 on side stream k-1
+// (forked from and joined back into s).
+template <typename F>
+cudaError_t each_class(deconv_plan_s *p, cudaStream_t s, size_t n, F fn) {
+  const bool fan = n > 1 && s == p->fan_main && p->fan_side.size() + 1 >= n;
+  if (fan) {
+    cudaError_t e = cudaEventRecord(p->fan_fork, s);
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t k = 0; k < n; ++k) {
+    cudaStream_t sk = s;
+    if (fan && k > 0) {
+      sk = p->fan_side[k - 1];
+      cudaError_t e = cudaStreamWaitEvent(sk, p->fan_fork, 0);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = fn(k, sk);
+    if (e != cudaSuccess) return e;
+    if (fan && k > 0) {
+      e = cudaEventRecord(p->fan_join[k - 1], sk);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (fan)
+    for (size_t k = 1; k < n; ++k) {
+      cudaError_t e = cudaStreamWaitEvent(s, p->fan_join[k - 1], 0);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
 // One iteration (column pass then row pass), d ping-pong by plan parity.
 template <typename T>
 cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s) {
-  for (const Cls &c : p->L.col_cls) {
-    cudaError_t e = launch_col<T>(col_args<T>(p, c), c.cfg, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const auto &cl = p->L.col_cls;
+  return each_class(p, s, cl.size(),
+                    [&](size_t k, cudaStream_t sk) { return launch_col<T>(col_args<T>(p, cl[k]), cl[k].cfg, sk); });
 }
 
 template <typename T>
 cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, T *d_out, T *x_out,
                      double *partials) {
-  for (const Cls &c : p->L.row_cls) {
-    cudaError_t e = launch_row<T>(row_args<T>(p, c, mode, d_in, d_out, x_out, partials), c.cfg, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const auto &cl = p->L.row_cls;
+  return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+    return launch_row<T>(row_args<T>(p, cl[k], mode, d_in, d_out, x_out, partials), cl[k].cfg, sk);
+  });
 }
 
 template <typename T>
@@ -534,14 +585,35 @@ deconv_status ensure_graph(deconv_plan_s *p) {
   if (p->gexec) return DECONV_OK;
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const size_t nside = std::max(p->L.row_cls.size(), p->L.col_cls.size()) - 1;
+  deconv_status st = DECONV_OK;
+  if (env_int("DECONV_FAN", 1) && nside > 0) {
+    if (cudaEventCreateWithFlags(&p->fan_fork, cudaEventDisableTiming) != cudaSuccess) st = DECONV_ECUDA;
+    for (size_t k = 0; k < nside && st == DECONV_OK; ++k) {
+      cudaStream_t sk = nullptr;
+      cudaEvent_t ek = nullptr;
+      if (cudaStreamCreateWithFlags(&sk, cudaStreamNonBlocking) != cudaSuccess) st = DECONV_ECUDA;
+      else p->fan_side.push_back(sk);
+      if (cudaEventCreateWithFlags(&ek, cudaEventDisableTiming) != cudaSuccess) st = DECONV_ECUDA;
+      else p->fan_join.push_back(ek);
+    }
+    if (st == DECONV_OK) p->fan_main = cs;
+  }
   const int saved = p->parity;
   p->parity = 0;
-  deconv_status st = DECONV_OK;
   cudaGraph_t g = nullptr;
-  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = DECONV_ECUDA;
+  if (st == DECONV_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    st = DECONV_ECUDA;
   for (int k = 0; k < kGraphIters && st == DECONV_OK; ++k) st = iterate<T>(p, cs, nullptr, nullptr, 0, 0);
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   p->parity = saved;
+  p->fan_main = nullptr;
+  for (cudaStream_t sk : p->fan_side) cudaStreamDestroy(sk);
+  for (cudaEvent_t ek : p->fan_join) cudaEventDestroy(ek);
+  if (p->fan_fork) cudaEventDestroy(p->fan_fork);
+  p->fan_side.clear();
+  p->fan_join.clear();
+  p->fan_fork = nullptr;
   if (st == DECONV_OK && e == cudaSuccess && g) {
     if (cudaGraphInstantiate(&p->gexec, g, 0) != cudaSuccess) {
       p->gexec = nullptr;
