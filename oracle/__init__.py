@@ -53,6 +53,9 @@ def _load():
         lib.or_init_ytilde.argtypes = [_D, _U8, i, i, i, i, _D]
         lib.or_admm.argtypes = [i, i, i, i, _D, _D, _U8, d, d, d, i, i, i, _D, _D, _D, _D, _D]
         lib.or_admm.restype = i
+        lib.or_admm_ex.argtypes = [i, i, i, i, _D, _D, _U8, d, _D, d, i, i, i, i, d, i, d, _D, _D, _D, _D, _D, _D]
+        lib.or_admm_ex.restype = i
+        lib.or_tikhonov.argtypes = [i, i, i, _D, _U8, i, d, _D, _D]
         lib.or_admm_grad.argtypes = [i, i, i, i, _D, _D, _U8, d, d, d, i, i, _D, _D, _D, _D, _D]
         lib.or_admm_grad.restype = i
         _lib = lib
@@ -164,23 +167,46 @@ def init_ytilde(y: np.ndarray, mask: np.ndarray, K: int, round_f32: bool = True)
 
 
 class State:
-    """Partial-ADMM state for C channels: yt (C,M,N), d and v (C,2,M,N)."""
+    """Partial-ADMM state for C channels: yt (C,M,N), d and v (C,2,M,N), and
+    the penalty mu the next iteration uses (None: the caller's mu)."""
 
-    def __init__(self, yt: np.ndarray, d: np.ndarray, v: np.ndarray):
-        self.yt, self.d, self.v = yt, d, v
+    def __init__(self, yt: np.ndarray, d: np.ndarray, v: np.ndarray, mu: Optional[float] = None):
+        self.yt, self.d, self.v, self.mu = yt, d, v, mu
 
     def copy(self) -> "State":
-        return State(self.yt.copy(), self.d.copy(), self.v.copy())
+        return State(self.yt.copy(), self.d.copy(), self.v.copy(), self.mu)
+
+
+def tikhonov(yt: np.ndarray, mask: np.ndarray, h: np.ndarray, iters: int, tau: float = 1e-3):
+    """Eqs. (ini_x)-(ini_z) on one channel plane from z^0 = the unobserved
+    entries of yt.  Returns (y~ with z^{iters}, x^{iters})."""
+    yt = _c(yt).copy()
+    M, N = yt.shape
+    m = np.ascontiguousarray(mask, np.uint8).reshape(M, N)
+    h = _c(h)
+    x = np.zeros((M, N))
+    _load().or_tikhonov(M, N, h.shape[0], _p(h), m.ctypes.data_as(_U8), int(iters), float(tau), _p(yt), _p(x))
+    return yt, x
+
+
+def passes_ad(K: int) -> int:
+    """BGS passes of the paper's Proposed-AD for a K x K = (2b+1) x (2b+1) blur: b."""
+    return max(1, K // 2)
 
 
 def admm(y: np.ndarray, mask: np.ndarray, h: np.ndarray, lam: float, mu: float, iters: int,
          relax: float = 2.0, state: Optional[State] = None, round_f32: bool = True,
-         stats: bool = False):
+         stats: bool = False, passes: int = 1, adapt_t: float = 0.0, tikh_iters: int = 0,
+         tikh_tau: float = 1e-3, mu_hist: bool = False):
     """Run `iters` partial-ADMM iterations on one image of C channels.
 
-    y, mask: (C, M, N).  Returns (x, state, stats) where x is (C, M, N) =
-    x^{iters}, state the final State and stats an (iters, 4) array of
-    [||dd||^2, ||dz||^2, mu ||dv||^2, J] (or None)."""
+    y, mask: (C, M, N).  passes: BGS passes per iteration; adapt_t > 0: the
+    penalty adaptation of Eq. (varying_penalty) with threshold t; tikh_iters
+    > 0 (fresh start only): Tikhonov warm start of z with tau = tikh_tau.
+    Returns (x, state, stats) where x is (C, M, N) = x^{iters}, state the
+    final State and stats an (iters, 4) array of [||dd||^2, ||dz||^2,
+    mu ||dv||^2, J] (or None); with mu_hist=True a fourth item, the (iters,)
+    penalties the iterations used."""
     y = _c(y)
     if y.ndim == 2:
         y = y[None]
@@ -189,14 +215,19 @@ def admm(y: np.ndarray, mask: np.ndarray, h: np.ndarray, lam: float, mu: float, 
     h = _c(h)
     init = state is None
     st = State(np.zeros((C, M, N)), np.zeros((C, 2, M, N)), np.zeros((C, 2, M, N))) if init else state.copy()
+    muv = np.array([float(mu if st.mu is None else st.mu)])
     x = np.zeros((C, M, N))
     s = np.zeros((max(iters, 1), 4)) if stats else None
-    rc = _load().or_admm(C, M, N, h.shape[0], _p(h), _p(y), m.ctypes.data_as(_U8), float(lam), float(mu),
-                         float(relax), int(iters), int(init), int(round_f32), _p(st.yt), _p(st.d),
-                         _p(st.v), _p(x), _p(s) if stats else None)
+    mh = np.zeros(max(iters, 1))
+    rc = _load().or_admm_ex(C, M, N, h.shape[0], _p(h), _p(y), m.ctypes.data_as(_U8), float(lam), _p(muv),
+                            float(relax), int(iters), int(init), int(round_f32), int(passes), float(adapt_t),
+                            int(tikh_iters), float(tikh_tau), _p(st.yt), _p(st.d), _p(st.v), _p(x),
+                            _p(s) if stats else None, _p(mh))
     if rc != 0:
-        raise RuntimeError(f"or_admm failed: {rc}")
-    return x, st, (s[:iters] if stats else None)
+        raise RuntimeError(f"or_admm_ex failed: {rc}")
+    st.mu = float(muv[0])
+    out = (x, st, (s[:iters] if stats else None))
+    return out + (mh[:iters],) if mu_hist else out
 
 
 def admm_grad(y: np.ndarray, mask: np.ndarray, h: np.ndarray, lam: float, mu: float, iters: int,

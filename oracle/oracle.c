@@ -316,25 +316,82 @@ void or_init_ytilde(const double *y, const uint8_t *mask, int M, int N, int K, i
     }
 }
 
+/* ------------------------------------------- Tikhonov initialisation ---
+ * Sec. III-B, Eqs. (ini_x)-(ini_z): z is initialised by alternating
+ * minimisation of f(x, z) + tau/2 ||x||^2,
+ *   x^i = (H^T H + tau I)^{-1} H^T [y; z^{i-1}],   z^i = M_z H x^i,
+ * from z^0 = the padded observation (yt on entry).  H^T H + tau I is BCCB;
+ * its eigenvalues are the DFT of its first column (T~^T T~ e_0 + tau e_0).
+ * One channel plane; yt is updated in place (unobserved entries), x
+ * receives x^{iters}.
+ */
+static double *tikhonov_denominator(int M, int N, const double *h, int K, double tau) {
+  size_t P = (size_t)M * N;
+  double *e = calloc(P, sizeof(double)), *t = malloc(P * sizeof(double)), *a = malloc(P * sizeof(double));
+  e[0] = 1.0;
+  or_conv_circ(e, M, N, h, K, t);
+  or_conv_circ_adj(t, M, N, h, K, a);
+  cplx *s = malloc(sizeof(cplx) * P);
+  for (size_t i = 0; i < P; ++i) s[i] = a[i] + tau * e[i];
+  fft2(s, M, N, -1);
+  double *den = malloc(P * sizeof(double));
+  for (size_t i = 0; i < P; ++i) den[i] = creal(s[i]);
+  free(e); free(t); free(a); free(s);
+  return den;
+}
+
+void or_tikhonov(int M, int N, int K, const double *h, const uint8_t *mask, int iters, double tau, double *yt,
+                 double *x) {
+  size_t P = (size_t)M * N;
+  double *den = tikhonov_denominator(M, N, h, K, tau);
+  double *rhs = malloc(P * sizeof(double)), *tmp = malloc(P * sizeof(double));
+  cplx *work = malloc(sizeof(cplx) * P);
+  for (int it = 0; it < iters; ++it) {
+    or_conv_circ_adj(yt, M, N, h, K, rhs); /* H^T [y; z] = T~^T y~ */
+    solve_x(rhs, den, M, N, x, work);
+    or_conv_circ(x, M, N, h, K, tmp);
+    for (size_t i = 0; i < P; ++i)
+      if (!mask[i]) yt[i] = tmp[i]; /* z = M_z H x */
+  }
+  free(den); free(rhs); free(tmp); free(work);
+}
+
 /* ------------------------------------------------------ partial ADMM ---
- * Eqs. (admm_aprox_1)-(admm_aprox_4) with one block-Gauss-Seidel pass, the
- * closed forms (dual_x_iter_resolved_boundaries) for x and the over-relaxed
- * z-update z = relax * M_z H x - (relax - 1) z (relax = 2 in Sec. II-B,
- * relax = 1 is the plain Eq. (dual_z_iter_resolved_boundaries)).  C channels
- * share the blur; the TV norm couples them (vectorial TV, Sec. III-C).
+ * Eqs. (admm_aprox_1)-(admm_aprox_4), the closed forms
+ * (dual_x_iter_resolved_boundaries) for x and the over-relaxed z-update
+ * z = relax * M_z H x - (relax - 1) z (relax = 2 in Sec. II-B, relax = 1 is
+ * the plain Eq. (dual_z_iter_resolved_boundaries)).  C channels share the
+ * blur; the TV norm couples them (vectorial TV, Sec. III-C).
+ *
+ * passes >= 1: block-Gauss-Seidel passes of steps (admm_aprox_1)-(admm_aprox_2)
+ * per iteration (Sec. II-C: an inner loop on x and z with v and d fixed;
+ * "Proposed-AD" uses b passes for a (2b+1) x (2b+1) blur, Sec. III-B).
+ * adapt_t > 0: penalty adaptation of Eq. (varying_penalty) after every
+ * iteration with threshold t: mu doubles (d halves) when
+ * ||d^{i+1} - d^i|| > t ||v^{i+1} - v^i||, mu halves (d doubles) when
+ * ||v^{i+1} - v^i|| > t ||d^{i+1} - d^i||; norms over all channels of the
+ * image.  tikh_iters > 0 (init only): Tikhonov warm start of z (or_tikhonov
+ * per channel, tau = tikh_tau), then x^0 = its last x.
  *
  * State (in/out when init == 0, out when init == 1): yt = y~ (observed
  * entries hold y, unobserved hold z), d = d_x as [C][2][M][N] (h then v
- * component), v = v_x with the same layout.  Output x = x^{iters}.
- * stats (nullable) receives per iteration
+ * component), v = v_x with the same layout; *mu_io = mu in, the final mu out.
+ * Initial state (init == 1): y~^0 = or_init_ytilde (then the warm start, if
+ * any), d^0 = 0, v^0 = D x^0 with x^0 = y~^0, or the warm start's x.
+ * Output x = x^{iters}.  stats (nullable) receives per iteration
  *   [ ||d^{i+1}-d^i||^2, ||z^{i+1}-z^i||^2, mu ||v^{i+1}-v^i||^2, J(x^{i+1}) ]
+ * (z change and x of the last pass; d^{i+1} before the rescaling; mu = mu^i)
  * with J(x) = 1/2 sum_obs (y - T~x)^2 + lambda sum_j ||(Dx)_j||, the
- * objective of Eq. (problem_xz) minimised over z.
+ * objective of Eq. (problem_xz) minimised over z.  mu_hist (nullable)
+ * receives mu^i, the penalty each iteration used.
  */
-int or_admm(int C, int M, int N, int K, const double *h, const double *y, const uint8_t *mask,
-            double lambda, double mu, double relax, int iters, int init, int round_f32,
-            double *yt, double *d, double *v, double *x, double *stats) {
+int or_admm_ex(int C, int M, int N, int K, const double *h, const double *y, const uint8_t *mask,
+               double lambda, double *mu_io, double relax, int iters, int init, int round_f32, int passes,
+               double adapt_t, int tikh_iters, double tikh_tau, double *yt, double *d, double *v, double *x,
+               double *stats, double *mu_hist) {
   size_t P = (size_t)M * N;
+  double mu = *mu_io;
+  if (passes < 1) return 1;
   double *den = solve_denominator(M, N, h, K, mu);
   double *rhs = malloc(P * sizeof(double)), *tmp = malloc(P * sizeof(double));
   double *dx = malloc(2 * C * P * sizeof(double)), *a = malloc(2 * C * P * sizeof(double));
@@ -344,33 +401,42 @@ int or_admm(int C, int M, int N, int K, const double *h, const double *y, const 
   if (init) {
     for (int c = 0; c < C; ++c) {
       or_init_ytilde(y + c * P, mask + c * P, M, N, K, round_f32, yt + c * P);
-      or_diff_fwd(yt + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P); /* v0 = D x0, x0 = y~0 */
+      if (tikh_iters > 0) {
+        or_tikhonov(M, N, K, h, mask + c * P, tikh_iters, tikh_tau, yt + c * P, x + c * P);
+        or_diff_fwd(x + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P); /* v0 = D x0, x0 = warm-start x */
+      } else {
+        or_diff_fwd(yt + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P); /* v0 = D x0, x0 = y~0 */
+      }
     }
     memset(d, 0, 2 * C * P * sizeof(double));
   }
   for (int it = 0; it < iters; ++it) {
-    /* (admm_aprox_1): x = (H^T H + mu D^T D)^{-1} [H^T [y; z] + mu D^T (v - d)] */
-    for (int c = 0; c < C; ++c) {
-      double *uh = a + 2 * c * P, *uv = a + (2 * c + 1) * P;
-      for (size_t i = 0; i < P; ++i) {
-        uh[i] = v[2 * c * P + i] - d[2 * c * P + i];
-        uv[i] = v[(2 * c + 1) * P + i] - d[(2 * c + 1) * P + i];
-      }
-      or_diff_adj(uh, uv, M, N, tmp);
-      or_conv_circ_adj(yt + c * P, M, N, h, K, rhs);
-      for (size_t i = 0; i < P; ++i) rhs[i] += mu * tmp[i];
-      solve_x(rhs, den, M, N, x + c * P, work);
-    }
-    /* (admm_aprox_2), over-relaxed: z = relax M_z H x - (relax - 1) z */
+    if (mu_hist) mu_hist[it] = mu;
     double dz2 = 0.0;
-    for (int c = 0; c < C; ++c) {
-      or_conv_circ(x + c * P, M, N, h, K, tmp);
-      for (size_t i = 0; i < P; ++i)
-        if (!mask[c * P + i]) {
-          double zn = relax * tmp[i] - (relax - 1.0) * yt[c * P + i];
-          dz2 += (zn - yt[c * P + i]) * (zn - yt[c * P + i]);
-          yt[c * P + i] = zn;
+    for (int pass = 0; pass < passes; ++pass) {
+      /* (admm_aprox_1): x = (H^T H + mu D^T D)^{-1} [H^T [y; z] + mu D^T (v - d)] */
+      for (int c = 0; c < C; ++c) {
+        double *uh = a + 2 * c * P, *uv = a + (2 * c + 1) * P;
+        for (size_t i = 0; i < P; ++i) {
+          uh[i] = v[2 * c * P + i] - d[2 * c * P + i];
+          uv[i] = v[(2 * c + 1) * P + i] - d[(2 * c + 1) * P + i];
         }
+        or_diff_adj(uh, uv, M, N, tmp);
+        or_conv_circ_adj(yt + c * P, M, N, h, K, rhs);
+        for (size_t i = 0; i < P; ++i) rhs[i] += mu * tmp[i];
+        solve_x(rhs, den, M, N, x + c * P, work);
+      }
+      /* (admm_aprox_2), over-relaxed: z = relax M_z H x - (relax - 1) z */
+      dz2 = 0.0;
+      for (int c = 0; c < C; ++c) {
+        or_conv_circ(x + c * P, M, N, h, K, tmp);
+        for (size_t i = 0; i < P; ++i)
+          if (!mask[c * P + i]) {
+            double zn = relax * tmp[i] - (relax - 1.0) * yt[c * P + i];
+            dz2 += (zn - yt[c * P + i]) * (zn - yt[c * P + i]);
+            yt[c * P + i] = zn;
+          }
+      }
     }
     /* (admm_aprox_3): v = vector-soft(D x + d, lambda / mu) */
     for (int c = 0; c < C; ++c) or_diff_fwd(x + c * P, M, N, dx + 2 * c * P, dx + (2 * c + 1) * P);
@@ -402,9 +468,31 @@ int or_admm(int C, int M, int N, int K, const double *h, const double *y, const 
       stats[4 * it + 2] = mu * dv2;
       stats[4 * it + 3] = 0.5 * fit + lambda * tv;
     }
+    /* Eq. (varying_penalty) and the rescaling of d */
+    if (adapt_t > 0.0) {
+      double nd = sqrt(dd2), nv = sqrt(dv2), f = 1.0;
+      if (nd > adapt_t * nv) f = 2.0;
+      else if (nv > adapt_t * nd) f = 0.5;
+      if (f != 1.0) {
+        mu *= f;
+        for (size_t i = 0; i < 2 * C * P; ++i) d[i] /= f;
+        free(den);
+        den = solve_denominator(M, N, h, K, mu);
+      }
+    }
   }
+  *mu_io = mu;
   free(den); free(rhs); free(tmp); free(dx); free(a); free(vn); free(work);
   return 0;
+}
+
+/* One BGS pass, fixed mu, no warm start (the iteration the paper calls
+ * Proposed-1). */
+int or_admm(int C, int M, int N, int K, const double *h, const double *y, const uint8_t *mask,
+            double lambda, double mu, double relax, int iters, int init, int round_f32,
+            double *yt, double *d, double *v, double *x, double *stats) {
+  return or_admm_ex(C, M, N, K, h, y, mask, lambda, &mu, relax, iters, init, round_f32, 1, 0.0, 0, 0.0, yt, d, v, x,
+                    stats, NULL);
 }
 
 /* --------------------------------------------------- reverse pass (grad) ---
