@@ -110,6 +110,30 @@ deconv_status deconv_plan_create(deconv_plan *out, const deconv_dims *dims, cons
 deconv_status deconv_solve(deconv_plan plan, const void *y, void *x, int32_t iters, int32_t warm,
                            double *stats);
 
+/* Variants of the iteration (Sec. II-C and III-B), applied by every later
+ * deconv_solve / deconv_solve_host call of the plan.
+ *   bgs_passes: block-Gauss-Seidel passes of the x- and z-steps per iteration
+ *     (Eqs. (admm_aprox_1)-(admm_aprox_2) repeated with v and d fixed), 1..64.
+ *     1 is the paper's Proposed-1; b for a (2b+1) x (2b+1) blur its
+ *     Proposed-AD.  The statistics describe the last pass.
+ *   tikh_iters, tikh_tau: a fresh solve (warm = 0) first runs tikh_iters >= 0
+ *     steps of the Tikhonov initialisation of Eqs. (ini_x)-(ini_z)
+ *     (x = (H^T H + tau I)^{-1} H^T [y; z], z = M_z H x, no over-relaxation,
+ *     tau = tikh_tau > 0; the paper uses 100 steps and tau = 1e-3), then starts
+ *     the ADMM from y~ = [y; z], x^0 = the last x, v^0 = D x^0, d^0 = 0.
+ *   adapt_t: 0 keeps mu fixed; >= 1 enables the penalty adaptation of
+ *     Eq. (varying_penalty) with threshold t (the paper uses 3) per image.
+ * Defaults: {1, 0, 1e-3, 0}.  Returns DECONV_EINVAL for values out of range.
+ * deconv_grad supports the defaults only (DECONV_EUNSUPPORTED otherwise). */
+typedef struct {
+  int32_t bgs_passes;
+  int32_t tikh_iters;
+  double tikh_tau;
+  double adapt_t;
+} deconv_options;
+
+deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
+
 /* Same as deconv_solve with warm = 0 and no statistics, but y_host and
  * x_host are HOST buffers (pinned or pageable) in the batch layout: the call
  * copies y to the device, runs, copies x back and synchronises the stream

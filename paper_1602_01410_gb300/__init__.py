@@ -29,7 +29,8 @@ DECONV_F32, DECONV_F64 = 0, 1
 EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "deconv_solve_host",
            "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
-           "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches")
+           "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches",
+           "deconv_set_options")
 
 
 class DeconvError(RuntimeError):
@@ -44,6 +45,11 @@ class deconv_dims(ctypes.Structure):
                 ("rows", ctypes.POINTER(ctypes.c_int32)), ("cols", ctypes.POINTER(ctypes.c_int32)),
                 ("ksize", ctypes.c_int32), ("kernel_per_image", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("relax", ctypes.c_float)]
+
+
+class deconv_options(ctypes.Structure):
+    _fields_ = [("bgs_passes", ctypes.c_int32), ("tikh_iters", ctypes.c_int32),
+                ("tikh_tau", ctypes.c_double), ("adapt_t", ctypes.c_double)]
 
 
 _lib = None
@@ -76,6 +82,7 @@ def load() -> ctypes.CDLL:
         lib.deconv_state_get.argtypes = [vp, vp]
         lib.deconv_state_set.argtypes = [vp, vp]
         lib.deconv_last_error.argtypes = []
+        lib.deconv_set_options.argtypes = [vp, ctypes.POINTER(deconv_options)]
         lib.deconv_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("deconv_status_string", "deconv_last_error"):
@@ -189,6 +196,12 @@ def deconv_state_set(plan: int, blob_ptr: int) -> None:
     _check(load().deconv_state_set(plan, blob_ptr), "deconv_state_set")
 
 
+def deconv_set_options(plan: int, bgs_passes: int = 1, tikh_iters: int = 0, tikh_tau: float = 1e-3,
+                       adapt_t: float = 0.0) -> None:
+    o = deconv_options(int(bgs_passes), int(tikh_iters), float(tikh_tau), float(adapt_t))
+    _check(load().deconv_set_options(plan, ctypes.byref(o)), "deconv_set_options")
+
+
 def deconv_plan_destroy(plan: int) -> None:
     _check(load().deconv_plan_destroy(plan), "deconv_plan_destroy")
 
@@ -245,6 +258,11 @@ class Plan:
         loss, dlam = deconv_grad(self.handle, y.data_ptr(), x_true.data_ptr(), iters, ckpt_every, gptr, n,
                                  dh.data_ptr(), None if x_out is None else x_out.data_ptr())
         return loss, dlam, dh
+
+    def set_options(self, bgs_passes: int = 1, tikh_iters: int = 0, tikh_tau: float = 1e-3,
+                    adapt_t: float = 0.0) -> None:
+        """BGS passes per iteration, Tikhonov warm start, penalty adaptation (see deconv.h)."""
+        deconv_set_options(self.handle, bgs_passes, tikh_iters, tikh_tau, adapt_t)
 
     def solve_host(self, y_host, x_host, iters: int) -> None:
         deconv_solve_host(self.handle, y_host.data_ptr(), x_host.data_ptr(), iters)

@@ -36,7 +36,13 @@ struct ImageDesc {
 // forward: (Y_row, R_row) = row spectra of y~ and r; inverse: (X_row, HX_row).
 template <typename T> struct alignas(4 * sizeof(T)) cpair { T ar, ai, br, bi; };
 
-enum RowMode { ROW_ITER = 0, ROW_INIT = 1, ROW_ADJ = 2 };
+// ROW_ITER: one iteration's row pass.  ROW_INIT: the initial state from y~0.
+// ROW_ADJ: reverse pass.  ROW_INNER: an inner block-Gauss-Seidel pass (and a
+// Tikhonov warm-start step): z-update, then the row spectrum of y~ alone into
+// the Y half of the row-spectral intermediate (the R half is kept).
+// ROW_WARM: the last warm-start step: z-update, then the initial state with
+// x^0 = the x just computed (d^0 = 0, v^0 = D x^0).
+enum RowMode { ROW_ITER = 0, ROW_INIT = 1, ROW_ADJ = 2, ROW_INNER = 3, ROW_WARM = 4 };
 
 template <typename T> struct RowArgs {
   const ImageDesc *desc;
@@ -69,6 +75,7 @@ template <typename T> struct ColArgs {
   const void *tw2;    // cx<T>, [k1][t] layout
   const T *s2;        // 4 sin^2 tables
   T mu;
+  T tikh;             // > 0: Tikhonov warm-start step, X = conj(H) Y / (|H|^2 + tikh) (R ignored)
   int *err;
   // Reverse pass only (power-of-two column pass):
   cpair<T> *spec_store;       // nullable: store (Y^, R^) after the forward column DFTs

@@ -133,7 +133,9 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
   cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
   T *bufr = reinterpret_cast<T *>(smem_raw);  // scalar view: x at 2k, second slot at 2k+1
   T *G = reinterpret_cast<T *>(buf + (size_t)N * ld);
-  const bool init = a.mode == ROW_INIT;
+  const bool init = a.mode == ROW_INIT;                            // x = y~0, no z-update
+  const bool g_one = init || a.mode == ROW_WARM;                   // initial state: d = 0, v = D x
+  const bool inner = a.mode == ROW_INNER;                          // z-update and Y spectrum only
   const cx<T> *din = reinterpret_cast<const cx<T> *>(a.d_in);
   cx<T> *dout = reinterpret_cast<cx<T> *>(a.d_out);
 
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
       const int sg = ch * nh + h;
       const T x0 = bufr[2 * (n * ld + sg)], xr = bufr[2 * (n1 * ld + sg)], xd = bufr[2 * (n * ld + sg + 1)];
       const T gh = xr - x0, gv = xd - x0;
-      cx<T> dold = din ? din[px0 + ch * P + (long long)i * N + n] : mk<T>(T(0), T(0));
+      cx<T> dold = (din && !inner) ? din[px0 + ch * P + (long long)i * N + n] : mk<T>(T(0), T(0));
       dh0[ch] = dold.x;
       dv0[ch] = dold.y;
       ah[ch] = gh + dold.x;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
       s += ah[ch] * ah[ch] + av[ch] * av[ch];
       tv += gh * gh + gv * gv;
     }
-    const T g = init ? T(1) : (s > tau2 ? T(1) - tau * rsqrt_t<T>(s) : T(0));
+    const T g = g_one ? T(1) : (s > tau2 ? T(1) - tau * rsqrt_t<T>(s) : T(0));
     G[h * N + n] = g;
     if (h >= 1) {
 #pragma unroll
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
         const int sg = ch * nh + h;
         const long long o = px0 + ch * P + (long long)i * N + n;
         const T dnh = (T(1) - g) * ah[ch], dnv = (T(1) - g) * av[ch];
-        dout[o] = mk<T>(dnh, dnv);
+        if (!inner) dout[o] = mk<T>(dnh, dnv);
         if (stats) s_dd += (dnh - dh0[ch]) * (dnh - dh0[ch]) + (dnv - dv0[ch]) * (dnv - dv0[ch]);
         const T yo = a.yt[o];
         T yn = yo;
@@ -232,12 +234,13 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
         const T x0 = bufr[2 * (n * ld + sg)], xl = bufr[2 * (nm * ld + sg)], xr = bufr[2 * (n1 * ld + sg)];
         const T xd = bufr[2 * (n * ld + sg + 1)], xu = bufr[2 * (n * ld + sg - 1)];
         const long long rowo = px0 + ch * P;
-        cx<T> d0 = din ? din[rowo + (long long)i * N + n] : mk<T>(T(0), T(0));
-        cx<T> dl = din ? din[rowo + (long long)i * N + nm] : mk<T>(T(0), T(0));
-        cx<T> du = din ? din[rowo + (long long)iu * N + n] : mk<T>(T(0), T(0));
+        const bool rd = din && !inner;
+        cx<T> d0 = rd ? din[rowo + (long long)i * N + n] : mk<T>(T(0), T(0));
+        cx<T> dl = rd ? din[rowo + (long long)i * N + nm] : mk<T>(T(0), T(0));
+        cx<T> du = rd ? din[rowo + (long long)iu * N + n] : mk<T>(T(0), T(0));
         const T uh0 = g0 * (xr - x0 + d0.x), uhl = gl * (x0 - xl + dl.x);
         const T uv0 = g0 * (xd - x0 + d0.y), uvu = gu * (x0 - xu + du.y);
-        const T r = a.mu * ((uhl - uh0) + (uvu - uv0));
+        const T r = inner ? T(0) : a.mu * ((uhl - uh0) + (uvu - uv0));
         const T yv = bufr[2 * (n * ld + sg) + 1];
         keep_y[k * C + ch] = yv;
         keep_r[k * C + ch] = r;
@@ -274,7 +277,11 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
       q.ai = T(0.5) * (c1.y - c2.y);
       q.br = T(0.5) * (c1.y + c2.y);
       q.bi = T(0.5) * (c2.x - c1.x);
-      st_pair(&a.S_out[spec0 + ((long long)ch * M + i) * Nh + k], q);
+      cpair<T> *dst = &a.S_out[spec0 + ((long long)ch * M + i) * Nh + k];
+      if (inner)
+        *reinterpret_cast<cx<T> *>(dst) = mk<T>(q.ar, q.ai);  // Y only; the R half is kept
+      else
+        st_pair(dst, q);
     }
   }
 
@@ -319,13 +326,13 @@ __global__ void __launch_bounds__(NT) col_pass_kernel(ColArgs<T> a) {
   fft_smem<T, NT, -1>(buf, M, S, ld, sc, tw);
 
   // Spectral solve of the x-step and the blur of its result.
-  const T mu = a.mu, scale = T(1) / (T(M) * T(N));
+  const T mu = a.mu, tikh = a.tikh, scale = T(1) / (T(M) * T(N));
   for (int e = threadIdx.x; e < M * w; e += NT) {
     const int k1 = e / w, ww = e - k1 * w, k2 = k20 + ww;
     const cx<T> h = __ldg(&H[(long long)k1 * Nh + k2]);
-    const T den = h.x * h.x + h.y * h.y + mu * (__ldg(&s2c[k1]) + __ldg(&s2r[k2]));
+    const T den = h.x * h.x + h.y * h.y + (tikh > T(0) ? tikh : mu * (__ldg(&s2c[k1]) + __ldg(&s2r[k2])));
     const T inv = scale / den;
-    const cx<T> Y = buf[k1 * ld + 2 * ww], R = buf[k1 * ld + 2 * ww + 1];
+    const cx<T> Y = buf[k1 * ld + 2 * ww], R = tikh > T(0) ? mk<T>(T(0), T(0)) : buf[k1 * ld + 2 * ww + 1];
     const cx<T> X = cscale<T>(cadd<T>(cmulc<T>(h, Y), R), inv);
     buf[k1 * ld + 2 * ww] = X;
     buf[k1 * ld + 2 * ww + 1] = cmul<T>(h, X);

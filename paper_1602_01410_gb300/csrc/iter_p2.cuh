@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
   const bool init = a.mode == ROW_INIT;
-  const bool adj = a.mode == ROW_ADJ;  // reverse pass: xbuf <- b, yt <- yt + T~b
+  const bool adj = a.mode == ROW_ADJ;      // reverse pass: xbuf <- b, yt <- yt + T~b
+  const bool inner = a.mode == ROW_INNER;  // then the row spectrum of y~ into the Y half of S_out
+  const unsigned gm = group_mask(TT);
   // Distinct buffers (x_out is written only when it is not the x buffer).
   T *__restrict__ yt = a.yt;
   T *__restrict__ xbuf = a.xbuf;
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
       }
     }
   }
-  if (!init) fft_mixed<T, TT, R, +1>(v, active, tile, q, group_mask(TT), gr, tw2, tw3, Ex);
+  if (!init) fft_mixed<T, TT, R, +1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
   cp_async_wait_all();
   __syncthreads();
   if (active && adj) {
@@ -145,13 +147,35 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
       if (xout) xout[rowp + p] = v[j].x;
       if (!init) {
         const T yo = yrow[p];
+        T ynew = yo;
         if (!((mrow[p >> 5] >> (p & 31)) & 1u)) {
           const T yn = relax * v[j].y - (relax - T(1)) * yo;
           yt[rowp + p] = yn;
+          ynew = yn;
           if (stats) s_dz += (yn - yo) * (yn - yo);
         } else if (stats) {
           s_fit += (yo - v[j].y) * (yo - v[j].y);
         }
+        if (inner) Ex[p] = mk<T>(ynew, T(0));
+      }
+    }
+  }
+  if (inner) {
+    // Forward row DFT of the updated y~ (real input: its spectrum is Y_row,
+    // Hermitian, of which k <= N/2 is stored).
+    if (R > 1) __syncthreads(); else __syncwarp(gm);
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < 32; ++m) v[m] = Ex[R * (q + TT * m) + gr];
+    }
+    if (R > 1) __syncthreads(); else __syncwarp(gm);
+    fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+    if (active) {
+      cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int k = q + TT * p2_slot<TT>(j) + L2 * gr;
+        if (2 * k <= N) *reinterpret_cast<cx<T> *>(&dst[k]) = v[j];
       }
     }
   }
@@ -192,7 +216,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
   const int iu = i == 0 ? M - 1 : i - 1, id = i + 1 == M ? 0 : i + 1;
-  const bool init = a.mode == ROW_INIT;
+  const bool init = a.mode == ROW_INIT || a.mode == ROW_WARM;  // d = 0, v = D x
   const T *__restrict__ xg = a.xbuf + px0;
   const cx<T> *__restrict__ dg = reinterpret_cast<const cx<T> *>(a.d_in) + px0;
   const T *__restrict__ yg = a.yt + px0;
@@ -323,7 +347,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
-  const bool init = a.mode == ROW_INIT;
+  const bool init = a.mode == ROW_INIT || a.mode == ROW_WARM;  // d = 0, v = D x
   cx<T> *__restrict__ dout = reinterpret_cast<cx<T> *>(a.d_out);
   T *Xs = reinterpret_cast<T *>(smem_raw);                               // [C][Rb+2][N]
   cx<T> *Ds = reinterpret_cast<cx<T> *>(Xs + (size_t)C * (Rb + 2) * N);  // [C][Rb+1][N]
@@ -504,7 +528,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     for (int j = 0; j < 32; ++j) col[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
   }
   __syncthreads();
-  const T mu = a.mu, scale = T(1) / (T(M) * T(N));
+  const T mu = a.mu, tikh = a.tikh, scale = T(1) / (T(M) * T(N));
   if (lane_ok && scol < w) {
     const int ww = scol;
     const T s2w = S2s[M + ww];
@@ -512,9 +536,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     cx<T> *cy = St + (size_t)(2 * ww) * SR, *cr = cy + SR;
     for (int k1 = r0t; k1 < M; k1 += rstep) {
       const cx<T> hv = Hs[k1 * w + ww];
-      const T den = hv.x * hv.x + hv.y * hv.y + mu * (S2s[k1] + s2w);
+      const T den = hv.x * hv.x + hv.y * hv.y + (tikh > T(0) ? tikh : mu * (S2s[k1] + s2w));
       const T inv = scale / den;
-      const cx<T> Y = cy[k1], Rv = cr[k1];
+      const cx<T> Y = cy[k1], Rv = tikh > T(0) ? mk<T>(T(0), T(0)) : cr[k1];
       const cx<T> B = cadd<T>(cmulc<T>(hv, Y), Rv);  // den * (solution spectrum)
       if (a.spec_store) {
         cpair<T> o;

@@ -427,6 +427,11 @@ struct deconv_plan_s {
   float relax = 2.0f;
   int parity = 0;
   bool have_state = false;
+  // Options (deconv_set_options): BGS passes per iteration, Tikhonov warm start, penalty adaptation.
+  int passes = 1;
+  int tikh_iters = 0;
+  double tikh_tau = 1e-3;
+  double adapt_t = 0.0;
   cudaGraphExec_t gexec = nullptr;
   // While a graph is captured: the kernel classes of one pass (disjoint sets
   // of images) fan out over side streams, so their launches run concurrently.
@@ -457,7 +462,7 @@ deconv_status cuda_fail(cudaError_t e, int line) {
 
 template <typename T>
 RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_in, T *d_out, T *x_out,
-                    double *partials) {
+                    double *partials, double relax) {
   const Layout &L = p->L;
   RowArgs<T> a{};
   a.desc = p->at<ImageDesc>(L.o_desc);
@@ -474,7 +479,7 @@ RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_i
   a.tw2 = p->ws + L.o_tw2;
   a.mu = (T)p->mu;
   a.tau = (T)(p->lambda / p->mu);
-  a.relax = (T)p->relax;
+  a.relax = (T)relax;
   a.lambda = (T)p->lambda;
   a.x_out = x_out;
   a.xbuf = p->at<T>(L.o_xbuf);
@@ -484,7 +489,7 @@ RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_i
 }
 
 template <typename T>
-ColArgs<T> col_args(const deconv_plan_s *p, const Cls &c) {
+ColArgs<T> col_args(const deconv_plan_s *p, const Cls &c, double tikh) {
   const Layout &L = p->L;
   ColArgs<T> a{};
   a.desc = p->at<ImageDesc>(L.o_desc);
@@ -497,6 +502,7 @@ ColArgs<T> col_args(const deconv_plan_s *p, const Cls &c) {
   a.tw2 = p->ws + L.o_tw2;
   a.s2 = p->at<T>(L.o_s2);
   a.mu = (T)p->mu;
+  a.tikh = (T)tikh;
   a.err = p->at<int>(L.o_err);
   return a;
 }
@@ -538,25 +544,38 @@ cudaError_t each_class(deconv_plan_s *p, cudaStream_t s, size_t n, F fn) {
 }
 
 // One iteration (column pass then row pass), d ping-pong by plan parity.
+// tikh > 0: a Tikhonov warm-start step (denominator |H|^2 + tikh, R ignored).
 template <typename T>
-cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s) {
+cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s, double tikh = 0.0) {
   const auto &cl = p->L.col_cls;
-  return each_class(p, s, cl.size(),
-                    [&](size_t k, cudaStream_t sk) { return launch_col<T>(col_args<T>(p, cl[k]), cl[k].cfg, sk); });
+  return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+    return launch_col<T>(col_args<T>(p, cl[k], tikh), cl[k].cfg, sk);
+  });
 }
 
+// relax < 0: the plan's over-relaxation.  ROW_INNER runs the inverse half
+// alone on the register-FFT classes (it ends with the forward spectrum of y~).
 template <typename T>
 cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, T *d_out, T *x_out,
-                     double *partials) {
+                     double *partials, double relax = -1.0) {
   const auto &cl = p->L.row_cls;
+  const double rx = relax < 0.0 ? p->relax : relax;
   return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
-    return launch_row<T>(row_args<T>(p, cl[k], mode, d_in, d_out, x_out, partials), cl[k].cfg, sk);
+    const RowArgs<T> a = row_args<T>(p, cl[k], mode, d_in, d_out, x_out, partials, rx);
+    if (mode == ROW_INNER && cl[k].cfg.kind == KIND_P2) return launch_row_half<T>(a, cl[k].cfg, 0, sk);
+    return launch_row<T>(a, cl[k].cfg, sk);
   });
 }
 
 template <typename T>
 deconv_status iterate(deconv_plan_s *p, cudaStream_t s, T *x_out, double *stats, int iters, int it) {
   const Layout &L = p->L;
+  // Inner BGS passes: x- and z-steps with v and d (hence the R half of the
+  // row-spectral intermediate) held fixed.
+  for (int k = 0; k + 1 < p->passes; ++k) {
+    CK(col_pass<T>(p, s));
+    CK(row_pass<T>(p, s, ROW_INNER, nullptr, nullptr, nullptr, nullptr));
+  }
   CK(col_pass<T>(p, s));
   double *partials = stats ? p->at<double>(L.o_partials) : nullptr;
   CK(row_pass<T>(p, s, ROW_ITER, dbuf<T>(p, p->parity), dbuf<T>(p, p->parity ^ 1), x_out, partials));
@@ -575,7 +594,17 @@ deconv_status init_state(deconv_plan_s *p, const T *y, T *x_out) {
   CK(launch_init_fill<T>(desc, L.B, L.total_px, p->at<long long>(L.o_pxbeg), y, p->at<uint32_t>(L.o_bits),
                          p->at<double>(L.o_means), L.K, p->at<T>(L.o_yt), s));
   p->parity = 0;
-  CK(row_pass<T>(p, s, ROW_INIT, nullptr, dbuf<T>(p, 0), x_out, nullptr));
+  const int nt = p->tikh_iters;
+  CK(row_pass<T>(p, s, ROW_INIT, nullptr, dbuf<T>(p, 0), nt > 0 ? nullptr : x_out, nullptr));
+  // Tikhonov warm start (Eqs. (ini_x)-(ini_z)): x = (H^T H + tau I)^{-1} H^T y~,
+  // z = M_z H x (no over-relaxation); the last step leaves x^0 = its x, d^0 = 0.
+  for (int k = 0; k < nt; ++k) {
+    CK(col_pass<T>(p, s, p->tikh_tau));
+    if (k + 1 < nt)
+      CK(row_pass<T>(p, s, ROW_INNER, nullptr, nullptr, nullptr, nullptr, 1.0));
+    else
+      CK(row_pass<T>(p, s, ROW_WARM, nullptr, dbuf<T>(p, 0), x_out, nullptr, 1.0));
+  }
   p->have_state = true;
   return DECONV_OK;
 }
@@ -780,6 +809,7 @@ size_t adj_smem(int C, int N, int rb, int tt, size_t esz) {
 }
 
 deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *G) {
+  if (p->passes != 1 || p->tikh_iters != 0 || p->adapt_t != 0.0) return DECONV_EUNSUPPORTED;
   const Layout &L = p->L;
   if (iters < 1 || k < 1) return DECONV_EINVAL;
   for (const auto *v : {&L.row_cls, &L.col_cls})
@@ -891,7 +921,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
     for (int j = s0; j < s1; ++j) {
       const int jj = j - s0;
       for (const Cls &cl : L.col_cls) {
-        ColArgs<T> ca = col_args<T>(p, cl);
+        ColArgs<T> ca = col_args<T>(p, cl, 0.0);
         ca.spec_store = reinterpret_cast<cpair<T> *>(at(G.o_segSpec) + jj * spec);
         CK(launch_col<T>(ca, cl.cfg, s));
       }
@@ -906,7 +936,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
       if (!start) {
         // C_{j+1} (first half): inverse row DFT of (bb, T~bb); yb += T~bb.
         for (const Cls &cl : L.row_cls) {
-          RowArgs<T> ra = row_args<T>(p, cl, ROW_ADJ, nullptr, nullptr, nullptr, nullptr);
+          RowArgs<T> ra = row_args<T>(p, cl, ROW_ADJ, nullptr, nullptr, nullptr, nullptr, p->relax);
           ra.S_in = reinterpret_cast<const cpair<T> *>(at(G.o_Sr1));
           ra.xbuf = reinterpret_cast<T *>(at(G.o_bbuf));
           ra.yt = reinterpret_cast<T *>(at(G.o_ybar));
@@ -947,7 +977,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
       CK(launch_add(res + 1, res + 2, s));
       // B_j: the x-step solve of the adjoint pair and the h-gradient spectrum.
       for (const Cls &cl : L.col_cls) {
-        ColArgs<T> ca = col_args<T>(p, cl);
+        ColArgs<T> ca = col_args<T>(p, cl, 0.0);
         ca.S_in = reinterpret_cast<const cpair<T> *>(at(G.o_Sr0));
         ca.S_out = reinterpret_cast<cpair<T> *>(at(G.o_Sr1));
         ca.spec_fwd = reinterpret_cast<const cpair<T> *>(at(G.o_segSpec) + jj * spec);
@@ -1037,6 +1067,23 @@ deconv_status deconv_plan_create(deconv_plan *out, const deconv_dims *dims, cons
     return st;
   }
   *out = p;
+  return DECONV_OK;
+}
+
+deconv_status deconv_set_options(deconv_plan p, const deconv_options *o) {
+  if (!p || !o) return DECONV_EINVAL;
+  if (o->bgs_passes < 1 || o->bgs_passes > 64 || o->tikh_iters < 0 || !(o->tikh_tau > 0.0) ||
+      !(o->adapt_t == 0.0 || o->adapt_t >= 1.0) || !std::isfinite(o->tikh_tau) || !std::isfinite(o->adapt_t))
+    return DECONV_EINVAL;
+  if (o->adapt_t != 0.0) return DECONV_EUNSUPPORTED;
+  if (o->bgs_passes != p->passes && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);  // the captured iteration has a different pass count
+    p->gexec = nullptr;
+  }
+  p->passes = o->bgs_passes;
+  p->tikh_iters = o->tikh_iters;
+  p->tikh_tau = o->tikh_tau;
+  p->adapt_t = o->adapt_t;
   return DECONV_OK;
 }
 
@@ -1167,8 +1214,13 @@ deconv_status deconv_kernel_launches(deconv_plan p, int32_t iters, int32_t mode,
   const Layout &L = p->L;
   long long row = 0, col = (long long)L.col_cls.size();
   for (const Cls &c : L.row_cls) row += c.cfg.kind == KIND_P2 ? 2 : 1;
-  const long long init = 3 + row;  // observed means (2 kernels), initial fill, initial row pass
-  const long long per_iter = col + row;
+  long long inner = 0;  // an inner BGS pass: the inverse half alone on register-FFT classes
+  for (const Cls &c : L.row_cls) inner += 1;
+  // observed means (2 kernels), initial fill, initial row pass, warm-start steps
+  const long long init = 3 + row + (p->tikh_iters > 0 ? (long long)p->tikh_iters * col +
+                                                            (long long)(p->tikh_iters - 1) * inner + row
+                                                      : 0);
+  const long long per_iter = col + row + (long long)(p->passes - 1) * (col + inner);
   if (mode == 0) {
     *count = init + (long long)iters * per_iter;
     return DECONV_OK;

@@ -13,8 +13,9 @@ def torch_dev():
     return torch, torch.device("cuda:0")
 
 
-def gpu_solve(prob: inputs.Problem, iters=None, stats=False, dtype=None, relax=None):
-    """Returns (list of (C, M, N) float64 arrays, stats array or None, plan)."""
+def gpu_solve(prob: inputs.Problem, iters=None, stats=False, dtype=None, relax=None, **opts):
+    """Returns (list of (C, M, N) float64 arrays, stats array or None, plan).
+    opts: deconv_set_options keywords (bgs_passes, tikh_iters, tikh_tau, adapt_t)."""
     import paper_1602_01410_gb300 as pkg
     torch, dev = torch_dev()
     dt = dtype or (torch.float32 if prob.dtype == "f32" else torch.float64)
@@ -24,6 +25,8 @@ def gpu_solve(prob: inputs.Problem, iters=None, stats=False, dtype=None, relax=N
     y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=dt, device=dev)
     plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu, channels=prob.channels,
                     relax=prob.relax if relax is None else relax)
+    if opts:
+        plan.set_options(**opts)
     st = torch.zeros((len(prob.shapes), max(iters, 1), 3), dtype=torch.float64, device=dev) if stats else None
     x = plan.solve(y, iters, stats=st)
     status = plan.sync()
@@ -41,13 +44,15 @@ def split(flat: np.ndarray, prob: inputs.Problem):
     return out
 
 
-def oracle_solve(prob: inputs.Problem, iters=None, stats=False, relax=None):
+def oracle_solve(prob: inputs.Problem, iters=None, stats=False, relax=None, bgs_passes=1, tikh_iters=0,
+                 tikh_tau=1e-3, adapt_t=0.0):
     iters = prob.iters if iters is None else iters
     xs, ss = [], []
     for j in range(len(prob.shapes)):
         x, _, s = oracle.admm(prob.y[j], prob.mask[j], prob.h, prob.lam, prob.mu, iters,
                               relax=prob.relax if relax is None else relax,
-                              round_f32=prob.dtype == "f32", stats=stats)
+                              round_f32=prob.dtype == "f32", stats=stats, passes=bgs_passes,
+                              tikh_iters=tikh_iters, tikh_tau=tikh_tau, adapt_t=adapt_t)
         xs.append(x)
         ss.append(s)
     return xs, ss

@@ -1,0 +1,85 @@
+"""GPU parity of the iteration's variants against the FP64 oracle:
+block-Gauss-Seidel passes (Sec. II-C, Proposed-AD) and the Tikhonov warm
+start (Eqs. (ini_x)-(ini_z)), on register-FFT lengths (powers of two,
+3 * 2^k), generic lengths and both channel counts.
+
+Tolerances: FP32 relative L2 <= 1e-5 for one iteration, <= 1e-4 for a few;
+the warm start with tau = 1e-3 divides by |H|^2 + 1e-3, which amplifies FP32
+rounding where |H| is small (<= 1e-3 after 20 steps); FP64 <= 1e-10."""
+import numpy as np
+import pytest
+
+from paper_1602_01410_gb300 import inputs
+
+from gpu_helpers import gpu_solve, oracle_solve, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(96, 160), (128, 128), (384, 256), (45, 75), (256, 384)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def check(prob, tol, **opts):
+    xg, _, _ = gpu_solve(prob, **opts)
+    xo, _ = oracle_solve(prob, **opts)
+    for a, b in zip(xg, xo):
+        assert rel_l2([a], [b]) <= tol
+
+
+def test_bgs_passes_one_iteration():
+    check(inputs.random_problem(41, SIZES, 7, mask_kind="random", frac=0.4, iters=1), 1e-5, bgs_passes=3)
+
+
+def test_bgs_passes_proposed_ad_ten_iterations():
+    prob = inputs.random_problem(42, [(128, 256), (96, 160)], 9, mask_kind="random", frac=0.3, iters=10,
+                                 psf="motion")
+    check(prob, 1e-4, bgs_passes=4)
+
+
+def test_bgs_passes_vectorial_tv():
+    prob = inputs.random_problem(43, [(128, 128), (60, 48), (384, 384)], 5, mask_kind="bayer", channels=3, iters=3)
+    check(prob, 3e-5, bgs_passes=2)
+
+
+def test_bgs_passes_fp64():
+    prob = inputs.random_problem(44, [(64, 64), (48, 60)], 5, mask_kind="random", frac=0.3, iters=4, dtype="f64")
+    check(prob, 1e-10, bgs_passes=3)
+
+
+def test_bgs_graph_replay_equals_direct_launches():
+    prob = inputs.random_problem(45, [(64, 80), (128, 128)], 5, mask_kind="random", frac=0.3, iters=45)
+    a, _, _ = gpu_solve(prob, bgs_passes=2)
+    b, _, _ = gpu_solve(prob, stats=True, bgs_passes=2)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
+def test_tikhonov_warm_start_alone():
+    prob = inputs.random_problem(46, SIZES, 7, mask_kind="random", frac=0.4, iters=0)
+    check(prob, 1e-5, tikh_iters=20, tikh_tau=0.1)
+    check(prob, 1e-3, tikh_iters=20, tikh_tau=1e-3)
+
+
+def test_tikhonov_then_admm():
+    prob = inputs.random_problem(47, [(128, 256), (96, 160)], 9, mask_kind="crop", iters=5, psf="uniform")
+    check(prob, 1e-4, tikh_iters=10, tikh_tau=0.05)
+
+
+def test_tikhonov_vectorial_fp64():
+    prob = inputs.random_problem(48, [(64, 64), (48, 60)], 5, mask_kind="bayer", channels=3, iters=3, dtype="f64")
+    check(prob, 1e-10, tikh_iters=15, tikh_tau=1e-3, bgs_passes=2)
+
+
+def test_options_validated():
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(49, [(32, 32)], 3, iters=1)
+    _, _, plan = gpu_solve(prob)
+    for bad in ({"bgs_passes": 0}, {"bgs_passes": 65}, {"tikh_iters": -1}, {"tikh_tau": 0.0}, {"adapt_t": 0.5}):
+        with pytest.raises(pkg.DeconvError) as e:
+            plan.set_options(**bad)
+        assert e.value.status == pkg.DECONV_EINVAL
