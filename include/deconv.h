@@ -124,6 +124,10 @@ deconv_status deconv_solve(deconv_plan plan, const void *y, void *x, int32_t ite
  *   adapt_t: 0 keeps mu fixed; >= 1 enables the penalty adaptation of
  *     Eq. (varying_penalty) with threshold t (the paper uses 3) per image.
  * Defaults: {1, 0, 1e-3, 0}.  Returns DECONV_EINVAL for values out of range.
+ * Under adaptation every iteration adds a residual-norm pass over x and d
+ * (the norms of Eq. (varying_penalty) are over all pixels of an image, so
+ * they are complete only after that pass) before the forward half that
+ * builds r with mu^{i+1}; v is kept in the workspace.
  * deconv_grad supports the defaults only (DECONV_EUNSUPPORTED otherwise). */
 typedef struct {
   int32_t bgs_passes;
@@ -133,6 +137,13 @@ typedef struct {
 } deconv_options;
 
 deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
+
+/* The penalty mu each image's next iteration uses (mu_host: host, batch
+ * doubles).  With adaptation off, or before the first fresh solve after it
+ * was switched on, every entry is the plan's mu.  Synchronises the stream.
+ * Under adaptation a warm solve (warm = 1) needs a fresh solve first
+ * (DECONV_EINVAL otherwise); state blobs do not carry mu or v. */
+deconv_status deconv_get_mu(deconv_plan plan, double *mu_host);
 
 /* Same as deconv_solve with warm = 0 and no statistics, but y_host and
  * x_host are HOST buffers (pinned or pageable) in the batch layout: the call

@@ -30,7 +30,7 @@ EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "decon
            "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
            "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches",
-           "deconv_set_options")
+           "deconv_set_options", "deconv_get_mu")
 
 
 class DeconvError(RuntimeError):
@@ -83,6 +83,7 @@ def load() -> ctypes.CDLL:
         lib.deconv_state_set.argtypes = [vp, vp]
         lib.deconv_last_error.argtypes = []
         lib.deconv_set_options.argtypes = [vp, ctypes.POINTER(deconv_options)]
+        lib.deconv_get_mu.argtypes = [vp, ctypes.POINTER(dbl)]
         lib.deconv_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("deconv_status_string", "deconv_last_error"):
@@ -202,6 +203,12 @@ def deconv_set_options(plan: int, bgs_passes: int = 1, tikh_iters: int = 0, tikh
     _check(load().deconv_set_options(plan, ctypes.byref(o)), "deconv_set_options")
 
 
+def deconv_get_mu(plan: int, nimg: int):
+    out = (ctypes.c_double * nimg)()
+    _check(load().deconv_get_mu(plan, out), "deconv_get_mu")
+    return [float(v) for v in out]
+
+
 def deconv_plan_destroy(plan: int) -> None:
     _check(load().deconv_plan_destroy(plan), "deconv_plan_destroy")
 
@@ -263,6 +270,10 @@ class Plan:
                     adapt_t: float = 0.0) -> None:
         """BGS passes per iteration, Tikhonov warm start, penalty adaptation (see deconv.h)."""
         deconv_set_options(self.handle, bgs_passes, tikh_iters, tikh_tau, adapt_t)
+
+    def get_mu(self):
+        """Per-image penalty of the next iteration (list of floats)."""
+        return deconv_get_mu(self.handle, len(self.shapes))
 
     def solve_host(self, y_host, x_host, iters: int) -> None:
         deconv_solve_host(self.handle, y_host.data_ptr(), x_host.data_ptr(), iters)

@@ -42,7 +42,10 @@ template <typename T> struct alignas(4 * sizeof(T)) cpair { T ar, ai, br, bi; };
 // the Y half of the row-spectral intermediate (the R half is kept).
 // ROW_WARM: the last warm-start step: z-update, then the initial state with
 // x^0 = the x just computed (d^0 = 0, v^0 = D x^0).
-enum RowMode { ROW_ITER = 0, ROW_INIT = 1, ROW_ADJ = 2, ROW_INNER = 3, ROW_WARM = 4 };
+// ROW_NORMS (penalty adaptation): the prox of the forward half only, for the
+// per-image residual norms ||d^{i+1} - d^i||^2 and ||v^{i+1} - v^i||^2 (no
+// z-update, no d or spectrum written; v^{i+1} replaces v^i in vbuf).
+enum RowMode { ROW_ITER = 0, ROW_INIT = 1, ROW_ADJ = 2, ROW_INNER = 3, ROW_WARM = 4, ROW_NORMS = 5 };
 
 template <typename T> struct RowArgs {
   const ImageDesc *desc;
@@ -60,6 +63,13 @@ template <typename T> struct RowArgs {
   T mu, tau, relax, lambda;
   T *x_out;               // nullable: x^{i+1} for owned rows
   T *xbuf;                // plan's x buffer (power-of-two row passes: written by the inverse half)
+  // Penalty adaptation (all NULL when mu is fixed): per image mu^{i+1} (mu^i
+  // during ROW_NORMS), mu^i, and the rescaling s = mu^i / mu^{i+1} of d^{i+1};
+  // v_x per pixel as d; residual-norm partials (2 doubles per row block).
+  const double *mu_img, *mu_prev_img, *dscale_img;
+  T *vbuf;
+  double *apart;
+  double lam64;           // lambda in double (tau = lambda / mu per image)
   double *partials;       // nullable: per work item [3] = sum dd^2, dz^2, J
   int *err;
 };
@@ -76,6 +86,7 @@ template <typename T> struct ColArgs {
   const T *s2;        // 4 sin^2 tables
   T mu;
   T tikh;             // > 0: Tikhonov warm-start step, X = conj(H) Y / (|H|^2 + tikh) (R ignored)
+  const double *mu_img;  // nullable: per-image mu (penalty adaptation)
   int *err;
   // Reverse pass only (power-of-two column pass):
   cpair<T> *spec_store;       // nullable: store (Y^, R^) after the forward column DFTs
@@ -166,6 +177,12 @@ template <typename T>
 cudaError_t launch_init_fill(const ImageDesc *desc_dev, int nimg, long long total_px,
                              const long long *img_px_begin_dev, const T *y, const uint32_t *bits,
                              const double *means, int K, T *yt, cudaStream_t s);
+// Penalty adaptation (Eq. (varying_penalty)): per image, reduce the residual
+// partials of ROW_NORMS and update mu, mu_prev and the d rescaling factor.
+cudaError_t launch_mu_update(const ImageDesc *desc_dev, int nimg, const double *apart, double *mu, double *mu_prev,
+                             double *dscale, double t, cudaStream_t s);
+// mu = mu_prev = mu0, dscale = 1 for nimg images.
+cudaError_t launch_mu_fill(double *mu, double *mu_prev, double *dscale, int nimg, double mu0, cudaStream_t s);
 cudaError_t launch_stats_reduce(const ImageDesc *desc_dev, int nimg, const double *partials, double *stats,
                                 int iters, int it, int *err, cudaStream_t s);
 

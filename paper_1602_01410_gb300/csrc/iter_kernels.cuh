@@ -164,11 +164,22 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
   if (!init) fft_smem<T, NT, +1>(buf, N, S, ld, sc, tw);
 
   // 2. z-update, a = D x + d, g, d^{i+1} (rows r0-1 .. r1-1; updates only on owned rows).
-  const T tau = a.tau, tau2 = a.tau * a.tau, relax = a.relax;
+  // Penalty: fixed, or per image (adaptation): tau = lambda / mu^i, r with
+  // mu^{i+1} and d^{i+1} rescaled by s (v - s d^{i+1} = ((1+s) g - s) a).
+  const bool norms = a.mode == ROW_NORMS;  // residual norms only (no z-update, no d, no spectrum)
+  T tau = a.tau, mur = a.mu, dsc = T(1);
+  if (a.mu_img) {
+    const int img = (int)(Dp - a.desc);
+    tau = T(a.lam64 / (norms ? a.mu_img[img] : a.mu_prev_img[img]));
+    mur = T(a.mu_img[img]);
+    dsc = T(a.dscale_img[img]);
+  }
+  const T tau2 = tau * tau, relax = a.relax;
+  cx<T> *vb = reinterpret_cast<cx<T> *>(a.vbuf);
   // Statistics: per-thread partials in the working precision, only when
   // requested (the FP64 pipe is slow); FP64 for the CTA and plan reductions.
   const bool stats = a.partials != nullptr;
-  T s_dd = T(0), s_dz = T(0), s_fit = T(0), s_tv = T(0);
+  T s_dd = T(0), s_dz = T(0), s_fit = T(0), s_tv = T(0), s_dv = T(0);
   for (int e = threadIdx.x; e < (nr + 1) * N; e += NT) {
     const int h = e / N, n = e - h * N, i = wrapi(r0 - 1 + h, M);
     const int n1 = (n + 1 == N) ? 0 : n + 1;
@@ -195,7 +206,15 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
         const int sg = ch * nh + h;
         const long long o = px0 + ch * P + (long long)i * N + n;
         const T dnh = (T(1) - g) * ah[ch], dnv = (T(1) - g) * av[ch];
-        if (!inner) dout[o] = mk<T>(dnh, dnv);
+        if (norms) {
+          const cx<T> vo = vb[o], vn = mk<T>(g * ah[ch], g * av[ch]);
+          s_dd += (dnh - dh0[ch]) * (dnh - dh0[ch]) + (dnv - dv0[ch]) * (dnv - dv0[ch]);
+          s_dv += (vn.x - vo.x) * (vn.x - vo.x) + (vn.y - vo.y) * (vn.y - vo.y);
+          vb[o] = vn;
+          continue;
+        }
+        if (!inner) dout[o] = mk<T>(dsc * dnh, dsc * dnv);
+        if (g_one && vb) vb[o] = mk<T>(g * ah[ch], g * av[ch]);  // v^0 = D x^0
         if (stats) s_dd += (dnh - dh0[ch]) * (dnh - dh0[ch]) + (dnv - dv0[ch]) * (dnv - dv0[ch]);
         const T yo = a.yt[o];
         T yn = yo;
@@ -215,9 +234,19 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
       if (stats) s_tv += sqrt(tv);
     }
   }
+  if (norms) {  // uniform: the whole CTA leaves here
+    double dd = double(s_dd), dv = double(s_dv), z = 0.0;
+    block_sum3<NT>(dd, dv, z);
+    if (threadIdx.x == 0) {
+      a.apart[2 * (long long)(Dp->row_pbase + wi - Dp->row_begin)] = dd;
+      a.apart[2 * (long long)(Dp->row_pbase + wi - Dp->row_begin) + 1] = dv;
+    }
+    return;
+  }
   __syncthreads();
 
-  // 3. r = mu D^T (v - d^{i+1}) with v - d^{i+1} = (2g - 1) a, on owned rows.
+  // 3. r = mu D^T (v - d^{i+1}) with v - d^{i+1} = (2g - 1) a, on owned rows
+  //    (((1+s) g - s) a and mu^{i+1} under penalty adaptation).
   T keep_y[KMAX * C], keep_r[KMAX * C];
   bool finite = true;
 #pragma unroll
@@ -227,7 +256,8 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
       const int h = 1 + e / N, n = e - (h - 1) * N;
       const int i = r0 + h - 1, iu = wrapi(i - 1, M);
       const int nm = (n == 0) ? N - 1 : n - 1, n1 = (n + 1 == N) ? 0 : n + 1;
-      const T g0 = T(2) * G[h * N + n] - T(1), gl = T(2) * G[h * N + nm] - T(1), gu = T(2) * G[(h - 1) * N + n] - T(1);
+      const T s1 = T(1) + dsc;
+      const T g0 = s1 * G[h * N + n] - dsc, gl = s1 * G[h * N + nm] - dsc, gu = s1 * G[(h - 1) * N + n] - dsc;
 #pragma unroll
       for (int ch = 0; ch < C; ++ch) {
         const int sg = ch * nh + h;
@@ -240,7 +270,7 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
         cx<T> du = rd ? din[rowo + (long long)iu * N + n] : mk<T>(T(0), T(0));
         const T uh0 = g0 * (xr - x0 + d0.x), uhl = gl * (x0 - xl + dl.x);
         const T uv0 = g0 * (xd - x0 + d0.y), uvu = gu * (x0 - xu + du.y);
-        const T r = inner ? T(0) : a.mu * ((uhl - uh0) + (uvu - uv0));
+        const T r = inner ? T(0) : mur * ((uhl - uh0) + (uvu - uv0));
         const T yv = bufr[2 * (n * ld + sg) + 1];
         keep_y[k * C + ch] = yv;
         keep_r[k * C + ch] = r;
@@ -326,7 +356,7 @@ __global__ void __launch_bounds__(NT) col_pass_kernel(ColArgs<T> a) {
   fft_smem<T, NT, -1>(buf, M, S, ld, sc, tw);
 
   // Spectral solve of the x-step and the blur of its result.
-  const T mu = a.mu, tikh = a.tikh, scale = T(1) / (T(M) * T(N));
+  const T mu = a.mu_img ? T(a.mu_img[Dp - a.desc]) : a.mu, tikh = a.tikh, scale = T(1) / (T(M) * T(N));
   for (int e = threadIdx.x; e < M * w; e += NT) {
     const int k1 = e / w, ww = e - k1 * w, k2 = k20 + ww;
     const cx<T> h = __ldg(&H[(long long)k1 * Nh + k2]);

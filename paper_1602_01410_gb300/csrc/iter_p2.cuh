@@ -227,9 +227,20 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
   const unsigned gm = group_mask(TT);
 
-  const T tau = a.tau, tau2 = a.tau * a.tau;
+  // Penalty: fixed, or per image (adaptation): tau = lambda / mu^i, r with
+  // mu^{i+1} and d^{i+1} rescaled by s (v - s d^{i+1} = ((1+s) g - s) a).
+  const bool norms = a.mode == ROW_NORMS;
+  T tau = a.tau, mur = a.mu, sc = T(1);
+  if (a.mu_img) {
+    const int img = (int)(Dp - a.desc);
+    tau = T(a.lam64 / (norms ? a.mu_img[img] : a.mu_prev_img[img]));
+    mur = T(a.mu_img[img]);
+    sc = T(a.dscale_img[img]);
+  }
+  const T tau2 = tau * tau, sc1 = T(1) + sc;
+  cx<T> *__restrict__ vb = reinterpret_cast<cx<T> *>(a.vbuf);
   const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
-  T s_dd = T(0), s_tv = T(0);
+  T s_dd = T(0), s_tv = T(0), s_dv = T(0);
   bool finite = true;
   if (active) {
 #pragma unroll 4
@@ -271,17 +282,36 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
       const T gl = init ? T(1) : (sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0));
       const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
       const T dnh = (T(1) - g0) * ah0, dnv = (T(1) - g0) * av0;
-      dout[px0 + ch * P + (long long)i * N + p] = mk<T>(dnh, dnv);
+      const long long o = px0 + ch * P + (long long)i * N + p;
+      if (norms) {
+        // residuals of Eq. (varying_penalty): d^{i+1} - d^i and v^{i+1} - v^i
+        const cx<T> vo = vb[o], vn = mk<T>(g0 * ah0, g0 * av0);
+        s_dd += (dnh - dh0) * (dnh - dh0) + (dnv - dv0) * (dnv - dv0);
+        s_dv += (vn.x - vo.x) * (vn.x - vo.x) + (vn.y - vo.y) * (vn.y - vo.y);
+        vb[o] = vn;
+        continue;
+      }
+      dout[o] = mk<T>(sc * dnh, sc * dnv);
+      if (init && vb) vb[o] = mk<T>(g0 * ah0, g0 * av0);  // v^0 = D x^0
       if (stats) {
         s_dd += (dnh - dh0) * (dnh - dh0) + (dnv - dv0) * (dnv - dv0);
         if (ch == 0) s_tv += sqrt(tv);
       }
-      const T r = a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
-                          ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
+      const T r = mur * (((sc1 * gl - sc) * ahl - (sc1 * g0 - sc) * ah0) +
+                         ((sc1 * gu - sc) * avu - (sc1 * g0 - sc) * av0));
       const T yv = yg[ch * P + (long long)i * N + p];
       finite = finite && isfinite(r) && isfinite(yv);
       Cs[p] = mk<T>(yv, r);
     }
+  }
+  if (norms) {  // uniform: the whole CTA leaves here
+    double dd = double(s_dd), dv = double(s_dv), z = 0.0;
+    block_sum3_dyn(dd, dv, z);
+    if (threadIdx.x == 0) {
+      a.apart[2 * (long long)(Dp->row_pbase + blk)] = dd;
+      a.apart[2 * (long long)(Dp->row_pbase + blk) + 1] = dv;
+    }
+    return;
   }
   if (!finite) atomicOr(a.err, 1);
   if (R > 1) __syncthreads(); else __syncwarp(gm);
@@ -528,7 +558,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     for (int j = 0; j < 32; ++j) col[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
   }
   __syncthreads();
-  const T mu = a.mu, tikh = a.tikh, scale = T(1) / (T(M) * T(N));
+  const T mu = a.mu_img ? T(a.mu_img[Dp - a.desc]) : a.mu, tikh = a.tikh, scale = T(1) / (T(M) * T(N));
   if (lane_ok && scol < w) {
     const int ww = scol;
     const T s2w = S2s[M + ww];

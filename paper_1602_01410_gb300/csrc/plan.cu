@@ -69,7 +69,7 @@ struct Layout {
   int row_grid = 0, col_grid = 0;
   size_t row_smem = 0, col_smem = 0;
   size_t o_yt, o_d0, o_d1, o_Sa, o_Sb, o_hhat, o_bits, o_tw, o_tw2, o_s2, o_desc, o_jobs, o_jobbeg, o_wordbeg,
-      o_pxbeg, o_planeimg, o_meanpart, o_means, o_partials, o_err, o_xbuf, o_clsimgs, total;
+      o_pxbeg, o_planeimg, o_meanpart, o_means, o_partials, o_err, o_xbuf, o_clsimgs, o_v, o_mu, o_apart, total;
 };
 
 bool is_pow2_32(int L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
@@ -411,6 +411,10 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   L.o_partials = take((size_t)L.total_row_items * 3 * sizeof(double));
   L.o_err = take(sizeof(int));
   L.o_xbuf = take(L.total_px * L.esz);
+  // penalty adaptation: v_x (as d), mu / mu_prev / d-rescaling per image, residual partials
+  L.o_v = take(L.total_px * 2 * L.esz);
+  L.o_mu = take((size_t)3 * L.B * sizeof(double));
+  L.o_apart = take((size_t)L.total_row_items * 2 * sizeof(double));
   for (auto *v : {&L.row_cls, &L.col_cls})
     for (auto &c : *v) c.o_imgs = take(c.imgs.size() * sizeof(int));
   L.total = o;
@@ -432,6 +436,7 @@ struct deconv_plan_s {
   int tikh_iters = 0;
   double tikh_tau = 1e-3;
   double adapt_t = 0.0;
+  bool adapt_ready = false;  // the per-image penalties and v were set by a fresh solve
   cudaGraphExec_t gexec = nullptr;
   // While a graph is captured: the kernel classes of one pass (disjoint sets
   // of images) fan out over side streams, so their launches run concurrently.
@@ -485,6 +490,14 @@ RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_i
   a.xbuf = p->at<T>(L.o_xbuf);
   a.partials = partials;
   a.err = p->at<int>(L.o_err);
+  if (p->adapt_t > 0.0) {
+    a.mu_img = p->at<double>(L.o_mu);
+    a.mu_prev_img = a.mu_img + L.B;
+    a.dscale_img = a.mu_img + 2 * L.B;
+    a.vbuf = p->at<T>(L.o_v);
+    a.apart = p->at<double>(L.o_apart);
+    a.lam64 = p->lambda;
+  }
   return a;
 }
 
@@ -504,6 +517,7 @@ ColArgs<T> col_args(const deconv_plan_s *p, const Cls &c, double tikh) {
   a.mu = (T)p->mu;
   a.tikh = (T)tikh;
   a.err = p->at<int>(L.o_err);
+  if (p->adapt_t > 0.0) a.mu_img = p->at<double>(L.o_mu);
   return a;
 }
 
@@ -560,10 +574,40 @@ cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, 
                      double *partials, double relax = -1.0) {
   const auto &cl = p->L.row_cls;
   const double rx = relax < 0.0 ? p->relax : relax;
+  const bool adapt = p->adapt_t > 0.0;
+  auto cfg_of = [&](size_t k) {
+    LaunchCfg c = cl[k].cfg;
+    if (adapt) c.stage = 0;  // the forward half that reads through L1 carries the adaptation
+    return c;
+  };
+  if (adapt && mode == ROW_ITER) {
+    // Penalty adaptation, Eq. (varying_penalty): z-update and residual norms,
+    // the per-image rule, then the forward half with mu^{i+1} and d rescaled.
+    const Layout &L = p->L;
+    cudaError_t e = each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+      const LaunchCfg c = cfg_of(k);
+      if (c.kind != KIND_P2)
+        return launch_row<T>(row_args<T>(p, cl[k], ROW_NORMS, d_in, d_out, x_out, nullptr, rx), c, sk);
+      cudaError_t e1 = launch_row_half<T>(row_args<T>(p, cl[k], ROW_ITER, d_in, d_out, x_out, partials, rx), c, 0, sk);
+      if (e1 != cudaSuccess) return e1;
+      return launch_row_half<T>(row_args<T>(p, cl[k], ROW_NORMS, d_in, d_out, x_out, nullptr, rx), c, 1, sk);
+    });
+    if (e != cudaSuccess) return e;
+    double *mu = p->at<double>(L.o_mu);
+    e = launch_mu_update(p->at<ImageDesc>(L.o_desc), L.B, p->at<double>(L.o_apart), mu, mu + L.B, mu + 2 * L.B,
+                         p->adapt_t, s);
+    if (e != cudaSuccess) return e;
+    return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+      const LaunchCfg c = cfg_of(k);
+      const RowArgs<T> a = row_args<T>(p, cl[k], ROW_ITER, d_in, d_out, x_out, partials, rx);
+      if (c.kind != KIND_P2) return launch_row<T>(a, c, sk);
+      return launch_row_half<T>(a, c, 1, sk);
+    });
+  }
   return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
     const RowArgs<T> a = row_args<T>(p, cl[k], mode, d_in, d_out, x_out, partials, rx);
-    if (mode == ROW_INNER && cl[k].cfg.kind == KIND_P2) return launch_row_half<T>(a, cl[k].cfg, 0, sk);
-    return launch_row<T>(a, cl[k].cfg, sk);
+    if (mode == ROW_INNER && cl[k].cfg.kind == KIND_P2) return launch_row_half<T>(a, cfg_of(k), 0, sk);
+    return launch_row<T>(a, cfg_of(k), sk);
   });
 }
 
@@ -594,6 +638,10 @@ deconv_status init_state(deconv_plan_s *p, const T *y, T *x_out) {
   CK(launch_init_fill<T>(desc, L.B, L.total_px, p->at<long long>(L.o_pxbeg), y, p->at<uint32_t>(L.o_bits),
                          p->at<double>(L.o_means), L.K, p->at<T>(L.o_yt), s));
   p->parity = 0;
+  if (p->adapt_t > 0.0) {
+    double *mu = p->at<double>(L.o_mu);
+    CK(launch_mu_fill(mu, mu + L.B, mu + 2 * L.B, L.B, p->mu, s));
+  }
   const int nt = p->tikh_iters;
   CK(row_pass<T>(p, s, ROW_INIT, nullptr, dbuf<T>(p, 0), nt > 0 ? nullptr : x_out, nullptr));
   // Tikhonov warm start (Eqs. (ini_x)-(ini_z)): x = (H^T H + tau I)^{-1} H^T y~,
@@ -606,6 +654,7 @@ deconv_status init_state(deconv_plan_s *p, const T *y, T *x_out) {
       CK(row_pass<T>(p, s, ROW_WARM, nullptr, dbuf<T>(p, 0), x_out, nullptr, 1.0));
   }
   p->have_state = true;
+  p->adapt_ready = p->adapt_t > 0.0;
   return DECONV_OK;
 }
 
@@ -759,7 +808,14 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
                     p->ws + L.o_hhat, p->at<long long>(L.o_jobbeg), s));
   CK(launch_pack_mask(p->at<ImageDesc>(L.o_desc), L.B, L.total_words, p->at<long long>(L.o_wordbeg), mask,
                       p->at<uint32_t>(L.o_bits), s));
-  for (const Cls &c : L.row_cls) CK(prepare_row<T>(c.cfg));
+  for (const Cls &c : L.row_cls) {
+    CK(prepare_row<T>(c.cfg));
+    if (c.cfg.stage) {  // the variant that reads through L1 (used under penalty adaptation)
+      LaunchCfg d = c.cfg;
+      d.stage = 0;
+      CK(prepare_row<T>(d));
+    }
+  }
   for (const Cls &c : L.col_cls) CK(prepare_col<T>(c.cfg));
   CK(cudaStreamSynchronize(s));
   return DECONV_OK;
@@ -1075,11 +1131,11 @@ deconv_status deconv_set_options(deconv_plan p, const deconv_options *o) {
   if (o->bgs_passes < 1 || o->bgs_passes > 64 || o->tikh_iters < 0 || !(o->tikh_tau > 0.0) ||
       !(o->adapt_t == 0.0 || o->adapt_t >= 1.0) || !std::isfinite(o->tikh_tau) || !std::isfinite(o->adapt_t))
     return DECONV_EINVAL;
-  if (o->adapt_t != 0.0) return DECONV_EUNSUPPORTED;
-  if (o->bgs_passes != p->passes && p->gexec) {
-    cudaGraphExecDestroy(p->gexec);  // the captured iteration has a different pass count
+  if ((o->bgs_passes != p->passes || o->adapt_t != p->adapt_t) && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);  // the captured iteration differs
     p->gexec = nullptr;
   }
+  if (o->adapt_t != p->adapt_t) p->adapt_ready = false;
   p->passes = o->bgs_passes;
   p->tikh_iters = o->tikh_iters;
   p->tikh_tau = o->tikh_tau;
@@ -1087,10 +1143,22 @@ deconv_status deconv_set_options(deconv_plan p, const deconv_options *o) {
   return DECONV_OK;
 }
 
+deconv_status deconv_get_mu(deconv_plan p, double *mu_host) {
+  if (!p || !mu_host) return DECONV_EINVAL;
+  if (!(p->adapt_t > 0.0 && p->adapt_ready)) {
+    for (int j = 0; j < p->L.B; ++j) mu_host[j] = p->mu;
+    return DECONV_OK;
+  }
+  CK(cudaMemcpyAsync(mu_host, p->ws + p->L.o_mu, sizeof(double) * p->L.B, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return DECONV_OK;
+}
+
 deconv_status deconv_solve(deconv_plan p, const void *y, void *x, int32_t iters, int32_t warm, double *stats) {
   if (!p || iters < 0 || (warm != 0 && warm != 1)) return DECONV_EINVAL;
   if (!warm && !y) return DECONV_EINVAL;
   if (warm && !p->have_state) return DECONV_EINVAL;
+  if (warm && p->adapt_t > 0.0 && !p->adapt_ready) return DECONV_EINVAL;  // no per-image penalties yet
   if (iters > 0 && !x) return DECONV_EINVAL;
   if (stats && iters == 0) stats = nullptr;
   return p->L.dtype == DECONV_F32 ? solve_t<float>(p, y, x, iters, warm, stats)
@@ -1220,7 +1288,9 @@ deconv_status deconv_kernel_launches(deconv_plan p, int32_t iters, int32_t mode,
   const long long init = 3 + row + (p->tikh_iters > 0 ? (long long)p->tikh_iters * col +
                                                             (long long)(p->tikh_iters - 1) * inner + row
                                                       : 0);
-  const long long per_iter = col + row + (long long)(p->passes - 1) * (col + inner);
+  long long adapt = 0;  // penalty adaptation: a residual-norm launch per class and the per-image rule
+  if (p->adapt_t > 0.0) adapt = (long long)L.row_cls.size() + 1;
+  const long long per_iter = col + row + adapt + (long long)(p->passes - 1) * (col + inner);
   if (mode == 0) {
     *count = init + (long long)iters * per_iter;
     return DECONV_OK;

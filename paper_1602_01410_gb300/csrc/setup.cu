@@ -236,6 +236,58 @@ __global__ void stats_reduce_kernel(const ImageDesc *desc, const double *partial
   }
 }
 
+// One CTA per image: fixed-order FP64 reduction of the image's row-block
+// partials, then the rule of Eq. (varying_penalty) with threshold t.
+__global__ void mu_update_kernel(const ImageDesc *desc, const double *apart, double *mu, double *mu_prev,
+                                 double *dscale, double t) {
+  const int img = blockIdx.x;
+  const ImageDesc &D = desc[img];
+  __shared__ double r[2][128];
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < D.row_blocks; q += blockDim.x) {
+    a += apart[2LL * (D.row_pbase + q)];
+    b += apart[2LL * (D.row_pbase + q) + 1];
+  }
+  r[0][threadIdx.x] = a;
+  r[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      r[0][threadIdx.x] += r[0][threadIdx.x + o];
+      r[1][threadIdx.x] += r[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nd = sqrt(r[0][0]), nv = sqrt(r[1][0]);
+    const double f = nd > t * nv ? 2.0 : (nv > t * nd ? 0.5 : 1.0);
+    const double m = mu[img];
+    mu_prev[img] = m;
+    mu[img] = f * m;
+    dscale[img] = 1.0 / f;
+  }
+}
+
+__global__ void mu_fill_kernel(double *mu, double *mu_prev, double *dscale, int n, double mu0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    mu[i] = mu0;
+    mu_prev[i] = mu0;
+    dscale[i] = 1.0;
+  }
+}
+
+cudaError_t launch_mu_update(const ImageDesc *desc_dev, int nimg, const double *apart, double *mu, double *mu_prev,
+                             double *dscale, double t, cudaStream_t s) {
+  mu_update_kernel<<<nimg, 128, 0, s>>>(desc_dev, apart, mu, mu_prev, dscale, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mu_fill(double *mu, double *mu_prev, double *dscale, int nimg, double mu0, cudaStream_t s) {
+  mu_fill_kernel<<<(nimg + 127) / 128, 128, 0, s>>>(mu, mu_prev, dscale, nimg, mu0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stats_reduce(const ImageDesc *desc_dev, int nimg, const double *partials, double *stats,
                                 int iters, int it, int *err, cudaStream_t s) {
   stats_reduce_kernel<<<nimg, 128, 0, s>>>(desc_dev, partials, stats, iters, it, err);

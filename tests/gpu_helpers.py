@@ -58,6 +58,19 @@ def oracle_solve(prob: inputs.Problem, iters=None, stats=False, relax=None, bgs_
     return xs, ss
 
 
+def oracle_final_mu(prob: inputs.Problem, iters=None, **opts):
+    """Final per-image penalty of the oracle run (penalty adaptation)."""
+    iters = prob.iters if iters is None else iters
+    out = []
+    for j in range(len(prob.shapes)):
+        _, st, _ = oracle.admm(prob.y[j], prob.mask[j], prob.h, prob.lam, prob.mu, iters, relax=prob.relax,
+                               round_f32=prob.dtype == "f32", passes=opts.get("bgs_passes", 1),
+                               tikh_iters=opts.get("tikh_iters", 0), tikh_tau=opts.get("tikh_tau", 1e-3),
+                               adapt_t=opts.get("adapt_t", 0.0))
+        out.append(st.mu)
+    return out
+
+
 def rel_l2(a, b) -> float:
     a = np.concatenate([v.ravel() for v in a])
     b = np.concatenate([v.ravel() for v in b])

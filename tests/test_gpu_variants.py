@@ -83,3 +83,59 @@ def test_options_validated():
         with pytest.raises(pkg.DeconvError) as e:
             plan.set_options(**bad)
         assert e.value.status == pkg.DECONV_EINVAL
+
+
+# ------------------------------------------------- penalty adaptation ---
+
+def check_adaptive(prob, tol, **opts):
+    from gpu_helpers import oracle_final_mu
+    xg, _, plan = gpu_solve(prob, **opts)
+    xo, _ = oracle_solve(prob, **opts)
+    mo = oracle_final_mu(prob, **opts)
+    mg = plan.get_mu()
+    print("final mu gpu", mg, "oracle", mo)
+    assert mg == mo
+    assert len(set(mo)) > 1 or mo[0] != prob.mu  # the rule fired
+    for a, b in zip(xg, xo):
+        assert rel_l2([a], [b]) <= tol
+
+
+def test_adaptive_mu_from_a_large_penalty():
+    prob = inputs.random_problem(51, SIZES, 7, mask_kind="random", frac=0.4, iters=12, mu=1.0)
+    check_adaptive(prob, 1e-4, adapt_t=3.0)
+
+
+def test_adaptive_mu_from_a_small_penalty():
+    prob = inputs.random_problem(52, [(128, 256), (96, 160), (384, 384)], 9, mask_kind="crop", iters=12,
+                                 mu=1e-5, lam=1e-4)
+    check_adaptive(prob, 1e-4, adapt_t=3.0)
+
+
+def test_adaptive_mu_vectorial_fp64_with_passes_and_warm_start():
+    prob = inputs.random_problem(53, [(64, 64), (48, 60)], 5, mask_kind="bayer", channels=3, iters=10,
+                                 dtype="f64", mu=1.0)
+    check_adaptive(prob, 1e-10, adapt_t=3.0, bgs_passes=2, tikh_iters=5, tikh_tau=1e-2)
+
+
+def test_adaptive_graph_replay_equals_direct_launches():
+    prob = inputs.random_problem(54, [(64, 80), (128, 128)], 5, mask_kind="random", frac=0.3, iters=45, mu=1.0)
+    a, _, pa = gpu_solve(prob, adapt_t=3.0)
+    b, _, pb = gpu_solve(prob, stats=True, adapt_t=3.0)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    assert pa.get_mu() == pb.get_mu()
+
+
+def test_adaptive_warm_continuation_needs_a_fresh_solve():
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(55, [(48, 64)], 5, mask_kind="random", frac=0.3, iters=7, mu=1.0)
+    full, _, _ = gpu_solve(prob, adapt_t=3.0)
+    _, _, plan = gpu_solve(prob, iters=4, adapt_t=3.0)
+    x = plan.solve(None, 3, warm=True)
+    assert plan.sync() == 0
+    assert np.array_equal(x.double().cpu().numpy().reshape(full[0].shape), full[0])
+    _, _, plan2 = gpu_solve(prob, iters=4)
+    plan2.set_options(adapt_t=3.0)
+    with pytest.raises(pkg.DeconvError) as e:
+        plan2.solve(None, 3, warm=True)
+    assert e.value.status == pkg.DECONV_EINVAL
