@@ -138,6 +138,19 @@ typedef struct {
 
 deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
 
+/* Arbitrary sizes (Sec. II-A: any pixel may be unobserved).  For an extended
+ * grid of M x N that the library does not run (a prime factor > 5), the
+ * smallest supported grid M_out x N_out >= M x N (smallest area among
+ * 2-3-5-smooth sides) for the given channel count, kernel size and dtype.
+ * The caller embeds its image at rows 0..M-1, columns 0..N-1 of the larger
+ * grid with the added rows and columns unobserved (mask 0): they become
+ * part of z, estimated like the boundary band.  The added band changes where
+ * the circular TV wraps, so the result is that of the enlarged problem, not
+ * of an M x N circular one.  Returns M_out = M, N_out = N when M x N runs as
+ * it is.  Host only. */
+deconv_status deconv_fast_shape(int32_t M, int32_t N, int32_t channels, int32_t ksize, int32_t dtype,
+                                int32_t *M_out, int32_t *N_out);
+
 /* The penalty mu each image's next iteration uses (mu_host: host, batch
  * doubles).  With adaptation off, or before the first fresh solve after it
  * was switched on, every entry is the plan's mu.  Synchronises the stream.

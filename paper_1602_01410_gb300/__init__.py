@@ -30,7 +30,7 @@ EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "decon
            "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
            "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches",
-           "deconv_set_options", "deconv_get_mu")
+           "deconv_set_options", "deconv_get_mu", "deconv_fast_shape")
 
 
 class DeconvError(RuntimeError):
@@ -84,6 +84,7 @@ def load() -> ctypes.CDLL:
         lib.deconv_last_error.argtypes = []
         lib.deconv_set_options.argtypes = [vp, ctypes.POINTER(deconv_options)]
         lib.deconv_get_mu.argtypes = [vp, ctypes.POINTER(dbl)]
+        lib.deconv_fast_shape.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.deconv_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("deconv_status_string", "deconv_last_error"):
@@ -207,6 +208,37 @@ def deconv_get_mu(plan: int, nimg: int):
     out = (ctypes.c_double * nimg)()
     _check(load().deconv_get_mu(plan, out), "deconv_get_mu")
     return [float(v) for v in out]
+
+
+def deconv_fast_shape(M: int, N: int, channels: int = 1, ksize: int = 3, dtype: int = DECONV_F32):
+    """Smallest supported extended grid >= M x N (see deconv.h)."""
+    mo, no = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().deconv_fast_shape(M, N, channels, ksize, dtype, ctypes.byref(mo), ctypes.byref(no)),
+           "deconv_fast_shape")
+    return int(mo.value), int(no.value)
+
+
+def enlarge(y, mask, shape):
+    """Embed (C, M, N) arrays y and mask (numpy or torch) at the top-left of a
+    (C, M2, N2) grid; the added pixels are unobserved (mask 0, y 0)."""
+    M2, N2 = shape
+    C, M, N = y.shape
+    if M2 < M or N2 < N:
+        raise ValueError("the enlarged grid must contain the original one")
+    if hasattr(y, "new_zeros"):  # torch
+        y2, m2 = y.new_zeros((C, M2, N2)), mask.new_zeros((C, M2, N2))
+    else:
+        import numpy as np
+        y2, m2 = np.zeros((C, M2, N2), y.dtype), np.zeros((C, M2, N2), mask.dtype)
+    y2[:, :M, :N] = y
+    m2[:, :M, :N] = mask
+    return y2, m2
+
+
+def crop(x, shape):
+    """The (C, M, N) window of an enlarged (C, M2, N2) result."""
+    M, N = shape
+    return x[:, :M, :N]
 
 
 def deconv_plan_destroy(plan: int) -> None:

@@ -1143,6 +1143,43 @@ deconv_status deconv_set_options(deconv_plan p, const deconv_options *o) {
   return DECONV_OK;
 }
 
+deconv_status deconv_fast_shape(int32_t M, int32_t N, int32_t channels, int32_t ksize, int32_t dtype,
+                                int32_t *M_out, int32_t *N_out) {
+  if (!M_out || !N_out || M < 1 || N < 1 || (channels != 1 && channels != 3) || ksize < 1 || !(ksize & 1) ||
+      (dtype != DECONV_F32 && dtype != DECONV_F64) || M < ksize || N < ksize)
+    return DECONV_EINVAL;
+  // The first few 2-3-5-smooth lengths at or above each side.
+  auto smooth_from = [](int L, int count) {
+    std::vector<int> v;
+    FftSched sc;
+    for (long long c = L; (int)v.size() < count && c <= (1 << 20); ++c)
+      if (factor235((int)c, &sc)) v.push_back((int)c);
+    return v;
+  };
+  const std::vector<int> ms = smooth_from(M, 12), ns = smooth_from(N, 12);
+  long long best = -1;
+  for (int m2 : ms)
+    for (int n2 : ns) {
+      const long long area = (long long)m2 * n2;
+      if (best >= 0 && area >= best) continue;
+      int32_t r = m2, c = n2;
+      deconv_dims d{};
+      d.batch = 1;
+      d.channels = channels;
+      d.rows = &r;
+      d.cols = &c;
+      d.ksize = ksize;
+      d.dtype = dtype;
+      d.relax = 2.0f;
+      Layout L;
+      if (build_layout(&d, &L) != DECONV_OK) continue;
+      best = area;
+      *M_out = m2;
+      *N_out = n2;
+    }
+  return best >= 0 ? DECONV_OK : DECONV_EUNSUPPORTED;
+}
+
 deconv_status deconv_get_mu(deconv_plan p, double *mu_host) {
   if (!p || !mu_host) return DECONV_EINVAL;
   if (!(p->adapt_t > 0.0 && p->adapt_ready)) {

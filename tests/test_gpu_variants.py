@@ -139,3 +139,38 @@ def test_adaptive_warm_continuation_needs_a_fresh_solve():
     with pytest.raises(pkg.DeconvError) as e:
         plan2.solve(None, 3, warm=True)
     assert e.value.status == pkg.DECONV_EINVAL
+
+
+# ------------------------------------------------------- arbitrary sizes ---
+
+def enlarged(prob):
+    import dataclasses
+    import paper_1602_01410_gb300 as pkg
+    ys, ms, xs = [], [], []
+    for y, m, x in zip(prob.y, prob.mask, prob.x_true):
+        shape = pkg.deconv_fast_shape(y.shape[1], y.shape[2], prob.channels, prob.ksize,
+                                      pkg.DECONV_F32 if prob.dtype == "f32" else pkg.DECONV_F64)
+        y2, m2 = pkg.enlarge(y, m, shape)
+        x2, _ = pkg.enlarge(x, m, shape)
+        ys.append(y2)
+        ms.append(m2)
+        xs.append(x2)
+    return dataclasses.replace(prob, y=ys, mask=ms, x_true=xs)
+
+
+def test_enlarged_prime_sizes():
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(61, [(67, 131), (101, 97), (257, 263)], 7, mask_kind="crop", iters=1)
+    big = enlarged(prob)
+    assert big.shapes == [(72, 135), (108, 100), (270, 270)]
+    check(big, 1e-5)
+    big.iters = 15
+    check(big, 1e-4)
+    xg, _, _ = gpu_solve(big)
+    for x, (M, N) in zip(xg, prob.shapes):
+        assert pkg.crop(x, (M, N)).shape == (prob.channels, M, N)
+
+
+def test_enlarged_rgb_with_all_variants():
+    prob = inputs.random_problem(62, [(61, 59)], 5, mask_kind="bayer", channels=3, iters=6, mu=1.0)
+    check_adaptive(enlarged(prob), 1e-4, adapt_t=3.0, bgs_passes=2, tikh_iters=4, tikh_tau=1e-2)
