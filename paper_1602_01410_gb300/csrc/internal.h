@@ -100,7 +100,9 @@ struct LaunchCfg {
   int kind;      // KernelKind
   int tt;        // KIND_P2: threads per sub-transform (sub-length / 32)
   int r;         // KIND_P2: length = r * 32 * tt, r in {1, 3, 5}
-  int stage;     // KIND_P2 rows, one channel: forward half stages its rows in shared memory
+  int stage;     // KIND_P2 rows, forward half: 0 reads through L1, 1 stages its rows (one
+                 // channel), 2 reads through L1 with penalty adaptation.  KIND_P2
+                 // columns: 1 = the variant with the Tikhonov step / per-image penalty
   int nt;        // threads per CTA
   int channels;  // 1 or 3
   int grid;      // CTAs

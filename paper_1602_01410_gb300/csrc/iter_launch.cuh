@@ -1,56 +1,36 @@
 // Launch wrappers for the iteration kernels: resolve the kernel of a
 // LaunchCfg (generic Stockham passes by CTA size and channel count, or the
-// power-of-two passes by threads per transform and channel count).
+// register-FFT passes by threads per transform, radix and channel count).
 #pragma once
 
 #include "iter_kernels.cuh"
-#include "iter_p2.cuh"
 
 namespace dcv {
 
 // 512-thread generic CTAs exist for FP32 only (FP64 registers would spill).
 template <typename T> constexpr int kMaxNt = sizeof(T) == 4 ? 512 : 256;
 
-// Power-of-two and R * 2^k row passes: half 0 = inverse (R1), half 1 = forward (R2).
-// The staged forward half exists for one channel only.
-template <typename T, int TT, int C, int R>
-static const void *row_p2_one(int half, int stage) {
-  if (!half) return (const void *)row_inv_p2_kernel<T, TT, C, R>;
-  if constexpr (C == 1)
-    if (stage) return (const void *)row_fwd_p2_staged_kernel<T, TT, C, R>;
-  return (const void *)row_fwd_p2_kernel<T, TT, C, R>;
-}
+// Register-FFT passes of lengths R * 32 * TT (TT = tt): the kernels live in
+// one translation unit per (type, R) (p2_tables.cuh), which compile in
+// parallel.  half 0: inverse half, 1: forward half (stage 0 reads through
+// L1, 1 stages its rows (one channel), 2 adds penalty adaptation), 2: the y~
+// spectrum of an inner pass.
+template <typename T, int R> const void *p2_row_kernel(int C, int tt, int half, int stage);
+template <typename T, int R> const void *p2_col_kernel(int tt, int ext);
 
-template <typename T, int C>
-static const void *row_p2_ptr(int tt, int r, int half, int stage) {
-  if (r == 1) {
-    switch (tt) {
-      case 2: return row_p2_one<T, 2, C, 1>(half, stage);
-      case 4: return row_p2_one<T, 4, C, 1>(half, stage);
-      case 8: return row_p2_one<T, 8, C, 1>(half, stage);
-      case 16: return row_p2_one<T, 16, C, 1>(half, stage);
-      case 32: return row_p2_one<T, 32, C, 1>(half, stage);
-    }
-  } else if (r == 3) {
-    switch (tt) {
-      case 4: return row_p2_one<T, 4, C, 3>(half, stage);
-      case 8: return row_p2_one<T, 8, C, 3>(half, stage);
-      case 16: return row_p2_one<T, 16, C, 3>(half, stage);
-    }
-  } else if (r == 5) {
-    switch (tt) {
-      case 4: return row_p2_one<T, 4, C, 5>(half, stage);
-      case 8: return row_p2_one<T, 8, C, 5>(half, stage);
-      case 16: return row_p2_one<T, 16, C, 5>(half, stage);
-    }
+template <typename T>
+static const void *p2_row_ptr(int C, int tt, int r, int half, int stage) {
+  switch (r) {
+    case 1: return p2_row_kernel<T, 1>(C, tt, half, stage);
+    case 3: return p2_row_kernel<T, 3>(C, tt, half, stage);
+    case 5: return p2_row_kernel<T, 5>(C, tt, half, stage);
   }
   return nullptr;
 }
 
 template <typename T>
 static const void *row_ptr(const LaunchCfg &c, int half = 0) {
-  if (c.kind == KIND_P2)
-    return c.channels == 3 ? row_p2_ptr<T, 3>(c.tt, c.r, half, c.stage) : row_p2_ptr<T, 1>(c.tt, c.r, half, c.stage);
+  if (c.kind == KIND_P2) return p2_row_ptr<T>(c.channels, c.tt, c.r, half, c.stage);
   if (c.nt == 512 && kMaxNt<T> == 512)
     return c.channels == 3 ? (const void *)row_pass_kernel<T, kMaxNt<T>, 3> : (const void *)row_pass_kernel<T, kMaxNt<T>, 1>;
   if (c.nt == 256)
@@ -61,26 +41,10 @@ static const void *row_ptr(const LaunchCfg &c, int half = 0) {
 template <typename T>
 static const void *col_ptr(const LaunchCfg &c) {
   if (c.kind == KIND_P2) {
-    if (c.r == 1) {
-      switch (c.tt) {
-        case 2: return (const void *)col_pass_p2_kernel<T, 2, 1>;
-        case 4: return (const void *)col_pass_p2_kernel<T, 4, 1>;
-        case 8: return (const void *)col_pass_p2_kernel<T, 8, 1>;
-        case 16: return (const void *)col_pass_p2_kernel<T, 16, 1>;
-        case 32: return (const void *)col_pass_p2_kernel<T, 32, 1>;
-      }
-    } else if (c.r == 3) {
-      switch (c.tt) {
-        case 4: return (const void *)col_pass_p2_kernel<T, 4, 3>;
-        case 8: return (const void *)col_pass_p2_kernel<T, 8, 3>;
-        case 16: return (const void *)col_pass_p2_kernel<T, 16, 3>;
-      }
-    } else if (c.r == 5) {
-      switch (c.tt) {
-        case 4: return (const void *)col_pass_p2_kernel<T, 4, 5>;
-        case 8: return (const void *)col_pass_p2_kernel<T, 8, 5>;
-        case 16: return (const void *)col_pass_p2_kernel<T, 16, 5>;
-      }
+    switch (c.r) {
+      case 1: return p2_col_kernel<T, 1>(c.tt, c.stage);
+      case 3: return p2_col_kernel<T, 3>(c.tt, c.stage);
+      case 5: return p2_col_kernel<T, 5>(c.tt, c.stage);
     }
     return nullptr;
   }
@@ -127,7 +91,7 @@ cudaError_t launch_row_half(const RowArgs<T> &a, const LaunchCfg &c, int half, c
 // Opt in to the dynamic shared memory a class needs (above 48 KB).
 template <typename T>
 cudaError_t prepare_row(const LaunchCfg &c) {
-  for (int half = 0; half < (c.kind == KIND_P2 ? 2 : 1); ++half) {
+  for (int half = 0; half < (c.kind == KIND_P2 ? 3 : 1); ++half) {
     const void *fn = row_ptr<T>(c, half);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_half_cfg(c, half).smem);
@@ -138,9 +102,15 @@ cudaError_t prepare_row(const LaunchCfg &c) {
 
 template <typename T>
 cudaError_t prepare_col(const LaunchCfg &c) {
-  const void *fn = col_ptr<T>(c);
-  if (!fn) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+  for (int ext = 0; ext < (c.kind == KIND_P2 ? 2 : 1); ++ext) {
+    LaunchCfg e = c;
+    e.stage = ext;
+    const void *fn = col_ptr<T>(e);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (r != cudaSuccess) return r;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace dcv

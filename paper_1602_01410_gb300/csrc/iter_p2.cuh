@@ -86,7 +86,6 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   const int i = r0 + hh;
   const bool init = a.mode == ROW_INIT;
   const bool adj = a.mode == ROW_ADJ;      // reverse pass: xbuf <- b, yt <- yt + T~b
-  const bool inner = a.mode == ROW_INNER;  // then the row spectrum of y~ into the Y half of S_out
   const unsigned gm = group_mask(TT);
   // Distinct buffers (x_out is written only when it is not the x buffer).
   T *__restrict__ yt = a.yt;
@@ -147,35 +146,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
       if (xout) xout[rowp + p] = v[j].x;
       if (!init) {
         const T yo = yrow[p];
-        T ynew = yo;
         if (!((mrow[p >> 5] >> (p & 31)) & 1u)) {
           const T yn = relax * v[j].y - (relax - T(1)) * yo;
           yt[rowp + p] = yn;
-          ynew = yn;
           if (stats) s_dz += (yn - yo) * (yn - yo);
         } else if (stats) {
           s_fit += (yo - v[j].y) * (yo - v[j].y);
         }
-        if (inner) Ex[p] = mk<T>(ynew, T(0));
-      }
-    }
-  }
-  if (inner) {
-    // Forward row DFT of the updated y~ (real input: its spectrum is Y_row,
-    // Hermitian, of which k <= N/2 is stored).
-    if (R > 1) __syncthreads(); else __syncwarp(gm);
-    if (active) {
-#pragma unroll
-      for (int m = 0; m < 32; ++m) v[m] = Ex[R * (q + TT * m) + gr];
-    }
-    if (R > 1) __syncthreads(); else __syncwarp(gm);
-    fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
-    if (active) {
-      cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int k = q + TT * p2_slot<TT>(j) + L2 * gr;
-        if (2 * k <= N) *reinterpret_cast<cx<T> *>(&dst[k]) = v[j];
       }
     }
   }
@@ -186,6 +163,48 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
       double *o = a.partials + 3 * (long long)(Dp->row_pbase + blk);
       o[1] = dz;
       o[2] = fit;
+    }
+  }
+}
+
+// ------------------------------------------------- row, y~ spectrum ---
+// Inner block-Gauss-Seidel pass / Tikhonov step, after the inverse half
+// updated z: the forward row DFT of y~ alone (real input, so its spectrum is
+// Y_row, Hermitian; k <= N/2 is stored into the Y half of S_out, the R half
+// is kept).  Same CTA layout as the inverse half; shared memory: one region
+// of R transpose tiles per (channel, row).
+template <typename T, int TT, int C, int R>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kernel(RowArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, RS = R * GS;
+  const int wi = blockIdx.x;
+  const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
+  const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb;
+  const int blk = wi - Dp->row_begin;
+  const int r0 = blk * Rb, nr = min(Rb, M - r0);
+  const long long P = (long long)M * N, px0 = Dp->px;
+  const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
+  const bool active = ch < C && hh < nr;
+  const int i = r0 + hh;
+  const unsigned gm = group_mask(TT);
+  cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)row_id * RS;
+  cx<T> *tile = Ex + gr * GS;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  cx<T> v[32];
+  if (active) {
+    const T *__restrict__ yrow = a.yt + px0 + ch * P + (long long)i * N;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = mk<T>(yrow[R * (q + TT * m) + gr], T(0));
+  }
+  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  if (active) {
+    cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int k = q + TT * p2_slot<TT>(j) + L2 * gr;
+      if (2 * k <= N) *reinterpret_cast<cx<T> *>(&dst[k]) = v[j];
     }
   }
 }
@@ -201,7 +220,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
 // Shared memory: one region of R transpose tiles per (channel, row); it
 // holds y~ + i r, then the transpose tiles and the exchange buffer, then the
 // transformed row.
-template <typename T, int TT, int C, int R>
+template <typename T, int TT, int C, int R, bool ADAPT>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, RS = R * GS;
@@ -229,9 +248,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
 
   // Penalty: fixed, or per image (adaptation): tau = lambda / mu^i, r with
   // mu^{i+1} and d^{i+1} rescaled by s (v - s d^{i+1} = ((1+s) g - s) a).
-  const bool norms = a.mode == ROW_NORMS;
+  const bool norms = ADAPT && a.mode == ROW_NORMS;
   T tau = a.tau, mur = a.mu, sc = T(1);
-  if (a.mu_img) {
+  if (ADAPT) {
     const int img = (int)(Dp - a.desc);
     tau = T(a.lam64 / (norms ? a.mu_img[img] : a.mu_prev_img[img]));
     mur = T(a.mu_img[img]);
@@ -283,7 +302,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
       const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
       const T dnh = (T(1) - g0) * ah0, dnv = (T(1) - g0) * av0;
       const long long o = px0 + ch * P + (long long)i * N + p;
-      if (norms) {
+      if (ADAPT && norms) {
         // residuals of Eq. (varying_penalty): d^{i+1} - d^i and v^{i+1} - v^i
         const cx<T> vo = vb[o], vn = mk<T>(g0 * ah0, g0 * av0);
         s_dd += (dnh - dh0) * (dnh - dh0) + (dnv - dv0) * (dnv - dv0);
@@ -291,20 +310,26 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
         vb[o] = vn;
         continue;
       }
-      dout[o] = mk<T>(sc * dnh, sc * dnv);
-      if (init && vb) vb[o] = mk<T>(g0 * ah0, g0 * av0);  // v^0 = D x^0
+      if (ADAPT) {
+        dout[o] = mk<T>(sc * dnh, sc * dnv);
+        if (init) vb[o] = mk<T>(g0 * ah0, g0 * av0);  // v^0 = D x^0
+      } else {
+        dout[o] = mk<T>(dnh, dnv);
+      }
       if (stats) {
         s_dd += (dnh - dh0) * (dnh - dh0) + (dnv - dv0) * (dnv - dv0);
         if (ch == 0) s_tv += sqrt(tv);
       }
-      const T r = mur * (((sc1 * gl - sc) * ahl - (sc1 * g0 - sc) * ah0) +
-                         ((sc1 * gu - sc) * avu - (sc1 * g0 - sc) * av0));
+      const T r = ADAPT ? mur * (((sc1 * gl - sc) * ahl - (sc1 * g0 - sc) * ah0) +
+                                 ((sc1 * gu - sc) * avu - (sc1 * g0 - sc) * av0))
+                        : a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
+                                  ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
       const T yv = yg[ch * P + (long long)i * N + p];
       finite = finite && isfinite(r) && isfinite(yv);
       Cs[p] = mk<T>(yv, r);
     }
   }
-  if (norms) {  // uniform: the whole CTA leaves here
+  if (ADAPT && norms) {  // uniform: the whole CTA leaves here
     double dd = double(s_dd), dv = double(s_dv), z = 0.0;
     block_sum3_dyn(dd, dv, z);
     if (threadIdx.x == 0) {
@@ -504,7 +529,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
 // place (their transpose tiles and exchange buffer are that column's
 // storage).  Shared memory: [2W columns of R tiles (+4 elements of padding,
 // which spreads the staging stores over the banks)][H^ tile M x w][sin^2 tables].
-template <typename T, int TT, int R>
+template <typename T, int TT, int R, bool EXT>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, SR = R * GS + 4;
@@ -558,7 +583,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     for (int j = 0; j < 32; ++j) col[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
   }
   __syncthreads();
-  const T mu = a.mu_img ? T(a.mu_img[Dp - a.desc]) : a.mu, tikh = a.tikh, scale = T(1) / (T(M) * T(N));
+  // EXT: a Tikhonov warm-start step (tikh > 0) or a per-image penalty.
+  const T mu = (EXT && a.mu_img) ? T(a.mu_img[Dp - a.desc]) : a.mu, tikh = EXT ? a.tikh : T(0);
+  const T scale = T(1) / (T(M) * T(N));
   if (lane_ok && scol < w) {
     const int ww = scol;
     const T s2w = S2s[M + ww];
@@ -566,9 +593,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     cx<T> *cy = St + (size_t)(2 * ww) * SR, *cr = cy + SR;
     for (int k1 = r0t; k1 < M; k1 += rstep) {
       const cx<T> hv = Hs[k1 * w + ww];
-      const T den = hv.x * hv.x + hv.y * hv.y + (tikh > T(0) ? tikh : mu * (S2s[k1] + s2w));
+      const T den = hv.x * hv.x + hv.y * hv.y + ((EXT && tikh > T(0)) ? tikh : mu * (S2s[k1] + s2w));
       const T inv = scale / den;
-      const cx<T> Y = cy[k1], Rv = tikh > T(0) ? mk<T>(T(0), T(0)) : cr[k1];
+      const cx<T> Y = cy[k1], Rv = (EXT && tikh > T(0)) ? mk<T>(T(0), T(0)) : cr[k1];
       const cx<T> B = cadd<T>(cmulc<T>(hv, Y), Rv);  // den * (solution spectrum)
       if (a.spec_store) {
         cpair<T> o;

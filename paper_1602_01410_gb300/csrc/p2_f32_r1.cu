@@ -1,0 +1,4 @@
+// FP32 register-FFT passes of lengths 2^k.
+#include "p2_tables.cuh"
+
+DCV_P2_INSTANTIATE(float, 1)

@@ -1,0 +1,4 @@
+// FP64 register-FFT passes of lengths 5*2^k.
+#include "p2_tables.cuh"
+
+DCV_P2_INSTANTIATE(double, 5)

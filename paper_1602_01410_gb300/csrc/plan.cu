@@ -562,13 +562,17 @@ cudaError_t each_class(deconv_plan_s *p, cudaStream_t s, size_t n, F fn) {
 template <typename T>
 cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s, double tikh = 0.0) {
   const auto &cl = p->L.col_cls;
+  const int ext = (tikh > 0.0 || p->adapt_t > 0.0) ? 1 : 0;  // the column variant with those terms
   return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
-    return launch_col<T>(col_args<T>(p, cl[k], tikh), cl[k].cfg, sk);
+    LaunchCfg c = cl[k].cfg;
+    c.stage = ext;
+    return launch_col<T>(col_args<T>(p, cl[k], tikh), c, sk);
   });
 }
 
-// relax < 0: the plan's over-relaxation.  ROW_INNER runs the inverse half
-// alone on the register-FFT classes (it ends with the forward spectrum of y~).
+// relax < 0: the plan's over-relaxation.  ROW_INNER runs, on the
+// register-FFT classes, the inverse half (z-update) and then the forward
+// spectrum of y~ alone (row_yspec_p2_kernel).
 template <typename T>
 cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, T *d_out, T *x_out,
                      double *partials, double relax = -1.0) {
@@ -577,7 +581,7 @@ cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, 
   const bool adapt = p->adapt_t > 0.0;
   auto cfg_of = [&](size_t k) {
     LaunchCfg c = cl[k].cfg;
-    if (adapt) c.stage = 0;  // the forward half that reads through L1 carries the adaptation
+    if (adapt) c.stage = 2;  // the forward half with penalty adaptation
     return c;
   };
   if (adapt && mode == ROW_ITER) {
@@ -606,7 +610,10 @@ cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, 
   }
   return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
     const RowArgs<T> a = row_args<T>(p, cl[k], mode, d_in, d_out, x_out, partials, rx);
-    if (mode == ROW_INNER && cl[k].cfg.kind == KIND_P2) return launch_row_half<T>(a, cfg_of(k), 0, sk);
+    if (mode == ROW_INNER && cl[k].cfg.kind == KIND_P2) {
+      cudaError_t e1 = launch_row_half<T>(a, cfg_of(k), 0, sk);  // z-update
+      return e1 != cudaSuccess ? e1 : launch_row_half<T>(a, cfg_of(k), 2, sk);  // y~ spectrum
+    }
     return launch_row<T>(a, cfg_of(k), sk);
   });
 }
@@ -810,9 +817,9 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
                       p->at<uint32_t>(L.o_bits), s));
   for (const Cls &c : L.row_cls) {
     CK(prepare_row<T>(c.cfg));
-    if (c.cfg.stage) {  // the variant that reads through L1 (used under penalty adaptation)
+    if (c.cfg.kind == KIND_P2) {  // the forward half with penalty adaptation
       LaunchCfg d = c.cfg;
-      d.stage = 0;
+      d.stage = 2;
       CK(prepare_row<T>(d));
     }
   }
@@ -1319,8 +1326,8 @@ deconv_status deconv_kernel_launches(deconv_plan p, int32_t iters, int32_t mode,
   const Layout &L = p->L;
   long long row = 0, col = (long long)L.col_cls.size();
   for (const Cls &c : L.row_cls) row += c.cfg.kind == KIND_P2 ? 2 : 1;
-  long long inner = 0;  // an inner BGS pass: the inverse half alone on register-FFT classes
-  for (const Cls &c : L.row_cls) inner += 1;
+  long long inner = 0;  // an inner BGS pass: the inverse half and the y~ spectrum on register-FFT classes
+  for (const Cls &c : L.row_cls) inner += c.cfg.kind == KIND_P2 ? 2 : 1;
   // observed means (2 kernels), initial fill, initial row pass, warm-start steps
   const long long init = 3 + row + (p->tikh_iters > 0 ? (long long)p->tikh_iters * col +
                                                             (long long)(p->tikh_iters - 1) * inner + row
