@@ -79,7 +79,8 @@ typedef struct {
   float relax;
 } deconv_dims;
 
-/* Bytes of device workspace a plan for `dims` needs.  Host only. */
+/* Bytes of device workspace a plan for `dims` needs (under any tuning the
+ * autotuner tries).  Host only. */
 deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes);
 
 /* Create a plan (Sec. II-B, the precomputation of the FFT-diagonalised
@@ -137,6 +138,34 @@ typedef struct {
 } deconv_options;
 
 deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
+
+/* Tuning of the launch shapes (the paper has no counterpart: it names no
+ * GPU).  row_ctas / col_ctas: CTAs a register-FFT row class / the column
+ * pass aims at (rows per CTA and spectral columns per CTA follow); 0 = the
+ * default (152, one per SM).  row_stage: -1 = default (the forward row half
+ * stages its rows in shared memory for one-channel plans of one row class),
+ * 0 = reads them through L1, 1 = stages them (one channel only). */
+typedef struct {
+  int32_t row_ctas;
+  int32_t col_ctas;
+  int32_t row_stage;
+} deconv_tune;
+
+/* Re-lays out a plan for another tuning (t = NULL: the defaults).  The
+ * workspace of deconv_workspace_size() holds every tuning deconv_autotune
+ * tries.  The iteration state is discarded (the next solve must be fresh).
+ * Synchronises the stream. */
+deconv_status deconv_retune(deconv_plan plan, const deconv_tune *t);
+deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
+
+/* Autotuner: times trial_iters iterations (after a fresh solve of y that
+ * builds the CUDA graph; the plan's options apply) under the default tuning
+ * and each candidate (row_ctas in {152, 304, 608}, col_ctas in {76, 152,
+ * 304, 608}, and for one channel row_stage in {0, 1}), keeps the fastest
+ * (best, best_ms_per_iter: nullable host outputs) and leaves the plan in it
+ * with no iteration state.  y: device, batch layout.  Synchronous. */
+deconv_status deconv_autotune(deconv_plan plan, const void *y, int32_t trial_iters, deconv_tune *best,
+                              float *best_ms_per_iter);
 
 /* Arbitrary sizes (Sec. II-A: any pixel may be unobserved).  For an extended
  * grid of M x N that the library does not run (a prime factor > 5), the

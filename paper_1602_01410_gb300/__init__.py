@@ -30,7 +30,8 @@ EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "decon
            "deconv_profile_passes", "deconv_sync", "deconv_plan_destroy", "deconv_status_string",
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
            "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches",
-           "deconv_set_options", "deconv_get_mu", "deconv_fast_shape")
+           "deconv_set_options", "deconv_get_mu", "deconv_fast_shape", "deconv_retune", "deconv_get_tune",
+           "deconv_autotune")
 
 
 class DeconvError(RuntimeError):
@@ -50,6 +51,10 @@ class deconv_dims(ctypes.Structure):
 class deconv_options(ctypes.Structure):
     _fields_ = [("bgs_passes", ctypes.c_int32), ("tikh_iters", ctypes.c_int32),
                 ("tikh_tau", ctypes.c_double), ("adapt_t", ctypes.c_double)]
+
+
+class deconv_tune(ctypes.Structure):
+    _fields_ = [("row_ctas", ctypes.c_int32), ("col_ctas", ctypes.c_int32), ("row_stage", ctypes.c_int32)]
 
 
 _lib = None
@@ -84,6 +89,9 @@ def load() -> ctypes.CDLL:
         lib.deconv_last_error.argtypes = []
         lib.deconv_set_options.argtypes = [vp, ctypes.POINTER(deconv_options)]
         lib.deconv_get_mu.argtypes = [vp, ctypes.POINTER(dbl)]
+        lib.deconv_retune.argtypes = [vp, ctypes.POINTER(deconv_tune)]
+        lib.deconv_get_tune.argtypes = [vp, ctypes.POINTER(deconv_tune)]
+        lib.deconv_autotune.argtypes = [vp, vp, i32, ctypes.POINTER(deconv_tune), ctypes.POINTER(ctypes.c_float)]
         lib.deconv_fast_shape.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.deconv_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -210,6 +218,24 @@ def deconv_get_mu(plan: int, nimg: int):
     return [float(v) for v in out]
 
 
+def deconv_retune(plan: int, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1) -> None:
+    t = deconv_tune(int(row_ctas), int(col_ctas), int(row_stage))
+    _check(load().deconv_retune(plan, ctypes.byref(t)), "deconv_retune")
+
+
+def deconv_get_tune(plan: int) -> dict:
+    t = deconv_tune()
+    _check(load().deconv_get_tune(plan, ctypes.byref(t)), "deconv_get_tune")
+    return {"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage}
+
+
+def deconv_autotune(plan: int, y_ptr: int, trial_iters: int = 20):
+    """Returns (best tuning as a dict, its ms per iteration)."""
+    t, ms = deconv_tune(), ctypes.c_float(0.0)
+    _check(load().deconv_autotune(plan, y_ptr, trial_iters, ctypes.byref(t), ctypes.byref(ms)), "deconv_autotune")
+    return {"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage}, float(ms.value)
+
+
 def deconv_fast_shape(M: int, N: int, channels: int = 1, ksize: int = 3, dtype: int = DECONV_F32):
     """Smallest supported extended grid >= M x N (see deconv.h)."""
     mo, no = ctypes.c_int32(0), ctypes.c_int32(0)
@@ -302,6 +328,13 @@ class Plan:
                     adapt_t: float = 0.0) -> None:
         """BGS passes per iteration, Tikhonov warm start, penalty adaptation (see deconv.h)."""
         deconv_set_options(self.handle, bgs_passes, tikh_iters, tikh_tau, adapt_t)
+
+    def autotune(self, y, trial_iters: int = 20):
+        """Pick the fastest launch tuning for this plan (see deconv_autotune)."""
+        return deconv_autotune(self.handle, y.data_ptr(), trial_iters)
+
+    def retune(self, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1) -> None:
+        deconv_retune(self.handle, row_ctas, col_ctas, row_stage)
 
     def get_mu(self):
         """Per-image penalty of the next iteration (list of floats)."""

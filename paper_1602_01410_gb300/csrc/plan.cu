@@ -154,7 +154,10 @@ bool fit_image(int M, int N, int C, int nt, size_t esz, int rb_pref, int w_pref,
   return true;
 }
 
-deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
+// Tuning of the register-FFT passes (deconv_tune); NULL or entries <= 0 /
+// < 0: the defaults (152 CTAs per row class and per column pass; the forward
+// row half staged for one-channel single-class plans).
+deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *tune = nullptr) {
   if (!d || d->batch < 1 || !d->rows || !d->cols) return DECONV_EINVAL;
   if (d->channels != 1 && d->channels != 3) return DECONV_EINVAL;
   if (d->ksize < 1 || d->ksize % 2 == 0) return DECONV_EINVAL;
@@ -233,11 +236,12 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   // the staged rows of three channels would leave room for one row per CTA,
   // and the classes of a batch run concurrently only while their CTAs fit on
   // the SMs side by side.
-  const int row_stage =
+  int row_stage =
       (L.C == 1 && p2_rows.size() == 1 && g_rows == 0) ? env_int("DECONV_ROW_STAGE", 1) : env_int("DECONV_ROW_STAGE", 0);
+  if (tune && tune->row_stage >= 0) row_stage = L.C == 1 ? (tune->row_stage ? 1 : 0) : 0;
   for (const auto &kv : p2_rows) {
     const int tt = kv.first / 8, r = kv.first % 8, N = r * 32 * tt;
-    const int rtarget = env_int("DECONV_P2_ROW_CTAS", 152);
+    const int rtarget = (tune && tune->row_ctas > 0) ? tune->row_ctas : env_int("DECONV_P2_ROW_CTAS", 152);
     int rb = (int)std::max<long long>(1, (kv.second + rtarget - 1) / rtarget);
     rb = env_int("DECONV_P2_ROW_BLOCK", rb);
     while (rb > 1 && (p2_row_threads(L.C, rb, tt, r) > maxthr ||
@@ -249,7 +253,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   {
     long long tot = 0;
     for (const auto &kv : p2_cols) tot += kv.second;
-    const int ctarget = env_int("DECONV_P2_COL_CTAS", 152);
+    const int ctarget = (tune && tune->col_ctas > 0) ? tune->col_ctas : env_int("DECONV_P2_COL_CTAS", 152);
     p2w_all = (int)std::max<long long>(1, (tot + ctarget - 1) / ctarget);
     p2w_all = env_int("DECONV_P2_COL_TILE", p2w_all);
   }
@@ -421,6 +425,17 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo) {
   return DECONV_OK;
 }
 
+// The tunings deconv_autotune tries: CTAs per register-FFT row class and per
+// column pass (a multiple of the 152 SMs, or half of it), and for one channel
+// the staged or L1 forward row half.
+std::vector<deconv_tune> tune_candidates(int channels) {
+  std::vector<deconv_tune> v;
+  for (int st : channels == 1 ? std::vector<int>{0, 1} : std::vector<int>{0})
+    for (int rc : {152, 304, 608})
+      for (int cc : {76, 152, 304, 608}) v.push_back(deconv_tune{rc, cc, st});
+  return v;
+}
+
 }  // namespace
 
 struct deconv_plan_s {
@@ -436,7 +451,12 @@ struct deconv_plan_s {
   int tikh_iters = 0;
   double tikh_tau = 1e-3;
   double adapt_t = 0.0;
-  bool adapt_ready = false;  // the per-image penalties and v were set by a fresh solve
+  bool adapt_ready = false;
+  // Creation arguments kept for re-tuning (deconv_retune / deconv_autotune).
+  deconv_dims dims{};
+  std::vector<int32_t> rows, cols;
+  size_t ws_bytes = 0;
+  deconv_tune tune{0, 0, -1};  // the per-image penalties and v were set by a fresh solve
   cudaGraphExec_t gexec = nullptr;
   // While a graph is captured: the kernel classes of one pass (disjoint sets
   // of images) fan out over side streams, so their launches run concurrently.
@@ -748,6 +768,59 @@ deconv_status solve_t(deconv_plan_s *p, const void *y, void *x, int iters, int w
   return run_iters<T>(p, static_cast<T *>(x), iters, stats);
 }
 
+// Shared-memory opt-in of every kernel variant a plan may launch.
+template <typename T>
+cudaError_t prepare_all(const Layout &L) {
+  for (const Cls &c : L.row_cls) {
+    cudaError_t e = prepare_row<T>(c.cfg);
+    if (e == cudaSuccess && c.cfg.kind == KIND_P2) {  // the forward half with penalty adaptation
+      LaunchCfg d = c.cfg;
+      d.stage = 2;
+      e = prepare_row<T>(d);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  for (const Cls &c : L.col_cls) {
+    cudaError_t e = prepare_col<T>(c.cfg);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Re-lays out the per-row-block and per-class tables for another tuning.
+// The arrays that do not depend on it (state, spectra, H^, tables) keep
+// their place and contents; the iteration state does not survive.
+template <typename T>
+deconv_status retune_t(deconv_plan_s *p, const deconv_tune *t) {
+  Layout L2;
+  deconv_status st = build_layout(&p->dims, &L2, t);
+  if (st != DECONV_OK) return st;
+  if (L2.total > p->ws_bytes) return DECONV_ENOMEM;
+  const Layout &L = p->L;
+  if (L2.o_yt != L.o_yt || L2.o_Sa != L.o_Sa || L2.o_Sb != L.o_Sb || L2.o_hhat != L.o_hhat ||
+      L2.o_bits != L.o_bits || L2.o_tw != L.o_tw || L2.o_tw2 != L.o_tw2 || L2.o_s2 != L.o_s2 ||
+      L2.o_desc != L.o_desc || L2.total_tw2 != L.total_tw2)
+    return DECONV_EUNSUPPORTED;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  p->L = L2;
+  cudaStream_t s = p->stream;
+  for (const auto *v : {&p->L.row_cls, &p->L.col_cls})
+    for (const Cls &c : *v)
+      CK(cudaMemcpyAsync(p->ws + c.o_imgs, c.imgs.data(), c.imgs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->ws + p->L.o_desc, p->L.desc.data(), p->L.desc.size() * sizeof(ImageDesc),
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(p->ws + p->L.o_err, 0, sizeof(int), s));
+  CK(prepare_all<T>(p->L));
+  CK(cudaStreamSynchronize(s));
+  p->have_state = false;
+  p->adapt_ready = false;
+  p->tune = t ? *t : deconv_tune{0, 0, -1};
+  return DECONV_OK;
+}
+
 template <typename T>
 deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
   const Layout &L = p->L;
@@ -815,15 +888,7 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
                     p->ws + L.o_hhat, p->at<long long>(L.o_jobbeg), s));
   CK(launch_pack_mask(p->at<ImageDesc>(L.o_desc), L.B, L.total_words, p->at<long long>(L.o_wordbeg), mask,
                       p->at<uint32_t>(L.o_bits), s));
-  for (const Cls &c : L.row_cls) {
-    CK(prepare_row<T>(c.cfg));
-    if (c.cfg.kind == KIND_P2) {  // the forward half with penalty adaptation
-      LaunchCfg d = c.cfg;
-      d.stage = 2;
-      CK(prepare_row<T>(d));
-    }
-  }
-  for (const Cls &c : L.col_cls) CK(prepare_col<T>(c.cfg));
+  CK(prepare_all<T>(L));
   CK(cudaStreamSynchronize(s));
   return DECONV_OK;
 }
@@ -1098,7 +1163,13 @@ deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes) {
   Layout L;
   deconv_status st = build_layout(dims, &L);
   if (st != DECONV_OK) return st;
-  *bytes = L.total;
+  size_t total = L.total;
+  // room for every tuning the autotuner tries (they differ in the per-row-block arrays only)
+  for (const deconv_tune &t : tune_candidates(dims->channels)) {
+    Layout Lt;
+    if (build_layout(dims, &Lt, &t) == DECONV_OK) total = std::max(total, Lt.total);
+  }
+  *bytes = total;
   return DECONV_OK;
 }
 
@@ -1119,6 +1190,12 @@ deconv_status deconv_plan_create(deconv_plan *out, const deconv_dims *dims, cons
   }
   p->stream = static_cast<cudaStream_t>(stream);
   p->ws = static_cast<char *>(workspace);
+  p->ws_bytes = workspace_bytes;
+  p->dims = *dims;
+  p->rows.assign(dims->rows, dims->rows + dims->batch);
+  p->cols.assign(dims->cols, dims->cols + dims->batch);
+  p->dims.rows = p->rows.data();
+  p->dims.cols = p->cols.data();
   p->lambda = lambda;
   p->mu = mu;
   p->relax = dims->relax;
@@ -1147,6 +1224,64 @@ deconv_status deconv_set_options(deconv_plan p, const deconv_options *o) {
   p->tikh_iters = o->tikh_iters;
   p->tikh_tau = o->tikh_tau;
   p->adapt_t = o->adapt_t;
+  return DECONV_OK;
+}
+
+deconv_status deconv_retune(deconv_plan p, const deconv_tune *t) {
+  if (!p) return DECONV_EINVAL;
+  if (t && (t->row_ctas < 0 || t->col_ctas < 0 || t->row_ctas > 65536 || t->col_ctas > 65536 || t->row_stage > 1))
+    return DECONV_EINVAL;
+  return p->L.dtype == DECONV_F32 ? retune_t<float>(p, t) : retune_t<double>(p, t);
+}
+
+deconv_status deconv_get_tune(deconv_plan p, deconv_tune *t) {
+  if (!p || !t) return DECONV_EINVAL;
+  *t = p->tune;
+  return DECONV_OK;
+}
+
+deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters, deconv_tune *best,
+                              float *best_ms_per_iter) {
+  if (!p || !y || trial_iters < 1 || trial_iters > 100000) return DECONV_EINVAL;
+  const bool f32 = p->L.dtype == DECONV_F32;
+  std::vector<deconv_tune> cands = tune_candidates(p->L.C);
+  cands.insert(cands.begin(), deconv_tune{0, 0, -1});  // the defaults
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  deconv_tune bt{0, 0, -1};
+  float bms = -1.f;
+  deconv_status st = DECONV_OK;
+  for (const deconv_tune &t : cands) {
+    if (deconv_retune(p, &t) != DECONV_OK) continue;  // a tuning this plan cannot take
+    // fresh solve (builds the CUDA graph), then two timed warm continuations
+    st = f32 ? solve_t<float>(p, y, nullptr, trial_iters, 0, nullptr) : solve_t<double>(p, y, nullptr, trial_iters, 0, nullptr);
+    float ms = -1.f;
+    for (int rep = 0; rep < 2 && st == DECONV_OK; ++rep) {
+      if (cudaEventRecord(e0, p->stream) != cudaSuccess) st = DECONV_ECUDA;
+      if (st == DECONV_OK)
+        st = f32 ? solve_t<float>(p, nullptr, nullptr, trial_iters, 1, nullptr)
+                 : solve_t<double>(p, nullptr, nullptr, trial_iters, 1, nullptr);
+      float m = 0.f;
+      if (st == DECONV_OK && (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                              cudaEventElapsedTime(&m, e0, e1) != cudaSuccess))
+        st = DECONV_ECUDA;
+      if (st == DECONV_OK && (ms < 0.f || m < ms)) ms = m;
+    }
+    if (st != DECONV_OK) break;
+    if (bms < 0.f || ms < bms) {
+      bms = ms;
+      bt = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DECONV_OK) return st;
+  if (bms < 0.f) return DECONV_EUNSUPPORTED;
+  st = deconv_retune(p, &bt);
+  if (st != DECONV_OK) return st;
+  if (best) *best = bt;
+  if (best_ms_per_iter) *best_ms_per_iter = bms / (float)trial_iters;
   return DECONV_OK;
 }
 

@@ -174,3 +174,40 @@ def test_enlarged_prime_sizes():
 def test_enlarged_rgb_with_all_variants():
     prob = inputs.random_problem(62, [(61, 59)], 5, mask_kind="bayer", channels=3, iters=6, mu=1.0)
     check_adaptive(enlarged(prob), 1e-4, adapt_t=3.0, bgs_passes=2, tikh_iters=4, tikh_tau=1e-2)
+
+
+# ------------------------------------------------------------- autotuner ---
+
+def test_every_tuning_keeps_parity():
+    prob = inputs.random_problem(71, [(128, 256), (384, 384), (96, 160), (64, 1024)], 7, mask_kind="random",
+                                 frac=0.3, iters=3)
+    xo, _ = oracle_solve(prob)
+    _, _, plan = gpu_solve(prob)
+    import torch
+    dev = torch.device("cuda:0")
+    y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=torch.float32, device=dev)
+    from gpu_helpers import split
+    for t in [(152, 76, 0), (608, 608, 1), (304, 152, 1), (0, 0, -1)]:
+        plan.retune(*t)
+        x = plan.solve(y, prob.iters)
+        assert plan.sync() == 0
+        for a, b in zip(split(x.double().cpu().numpy(), prob), xo):
+            assert rel_l2([a], [b]) <= 3e-5
+
+
+def test_autotune_picks_a_candidate_and_keeps_parity():
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(72, [(256, 256), (384, 384)], 5, mask_kind="random", frac=0.3, iters=4)
+    xo, _ = oracle_solve(prob)
+    _, _, plan = gpu_solve(prob)
+    import torch
+    y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=torch.float32, device=torch.device("cuda:0"))
+    best, ms = plan.autotune(y, 10)
+    assert ms > 0 and best == pkg.deconv_get_tune(plan.handle)
+    with pytest.raises(pkg.DeconvError):
+        plan.solve(None, 2, warm=True)  # retuning discards the iteration state
+    x = plan.solve(y, prob.iters)
+    assert plan.sync() == 0
+    from gpu_helpers import split
+    for a, b in zip(split(x.double().cpu().numpy(), prob), xo):
+        assert rel_l2([a], [b]) <= 3e-5
