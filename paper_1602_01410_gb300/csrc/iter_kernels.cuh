@@ -46,6 +46,13 @@ __device__ __forceinline__ bool mask_bit(const uint32_t *bits, long long word0, 
 
 // Image of work item wi within a kernel class (its images in order of
 // increasing first work item).
+// Programmatic dependent launch: the iteration kernels may be launched while
+// their predecessor in the stream is still running (plan option); everything
+// before this wait reads only the plan's immutable tables (image
+// descriptors, class lists), everything after it may read and write the
+// state.  Without the launch attribute it returns at once.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 __device__ __forceinline__ int find_item(const ImageDesc *desc, const int *imgs, int n, int wi, bool row) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -139,6 +146,7 @@ __global__ void __launch_bounds__(NT) row_pass_kernel(RowArgs<T> a) {
   const cx<T> *din = reinterpret_cast<const cx<T> *>(a.d_in);
   cx<T> *dout = reinterpret_cast<cx<T> *>(a.d_out);
 
+  griddep_wait();
   // 1. rows r0-1 .. r1 of x + i T~x (ROW_ITER: Hermitian-extended inverse
   //    input; ROW_INIT: x^0 = y~0, imaginary part unused).
   if (init) {
@@ -346,6 +354,7 @@ __global__ void __launch_bounds__(NT) col_pass_kernel(ColArgs<T> a) {
   cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
   const long long base = Dp->spec + (long long)ch * M * Nh + k20;
 
+  griddep_wait();
   for (int e = threadIdx.x; e < M * w; e += NT) {
     const int i = e / w, ww = e - i * w;
     const cpair<T> q = ld_pair(&a.S_in[base + (long long)i * Nh + ww]);

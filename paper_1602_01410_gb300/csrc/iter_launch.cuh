@@ -3,6 +3,8 @@
 // register-FFT passes by threads per transform, radix and channel count).
 #pragma once
 
+#include <cstdlib>
+
 #include "iter_kernels.cuh"
 
 namespace dcv {
@@ -53,12 +55,33 @@ static const void *col_ptr(const LaunchCfg &c) {
   return nullptr;
 }
 
+// Programmatic dependent launch of the iteration kernels (DECONV_PDL=0 turns
+// it off): a kernel may start while its predecessor finishes, and waits in
+// griddep_wait() before it touches the state.
+static inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char *v = std::getenv("DECONV_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 template <typename A>
 static cudaError_t launch_ptr(const void *fn, const A &a, const LaunchCfg &c, cudaStream_t s) {
   if (!fn) return cudaErrorInvalidValue;
   if (c.grid <= 0) return cudaSuccess;
   void *args[] = {const_cast<A *>(&a)};
-  return cudaLaunchKernel(fn, dim3(c.grid), dim3(c.nt), args, c.smem, s);
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(c.grid);
+  lc.blockDim = dim3(c.nt);
+  lc.dynamicSmemBytes = c.smem;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = attr;
+  lc.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelExC(&lc, fn, args);
 }
 
 // The configuration of one half of a register-FFT row pass (its own shared memory size).

@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
 
+  griddep_wait();
   if (!init && !adj) {
     for (int c = 0; c < C; ++c) {
       copy_async<T>(Ys + (size_t)c * Rb * N, yt + px0 + c * P + (long long)r0 * N, nr * N, threadIdx.x, blockDim.x);
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kerne
   cx<T> *tile = Ex + gr * GS;
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  griddep_wait();
   cx<T> v[32];
   if (active) {
     const T *__restrict__ yrow = a.yt + px0 + ch * P + (long long)i * N;
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
   const unsigned gm = group_mask(TT);
 
+  griddep_wait();
   // Penalty: fixed, or per image (adaptation): tau = lambda / mu^i, r with
   // mu^{i+1} and d^{i+1} rescaled by s (v - s d^{i+1} = ((1+s) g - s) a).
   const bool norms = ADAPT && a.mode == ROW_NORMS;
@@ -415,6 +418,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
 
+  griddep_wait();
   for (int c = 0; c < C; ++c) {
     for (int k = 0; k < nr + 2; ++k)
       copy_async<T>(Xs + ((size_t)c * (Rb + 2) + k) * N, a.xbuf + px0 + c * P + (long long)wrapi(r0 - 1 + k, M) * N,
@@ -559,6 +563,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   const int S2 = 2 * Dp->W, scol = threadIdx.x % S2, r0t = threadIdx.x / S2, rstep = nthr / S2;
   const bool lane_ok = threadIdx.x < rstep * S2;  // threads beyond whole column sets stay idle here
   const bool scol_on = lane_ok && scol < 2 * w;
+  griddep_wait();
   if (scol_on)
     for (int ii = r0t; ii < M; ii += rstep)
       cp_async<sizeof(cx<T>)>(&St[scol * SR + ii],
