@@ -264,7 +264,64 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
   T s_dd = T(0), s_tv = T(0), s_dv = T(0);
   bool finite = true;
-  if (active) {
+  cx<T> v[32];
+  // Several channels, no statistics: the channel groups of a row share the
+  // per-channel squared norms of a at (i,p) and (i-1,p) through shared memory
+  // (the norm at (i,p-1) is that of the pixel to the left), instead of each
+  // group recomputing every channel's neighbourhood.
+  bool shared_norms = false;
+  if constexpr (C > 1 && !ADAPT) shared_norms = !stats;
+  if (shared_norms) {
+    T *N0 = reinterpret_cast<T *>(Cs), *NU = N0 + N;  // this (channel, row): |a(i,p)|^2, |a(i-1,p)|^2
+    const T *xr = xg + ch * P + (long long)i * N, *xu = xg + ch * P + (long long)iu * N,
+            *xd = xg + ch * P + (long long)id * N;
+    const cx<T> *dr = dg + ch * P + (long long)i * N, *dru = dg + ch * P + (long long)iu * N;
+    if (active) {
+#pragma unroll 4
+      for (int m = 0; m < 32; ++m) {
+        const int p = q + TT * m + L2 * gr;
+        const int p1 = (p + 1 == N) ? 0 : p + 1;
+        const T x0 = xr[p], xup = xu[p];
+        const cx<T> d0 = init ? mk<T>(T(0), T(0)) : dr[p], du = init ? mk<T>(T(0), T(0)) : dru[p];
+        const T a_h = (xr[p1] - x0) + d0.x, a_v = (xd[p] - x0) + d0.y;
+        const T a_hu = (xu[p1] - xup) + du.x, a_vu = (x0 - xup) + du.y;
+        N0[p] = a_h * a_h + a_v * a_v;
+        NU[p] = a_hu * a_hu + a_vu * a_vu;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      const T *N0r = reinterpret_cast<const T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)hh * RS);
+      const size_t cstride = (size_t)Rb * RS * 2;  // floats between the channels' regions of this row
+#pragma unroll 4
+      for (int m = 0; m < 32; ++m) {
+        const int p = q + TT * m + L2 * gr;
+        const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
+        T s0 = T(0), sl = T(0), su = T(0);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T *n0 = N0r + c * cstride;
+          s0 += n0[p];
+          sl += n0[pm];
+          su += n0[N + p];
+        }
+        const T x0 = xr[p], xup = xu[p];
+        const cx<T> d0 = init ? mk<T>(T(0), T(0)) : dr[p];
+        const T dlh = init ? T(0) : dr[pm].x, duv = init ? T(0) : dru[p].y;
+        const T ah0 = (xr[p1] - x0) + d0.x, av0 = (xd[p] - x0) + d0.y;
+        const T ahl = (x0 - xr[pm]) + dlh, avu = (x0 - xup) + duv;
+        const T g0 = init ? T(1) : (s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0));
+        const T gl = init ? T(1) : (sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0));
+        const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
+        dout[px0 + ch * P + (long long)i * N + p] = mk<T>((T(1) - g0) * ah0, (T(1) - g0) * av0);
+        const T r = a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
+                            ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
+        const T yv = yg[ch * P + (long long)i * N + p];
+        finite = finite && isfinite(r) && isfinite(yv);
+        v[m] = mk<T>(yv, r);
+      }
+    }
+  } else if (active) {
 #pragma unroll 4
     for (int m = 0; m < 32; ++m) {
       const int p = q + TT * m + L2 * gr;
@@ -342,14 +399,29 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
     return;
   }
   if (!finite) atomicOr(a.err, 1);
-  if (R > 1) __syncthreads(); else __syncwarp(gm);
-  cx<T> v[32];
-  if (active) {
+  if (shared_norms) {
+    __syncthreads();  // every channel group has read the norms before the region is reused
+    if (R > 1) {  // natural order -> decimation-in-time order of the sub-transforms
+      if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+        for (int m = 0; m < 32; ++m) Cs[q + TT * m + L2 * gr] = v[m];
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+      }
+      __syncthreads();
+    }
+  } else {
+    if (R > 1) __syncthreads(); else __syncwarp(gm);
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+    }
+    // every group of the row has read its inputs before the tiles overwrite them
+    if (R > 1) __syncthreads(); else __syncwarp(gm);
   }
-  // every group of the row has read its inputs before the tiles overwrite them
-  if (R > 1) __syncthreads(); else __syncwarp(gm);
   fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Cs);
   if (active) {
 #pragma unroll

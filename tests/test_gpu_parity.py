@@ -232,3 +232,14 @@ def test_mixed_radix_fp64():
     xg, _, _ = gpu_solve(prob)
     xo, _ = oracle_solve(prob)
     assert rel_l2(xg, xo) <= 1e-10
+
+
+def test_vectorial_tv_register_passes_without_stats():
+    # three channels, every register-FFT radix, statistics off (the channel
+    # groups of a row share their squared norms through shared memory)
+    prob = inputs.random_problem(31, [(64, 64), (128, 256), (384, 384), (640, 768), (512, 1280)], 7,
+                                 mask_kind="bayer", channels=3, iters=3)
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    for a, b in zip(xg, xo):
+        assert rel_l2([a], [b]) <= 3e-5
