@@ -311,6 +311,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch tuning (the autotuner runs at plan set-up, outside the timing)")
     ap.add_argument("--tune-iters", type=int, default=20)
+    ap.add_argument("--images", type=str, default="",
+                    help="comma-separated image indices of the batch to keep (small profiling cases)")
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the e2e, per-pass and CPU-baseline legs (profiling runs)")
     args = ap.parse_args()
@@ -342,6 +344,8 @@ def main():
     prob = make_problem(args.config)
     if args.iters > 0:
         prob.iters = args.iters
+    if args.images:
+        prob = subset_problem(prob, [int(v) for v in args.images.split(",")])
     total_px_all = prob.pixels()
     sharded = world > 1 and len(prob.shapes) > 1
     if sharded:

@@ -55,14 +55,15 @@ cudaError_t launch_add(double *acc, const double *v, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_taps(const ImageDesc *desc, int img, int Nh, int C, int K, const void *G, double *E, void *dh,
-                        int accumulate, cudaStream_t s) {
-  taps_stage1_kernel<T><<<(K * Nh + 127) / 128, 128, 0, s>>>(desc, img, C, K, reinterpret_cast<const cx<T> *>(G),
-                                                             reinterpret_cast<double2 *>(E));
+cudaError_t launch_taps(const ImageDesc *desc, int img, int M, int N, int C, int K, const void *G, double *E,
+                        void *dh, int accumulate, cudaStream_t s) {
+  const int Nh = N / 2 + 1, threads = 32 * (K < 32 ? K : 32);
+  taps_stage1_kernel<T><<<Nh, threads, (size_t)M * sizeof(double2), s>>>(
+      desc, img, C, K, reinterpret_cast<const cx<T> *>(G), reinterpret_cast<double2 *>(E));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  taps_stage2_kernel<T><<<(K * K + 127) / 128, 128, 0, s>>>(desc, img, K, reinterpret_cast<const double2 *>(E),
-                                                            reinterpret_cast<T *>(dh), accumulate);
+  taps_stage2_kernel<T><<<K, threads, (size_t)N * sizeof(double2), s>>>(
+      desc, img, K, reinterpret_cast<const double2 *>(E), reinterpret_cast<T *>(dh), accumulate);
   return cudaGetLastError();
 }
 
@@ -70,8 +71,8 @@ cudaError_t launch_taps(const ImageDesc *desc, int img, int Nh, int C, int K, co
   template cudaError_t launch_adj<T>(const AdjArgs<T> &, int, int, int, int, size_t, cudaStream_t);           \
   template cudaError_t prepare_adj<T>(int, int, size_t);                                                       \
   template cudaError_t launch_sqerr<T>(const T *, const T *, long long, double *, int, cudaStream_t);          \
-  template cudaError_t launch_taps<T>(const ImageDesc *, int, int, int, int, const void *, double *, void *, int, \
-                                      cudaStream_t);
+  template cudaError_t launch_taps<T>(const ImageDesc *, int, int, int, int, int, const void *, double *, void *, \
+                                      int, cudaStream_t);
 INST(float)
 INST(double)
 

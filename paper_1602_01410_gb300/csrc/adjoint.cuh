@@ -198,48 +198,80 @@ __global__ void sum_kernel(const double *v, int n, double scale, double *out) {
 // dL/dh from the accumulated spectrum G (per image and channel, M x (N/2+1)):
 // dL/dh[p+b][q+b] = (1/(MN)) sum_k w(k2) Re(G(k) exp(2 pi i (k1 p/M + k2 q/N))),
 // w = 1 at k2 = 0 and N/2, 2 elsewhere (G of real correlations is Hermitian).
-// Stage 1: E(p, k2) = sum_k1 G(k1, k2) exp(2 pi i k1 p / M), summed over channels.
+// Sums in FP64; the roots of unity come from a per-block table built with
+// sincospi.  Warp-shuffle reductions, one warp per output.
+//
+// Stage 1: E(p, k2) = sum_c sum_k1 G_c(k1, k2) exp(2 pi i k1 p / M).  One
+// block per k2, warps over p, lanes over k1.
 template <typename T>
 __global__ void taps_stage1_kernel(const ImageDesc *desc, int img, int C, int K, const cx<T> *G, double2 *E) {
+  extern __shared__ double2 rootM[];  // exp(2 pi i j / M), j < M
   const ImageDesc &D = desc[img];
   const int M = D.M, Nh = D.Nh, b = K / 2;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= K * Nh) return;
-  const int pi = e / Nh, k2 = e - pi * Nh, p = pi - b;
-  double re = 0.0, im = 0.0;
-  for (int c = 0; c < C; ++c) {
-    const cx<T> *Gc = G + D.spec + (long long)c * M * Nh;
-    for (int k1 = 0; k1 < M; ++k1) {
-      const long long ph = (((long long)k1 * p) % M + M) % M;
-      float s, co;
-      sincospif(2.0f * (float)ph / (float)M, &s, &co);
-      const cx<T> gv = Gc[(long long)k1 * Nh + k2];
-      re += double(gv.x) * co - double(gv.y) * s;
-      im += double(gv.x) * s + double(gv.y) * co;
-    }
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)j / (double)M, &sn, &cs);
+    rootM[j] = make_double2(cs, sn);
   }
-  E[e] = make_double2(re, im);
+  __syncthreads();
+  const int k2 = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int pi = warp; pi < K; pi += nw) {
+    const int p = pi - b, pm = ((p % M) + M) % M;
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < C; ++c) {
+      const cx<T> *Gc = G + D.spec + (long long)c * M * Nh + k2;
+      int ph = (int)(((long long)lane * pm) % M);
+      const int step = (int)((32LL * pm) % M);
+      for (int k1 = lane; k1 < M; k1 += 32) {
+        const cx<T> gv = Gc[(long long)k1 * Nh];
+        const double2 w = rootM[ph];
+        re += double(gv.x) * w.x - double(gv.y) * w.y;
+        im += double(gv.x) * w.y + double(gv.y) * w.x;
+        ph += step;
+        if (ph >= M) ph -= M;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) E[pi * Nh + k2] = make_double2(re, im);
+  }
 }
 
 // Stage 2: dh[p][q] (+)= (1/(MN)) sum_k2 w(k2) Re(E(p, k2) exp(2 pi i k2 q / N)).
+// One block per p, warps over q, lanes over k2.
 template <typename T>
 __global__ void taps_stage2_kernel(const ImageDesc *desc, int img, int K, const double2 *E, T *dh, int accumulate) {
+  extern __shared__ double2 rootN[];  // exp(2 pi i j / N), j < N
   const ImageDesc &D = desc[img];
   const int N = D.N, Nh = D.Nh, b = K / 2;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= K * K) return;
-  const int pi = e / K, qi = e - pi * K, q = qi - b;
-  double s = 0.0;
-  for (int k2 = 0; k2 < Nh; ++k2) {
-    const long long ph = (((long long)k2 * q) % N + N) % N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
     double sn, cs;
-    sincospi(2.0 * (double)ph / (double)N, &sn, &cs);
-    const double wgt = (k2 == 0 || 2 * k2 == N) ? 1.0 : 2.0;
-    const double2 ev = E[pi * Nh + k2];
-    s += wgt * (ev.x * cs - ev.y * sn);
+    sincospi(2.0 * (double)j / (double)N, &sn, &cs);
+    rootN[j] = make_double2(cs, sn);
   }
-  s /= (double)D.M * (double)N;
-  dh[e] = accumulate ? dh[e] + (T)s : (T)s;
+  __syncthreads();
+  const int pi = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int qi = warp; qi < K; qi += nw) {
+    const int q = qi - b, qm = ((q % N) + N) % N;
+    double acc = 0.0;
+    int ph = (int)(((long long)lane * qm) % N);
+    const int step = (int)((32LL * qm) % N);
+    for (int k2 = lane; k2 < Nh; k2 += 32) {
+      const double wgt = (k2 == 0 || 2 * k2 == N) ? 1.0 : 2.0;
+      const double2 ev = E[pi * Nh + k2], w = rootN[ph];
+      acc += wgt * (ev.x * w.x - ev.y * w.y);
+      ph += step;
+      if (ph >= N) ph -= N;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const double sres = acc / ((double)D.M * (double)N);
+      const int e = pi * K + qi;
+      dh[e] = accumulate ? dh[e] + (T)sres : (T)sres;
+    }
+  }
 }
 
 }  // namespace dcv

@@ -156,8 +156,8 @@ cudaError_t launch_sqerr(const T *x, const T *xt, long long n, double *part, int
 cudaError_t launch_sum(const double *v, int n, double scale, double *out, cudaStream_t s);
 cudaError_t launch_add(double *acc, const double *v, cudaStream_t s);
 template <typename T>
-cudaError_t launch_taps(const ImageDesc *desc, int img, int Nh, int C, int K, const void *G, double *E, void *dh,
-                        int accumulate, cudaStream_t s);
+cudaError_t launch_taps(const ImageDesc *desc, int img, int M, int N, int C, int K, const void *G, double *E,
+                        void *dh, int accumulate, cudaStream_t s);
 
 // Setup kernels (setup.cu).
 struct HhatJob {          // one half-spectrum to compute

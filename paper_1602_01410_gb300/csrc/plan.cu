@@ -1119,7 +1119,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
   CK(cudaMemsetAsync(dh, 0, (size_t)nk * L.K * L.K * sizeof(T), s));
   for (int j = 0; j < L.B; ++j) {
     T *dhj = static_cast<T *>(dh) + (L.kernel_per_image ? (size_t)j * L.K * L.K : 0);
-    CK(launch_taps<T>(desc, j, L.desc[j].Nh, L.C, L.K, at(G.o_G), reinterpret_cast<double *>(at(G.o_E)), dhj, 1, s));
+    CK(launch_taps<T>(desc, j, L.desc[j].M, L.desc[j].N, L.C, L.K, at(G.o_G), reinterpret_cast<double *>(at(G.o_E)), dhj, 1, s));
   }
   double hres[2] = {0, 0};
   CK(cudaMemcpyAsync(hres, res, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
