@@ -144,11 +144,16 @@ deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
  * pass aims at (rows per CTA and spectral columns per CTA follow); 0 = the
  * default (152, one per SM).  row_stage: -1 = default (the forward row half
  * stages its rows in shared memory for one-channel plans of one row class),
- * 0 = reads them through L1, 1 = stages them (one channel only). */
+ * 0 = reads them through L1, 1 = stages them (one channel only).
+ * fft_values: 16 gives a power-of-two row or column of length L to L/16
+ * threads (more resident warps), 32 to L/32 threads (fewer barriers). */
 typedef struct {
   int32_t row_ctas;
   int32_t col_ctas;
   int32_t row_stage;
+  int32_t fft_values;     /* power-of-two row transforms: complex values per thread, 16 or 32; 0 = default
+                            (16 for one channel, 32 for three) */
+  int32_t col_fft_values; /* the same for the column transforms; 0 = default (32) */
 } deconv_tune;
 
 /* Re-lays out a plan for another tuning (t = NULL: the defaults).  The
@@ -160,8 +165,9 @@ deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
 
 /* Autotuner: times trial_iters iterations (after a fresh solve of y that
  * builds the CUDA graph; the plan's options apply) under the default tuning
- * and each candidate (row_ctas in {152, 304, 608}, col_ctas in {76, 152,
- * 304, 608}, and for one channel row_stage in {0, 1}), keeps the fastest
+ * and each candidate (row_ctas and col_ctas in {152, 608}, fft_values and
+ * col_fft_values in {16, 32}, and for one channel row_stage in {0, 1}), keeps
+ * the fastest
  * (best, best_ms_per_iter: nullable host outputs) and leaves the plan in it
  * with no iteration state.  y: device, batch layout.  Synchronous. */
 deconv_status deconv_autotune(deconv_plan plan, const void *y, int32_t trial_iters, deconv_tune *best,

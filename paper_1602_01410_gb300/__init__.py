@@ -54,7 +54,8 @@ class deconv_options(ctypes.Structure):
 
 
 class deconv_tune(ctypes.Structure):
-    _fields_ = [("row_ctas", ctypes.c_int32), ("col_ctas", ctypes.c_int32), ("row_stage", ctypes.c_int32)]
+    _fields_ = [("row_ctas", ctypes.c_int32), ("col_ctas", ctypes.c_int32), ("row_stage", ctypes.c_int32),
+                ("fft_values", ctypes.c_int32), ("col_fft_values", ctypes.c_int32)]
 
 
 _lib = None
@@ -218,22 +219,26 @@ def deconv_get_mu(plan: int, nimg: int):
     return [float(v) for v in out]
 
 
-def deconv_retune(plan: int, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1) -> None:
-    t = deconv_tune(int(row_ctas), int(col_ctas), int(row_stage))
+def deconv_retune(plan: int, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
+                  col_fft_values: int = 0) -> None:
+    t = deconv_tune(int(row_ctas), int(col_ctas), int(row_stage), int(fft_values), int(col_fft_values))
     _check(load().deconv_retune(plan, ctypes.byref(t)), "deconv_retune")
 
 
 def deconv_get_tune(plan: int) -> dict:
     t = deconv_tune()
     _check(load().deconv_get_tune(plan, ctypes.byref(t)), "deconv_get_tune")
-    return {"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage}
+    return {"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage, "fft_values": t.fft_values,
+            "col_fft_values": t.col_fft_values}
 
 
 def deconv_autotune(plan: int, y_ptr: int, trial_iters: int = 20):
     """Returns (best tuning as a dict, its ms per iteration)."""
     t, ms = deconv_tune(), ctypes.c_float(0.0)
     _check(load().deconv_autotune(plan, y_ptr, trial_iters, ctypes.byref(t), ctypes.byref(ms)), "deconv_autotune")
-    return {"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage}, float(ms.value)
+    return ({"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage, "fft_values": t.fft_values,
+            "col_fft_values": t.col_fft_values},
+            float(ms.value))
 
 
 def deconv_fast_shape(M: int, N: int, channels: int = 1, ksize: int = 3, dtype: int = DECONV_F32):
@@ -333,8 +338,9 @@ class Plan:
         """Pick the fastest launch tuning for this plan (see deconv_autotune)."""
         return deconv_autotune(self.handle, y.data_ptr(), trial_iters)
 
-    def retune(self, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1) -> None:
-        deconv_retune(self.handle, row_ctas, col_ctas, row_stage)
+    def retune(self, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
+               col_fft_values: int = 0) -> None:
+        deconv_retune(self.handle, row_ctas, col_ctas, row_stage, fft_values, col_fft_values)
 
     def get_mu(self):
         """Per-image penalty of the next iteration (list of floats)."""

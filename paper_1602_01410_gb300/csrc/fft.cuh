@@ -295,6 +295,104 @@ __device__ __forceinline__ void fft_mixed(cx<T> (&v)[32], bool active, cx<T> *ti
 }
 
 // ---------------------------------------------------------------------------
+// Register-resident transform of length L = 16 TT by TT threads holding 16
+// complex values each (TT in {1, 2, 4, 8, 16, 32, 64}): twice the threads of
+// fft_p2 for the same length, so twice the resident warps for a pass whose
+// parallelism is its row or column count.  Index split n = q + TT m
+// (q < TT, m < 16), k = k1 + 16 k2: a 16-point DFT in registers, the twiddle
+// w_L^(q k1) from a [k1][q] table, then the TT-point DFTs over q for every
+// k1: for TT <= 16 one transpose through the group's tile and TT-point DFTs
+// in registers; for TT = A B (A = 4 or 8, B = TT / A) two transposes with a
+// B-point stage, the twiddle w_TT^(a c) ([a][c] table) and an A-point stage
+// (q = a + A b, k2 = c + B d).  Thread q enters with v[m] = x[q + TT m] and
+// leaves with v[r] = X[v16_pos<TT>(q, r)].  Groups of 64 threads span two
+// warps and synchronise with the named barrier `bar` (1..15).
+template <int TT> __device__ __forceinline__ void group_bar(unsigned gmask, int bar) {
+  if constexpr (TT <= 32)
+    __syncwarp(gmask);
+  else
+    asm volatile("bar.sync %0, %1;\n" ::"r"(bar), "n"(TT) : "memory");
+}
+
+template <int TT> __host__ __device__ constexpr int v16_A() { return TT == 64 ? 8 : 4; }
+
+// Output position of register r of thread q (see fft_v16).
+template <int TT> __device__ __forceinline__ int v16_pos(int q, int r) {
+  if constexpr (TT <= 16) {
+    return q + TT * (r / TT + (16 / TT) * (r % TT));
+  } else {
+    constexpr int A = v16_A<TT>(), B = TT / A;
+    return (q / B) * (16 / A) + r / A + 16 * (q % B + B * (r % A));
+  }
+}
+
+// Shared tile of one group (complex elements).
+__host__ __device__ constexpr int v16_group_stride_h(int tt) {
+  return tt <= 16 ? 16 * (tt + 1) + (tt < 16 ? tt : 0) : 16 * (tt / (tt == 64 ? 8 : 4)) * ((tt == 64 ? 8 : 4) + 1);
+}
+template <int TT> __host__ __device__ constexpr int v16_group_stride() { return v16_group_stride_h(TT); }
+
+template <typename T, int TT, int SIGN>
+__device__ __forceinline__ void fft_v16(cx<T> (&v)[16], cx<T> *tile, int q, unsigned gmask, int bar,
+                                        const cx<T> *__restrict__ tw16, const cx<T> *__restrict__ twab) {
+  Dft<T, 16, SIGN>::run(v);
+  if constexpr (TT > 1) {
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+      cx<T> w = __ldg(&tw16[k1 * TT + q]);
+      if (SIGN > 0) w.y = -w.y;
+      v[k1] = cmul<T>(v[k1], w);
+    }
+    if constexpr (TT <= 16) {
+      constexpr int LD = TT + 1;
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) tile[k1 * LD + q] = v[k1];
+      group_bar<TT>(gmask, bar);
+#pragma unroll
+      for (int j = 0; j < 16 / TT; ++j) {
+#pragma unroll
+        for (int t = 0; t < TT; ++t) v[j * TT + t] = tile[(q + TT * j) * LD + t];
+        Dft<T, TT, SIGN>::run(&v[j * TT]);
+      }
+      group_bar<TT>(gmask, bar);
+    } else {
+      constexpr int A = v16_A<TT>(), B = TT / A, LD1 = TT + 1, LD2 = A + 1;
+      const int a = q % A, b = q / A;
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) tile[k1 * LD1 + q] = v[k1];
+      group_bar<TT>(gmask, bar);
+#pragma unroll
+      for (int i = 0; i < 16 / B; ++i)
+#pragma unroll
+        for (int b2 = 0; b2 < B; ++b2) v[i * B + b2] = tile[(b * (16 / B) + i) * LD1 + a + A * b2];
+      group_bar<TT>(gmask, bar);
+#pragma unroll
+      for (int i = 0; i < 16 / B; ++i) Dft<T, B, SIGN>::run(&v[i * B]);
+#pragma unroll
+      for (int c = 1; c < B; ++c) {
+        cx<T> w = __ldg(&twab[a * B + c]);
+        if (SIGN > 0) w.y = -w.y;
+#pragma unroll
+        for (int i = 0; i < 16 / B; ++i) v[i * B + c] = cmul<T>(v[i * B + c], w);
+      }
+#pragma unroll
+      for (int i = 0; i < 16 / B; ++i)
+#pragma unroll
+        for (int c = 0; c < B; ++c) tile[((b * (16 / B) + i) * B + c) * LD2 + a] = v[i * B + c];
+      group_bar<TT>(gmask, bar);
+      const int c2 = q % B, e = q / B;
+#pragma unroll
+      for (int i = 0; i < 16 / A; ++i)
+#pragma unroll
+        for (int a2 = 0; a2 < A; ++a2) v[i * A + a2] = tile[((e * (16 / A) + i) * B + c2) * LD2 + a2];
+      group_bar<TT>(gmask, bar);
+#pragma unroll
+      for (int i = 0; i < 16 / A; ++i) Dft<T, A, SIGN>::run(&v[i * A]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // One radix-R Stockham pass over S signals of length L held in buf.  The
 // host plans S * L <= 30 NT so that every butterfly has a register slot.
 template <typename T, int NT, int R, int SIGN>

@@ -29,6 +29,8 @@ struct ImageDesc {
   int s2_row, s2_col;    // 4 sin^2(pi k / L) table offsets for N and M
   int tw2_row, tw2_col;  // [k1][t] twiddle-table offsets of the power-of-two (sub-)length, -1 if none
   int tw3_row, tw3_col;  // [r][k2] twiddles exp(-2 pi i r k2 / L) of a length R * 2^k, -1 if none
+  int tw16_row, tw16_col;  // 16 values per thread: [k1][q] twiddles exp(-2 pi i k1 q / L), -1 if none
+  int twab_row, twab_col;  // 16 values per thread, L >= 512: [a][c] twiddles exp(-2 pi i a c / (L/16))
   FftSched sched_row, sched_col;
 };
 
@@ -98,8 +100,9 @@ template <typename T> struct ColArgs {
 enum KernelKind { KIND_GENERIC = 0, KIND_P2 = 1 };
 struct LaunchCfg {
   int kind;      // KernelKind
-  int tt;        // KIND_P2: threads per sub-transform (sub-length / 32)
-  int r;         // KIND_P2: length = r * 32 * tt, r in {1, 3, 5}
+  int tt;        // KIND_P2: threads per sub-transform (sub-length / v)
+  int r;         // KIND_P2: length = r * v * tt, r in {1, 3, 5}
+  int v;         // KIND_P2: complex values per thread, 32 (fft_p2 / fft_mixed) or 16 (fft_v16, r = 1)
   int stage;     // KIND_P2 rows, forward half: 0 reads through L1, 1 stages its rows (one
                  // channel), 2 reads through L1 with penalty adaptation.  KIND_P2
                  // columns: 1 = the variant with the Tikhonov step / per-image penalty

@@ -17,22 +17,22 @@ template <typename T> constexpr int kMaxNt = sizeof(T) == 4 ? 512 : 256;
 // parallel.  half 0: inverse half, 1: forward half (stage 0 reads through
 // L1, 1 stages its rows (one channel), 2 adds penalty adaptation), 2: the y~
 // spectrum of an inner pass.
-template <typename T, int R> const void *p2_row_kernel(int C, int tt, int half, int stage);
-template <typename T, int R> const void *p2_col_kernel(int tt, int ext);
+template <typename T, int R> const void *p2_row_kernel(int C, int tt, int v, int half, int stage);
+template <typename T, int R> const void *p2_col_kernel(int tt, int v, int ext);
 
 template <typename T>
-static const void *p2_row_ptr(int C, int tt, int r, int half, int stage) {
+static const void *p2_row_ptr(int C, int tt, int r, int v, int half, int stage) {
   switch (r) {
-    case 1: return p2_row_kernel<T, 1>(C, tt, half, stage);
-    case 3: return p2_row_kernel<T, 3>(C, tt, half, stage);
-    case 5: return p2_row_kernel<T, 5>(C, tt, half, stage);
+    case 1: return p2_row_kernel<T, 1>(C, tt, v, half, stage);
+    case 3: return p2_row_kernel<T, 3>(C, tt, v, half, stage);
+    case 5: return p2_row_kernel<T, 5>(C, tt, v, half, stage);
   }
   return nullptr;
 }
 
 template <typename T>
 static const void *row_ptr(const LaunchCfg &c, int half = 0) {
-  if (c.kind == KIND_P2) return p2_row_ptr<T>(c.channels, c.tt, c.r, half, c.stage);
+  if (c.kind == KIND_P2) return p2_row_ptr<T>(c.channels, c.tt, c.r, c.v ? c.v : 32, half, c.stage);
   if (c.nt == 512 && kMaxNt<T> == 512)
     return c.channels == 3 ? (const void *)row_pass_kernel<T, kMaxNt<T>, 3> : (const void *)row_pass_kernel<T, kMaxNt<T>, 1>;
   if (c.nt == 256)
@@ -44,9 +44,9 @@ template <typename T>
 static const void *col_ptr(const LaunchCfg &c) {
   if (c.kind == KIND_P2) {
     switch (c.r) {
-      case 1: return p2_col_kernel<T, 1>(c.tt, c.stage);
-      case 3: return p2_col_kernel<T, 3>(c.tt, c.stage);
-      case 5: return p2_col_kernel<T, 5>(c.tt, c.stage);
+      case 1: return p2_col_kernel<T, 1>(c.tt, c.v ? c.v : 32, c.stage);
+      case 3: return p2_col_kernel<T, 3>(c.tt, c.v ? c.v : 32, c.stage);
+      case 5: return p2_col_kernel<T, 5>(c.tt, c.v ? c.v : 32, c.stage);
     }
     return nullptr;
   }

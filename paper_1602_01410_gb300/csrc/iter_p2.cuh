@@ -55,6 +55,28 @@ template <int TT> __device__ __forceinline__ constexpr int p2_unslot(int m) {
   return (m % (32 / TT)) * TT + m / (32 / TT);
 }
 
+// Register-transform helpers for V = 32 (fft_p2 / fft_mixed) or V = 16
+// (fft_v16, R = 1) values per thread.
+template <int V, int TT> __device__ __forceinline__ int reg_pos(int q, int j) {
+  if constexpr (V == 32)
+    return q + TT * p2_slot<TT>(j);
+  else
+    return v16_pos<TT>(q, j);
+}
+template <int V, int TT> __host__ __device__ constexpr int reg_group_stride() {
+  return V == 32 ? p2_group_stride<TT>() : v16_group_stride<TT>();
+}
+template <typename T, int V, int TT, int R, int SIGN>
+__device__ __forceinline__ void fft_reg(cx<T> (&v)[V], bool active, cx<T> *tile, int q, unsigned gm, int bar, int gr,
+                                        const cx<T> *__restrict__ tw2, const cx<T> *__restrict__ tw3, cx<T> *E) {
+  if constexpr (V == 32) {
+    fft_mixed<T, TT, R, SIGN>(v, active, tile, q, gm, gr, tw2, tw3, E);
+  } else {
+    static_assert(R == 1, "16 values per thread: power-of-two lengths only");
+    if (active) fft_v16<T, TT, SIGN>(v, tile, q, gm, bar, tw2, tw3);
+  }
+}
+
 // All three kernels below handle L = R * 32 * TT (R in {1, 3, 5}): a
 // transform of length L is done by R groups of TT threads (fft_mixed); with
 // R = 1 it is fft_p2 alone.  Work item layout: group g of a CTA serves
@@ -70,10 +92,10 @@ template <int TT> __device__ __forceinline__ constexpr int p2_unslot(int m) {
 // xbuf <- b, yt <- yt + T~b instead of the z-update.
 // Shared memory: [one region of R transpose tiles per (channel, row), which
 // the R groups also use as their exchange buffer][y~ C x Rb x N][mask words].
-template <typename T, int TT, int C, int R>
+template <typename T, int TT, int C, int R, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, RS = R * GS;
+  constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, RS = R * GS;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb, wpr = N / 32;
@@ -81,6 +103,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   const int r0 = blk * Rb, nr = min(Rb, M - r0);
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int bar = 1 + g;  // named barrier of a 64-thread group (group_bar)
   const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
@@ -95,8 +118,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   cx<T> *tile = Ex + gr * GS;
   T *Ys = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)C * Rb * RS);  // [C][Rb][N]
   uint32_t *Ms = reinterpret_cast<uint32_t *>(Ys + (size_t)C * Rb * N);              // [C][Rb][N/32]
-  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
 
   griddep_wait();
   if (!init && !adj) {
@@ -110,29 +133,29 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
 
   const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
   T s_dz = T(0), s_fit = T(0);
-  cx<T> v[32];
+  cx<T> v[V];
   const long long rowp = px0 + ch * P + (long long)i * N;
   if (active) {
     if (init) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = mk<T>(yt[rowp + q + TT * p2_slot<TT>(j) + L2 * gr], T(0));
+      for (int j = 0; j < V; ++j) v[j] = mk<T>(yt[rowp + reg_pos<V, TT>(q, j) + L2 * gr], T(0));
     } else {
       const cpair<T> *src = a.S_in + Dp->spec + ((long long)ch * M + i) * Nh;
 #pragma unroll
-      for (int m = 0; m < 32; ++m) {
+      for (int m = 0; m < V; ++m) {
         const int n = R * (q + TT * m) + gr;
         const cpair<T> c = src[2 * n <= N ? n : N - n];
         v[m] = 2 * n <= N ? mk<T>(c.ar - c.bi, c.ai + c.br) : mk<T>(c.ar + c.bi, c.br - c.ai);
       }
     }
   }
-  if (!init) fft_mixed<T, TT, R, +1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  if (!init) fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Ex);
   cp_async_wait_all();
   __syncthreads();
   if (active && adj) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int p = q + TT * p2_slot<TT>(j) + L2 * gr;
+    for (int j = 0; j < V; ++j) {
+      const int p = reg_pos<V, TT>(q, j) + L2 * gr;
       xbuf[rowp + p] = v[j].x;
       yt[rowp + p] += v[j].y;
     }
@@ -141,8 +164,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
     const T *yrow = Ys + ((size_t)ch * Rb + hh) * N;
     const uint32_t *mrow = Ms + ((size_t)ch * Rb + hh) * wpr;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int p = q + TT * p2_slot<TT>(j) + L2 * gr;
+    for (int j = 0; j < V; ++j) {
+      const int p = reg_pos<V, TT>(q, j) + L2 * gr;
       xbuf[rowp + p] = v[j].x;
       if (xout) xout[rowp + p] = v[j].x;
       if (!init) {
@@ -174,10 +197,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
 // Y_row, Hermitian; k <= N/2 is stored into the Y half of S_out, the R half
 // is kept).  Same CTA layout as the inverse half; shared memory: one region
 // of R transpose tiles per (channel, row).
-template <typename T, int TT, int C, int R>
+template <typename T, int TT, int C, int R, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, RS = R * GS;
+  constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, RS = R * GS;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb;
@@ -185,27 +208,28 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kerne
   const int r0 = blk * Rb, nr = min(Rb, M - r0);
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int bar = 1 + g;  // named barrier of a 64-thread group (group_bar)
   const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
   const unsigned gm = group_mask(TT);
   cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)row_id * RS;
   cx<T> *tile = Ex + gr * GS;
-  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
   griddep_wait();
-  cx<T> v[32];
+  cx<T> v[V];
   if (active) {
     const T *__restrict__ yrow = a.yt + px0 + ch * P + (long long)i * N;
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = mk<T>(yrow[R * (q + TT * m) + gr], T(0));
+    for (int m = 0; m < V; ++m) v[m] = mk<T>(yrow[R * (q + TT * m) + gr], T(0));
   }
-  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Ex);
   if (active) {
     cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int k = q + TT * p2_slot<TT>(j) + L2 * gr;
+    for (int j = 0; j < V; ++j) {
+      const int k = reg_pos<V, TT>(q, j) + L2 * gr;
       if (2 * k <= N) *reinterpret_cast<cx<T> *>(&dst[k]) = v[j];
     }
   }
@@ -222,10 +246,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kerne
 // Shared memory: one region of R transpose tiles per (channel, row); it
 // holds y~ + i r, then the transpose tiles and the exchange buffer, then the
 // transformed row.
-template <typename T, int TT, int C, int R, bool ADAPT>
+template <typename T, int TT, int C, int R, bool ADAPT, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, RS = R * GS;
+  constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, RS = R * GS;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb;
@@ -233,6 +257,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   const int r0 = blk * Rb, nr = min(Rb, M - r0);
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int bar = 1 + g;  // named barrier of a 64-thread group (group_bar)
   const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
@@ -244,8 +269,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   cx<T> *__restrict__ dout = reinterpret_cast<cx<T> *>(a.d_out);
   cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)row_id * RS;  // this row's region
   cx<T> *tile = Cs + gr * GS;
-  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
   const unsigned gm = group_mask(TT);
 
   griddep_wait();
@@ -264,7 +289,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
   T s_dd = T(0), s_tv = T(0), s_dv = T(0);
   bool finite = true;
-  cx<T> v[32];
+  cx<T> v[V];
   // Several channels, no statistics: the channel groups of a row share the
   // per-channel squared norms of a at (i,p) and (i-1,p) through shared memory
   // (the norm at (i,p-1) is that of the pixel to the left), instead of each
@@ -278,7 +303,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
     const cx<T> *dr = dg + ch * P + (long long)i * N, *dru = dg + ch * P + (long long)iu * N;
     if (active) {
 #pragma unroll 4
-      for (int m = 0; m < 32; ++m) {
+      for (int m = 0; m < V; ++m) {
         const int p = q + TT * m + L2 * gr;
         const int p1 = (p + 1 == N) ? 0 : p + 1;
         const T x0 = xr[p], xup = xu[p];
@@ -294,7 +319,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
       const T *N0r = reinterpret_cast<const T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)hh * RS);
       const size_t cstride = (size_t)Rb * RS * 2;  // floats between the channels' regions of this row
 #pragma unroll 4
-      for (int m = 0; m < 32; ++m) {
+      for (int m = 0; m < V; ++m) {
         const int p = q + TT * m + L2 * gr;
         const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
         T s0 = T(0), sl = T(0), su = T(0);
@@ -323,7 +348,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
     }
   } else if (active) {
 #pragma unroll 4
-    for (int m = 0; m < 32; ++m) {
+    for (int m = 0; m < V; ++m) {
       const int p = q + TT * m + L2 * gr;
       const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
       T s0 = T(0), sl = T(0), su = T(0), tv = T(0);
@@ -404,30 +429,30 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
     if (R > 1) {  // natural order -> decimation-in-time order of the sub-transforms
       if (active) {
 #pragma unroll
-        for (int m = 0; m < 32; ++m) Cs[q + TT * m + L2 * gr] = v[m];
+        for (int m = 0; m < V; ++m) Cs[q + TT * m + L2 * gr] = v[m];
       }
       __syncthreads();
       if (active) {
 #pragma unroll
-        for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+        for (int m = 0; m < V; ++m) v[m] = Cs[R * (q + TT * m) + gr];
       }
       __syncthreads();
     }
   } else {
-    if (R > 1) __syncthreads(); else __syncwarp(gm);
+    if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
     if (active) {
 #pragma unroll
-      for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+      for (int m = 0; m < V; ++m) v[m] = Cs[R * (q + TT * m) + gr];
     }
     // every group of the row has read its inputs before the tiles overwrite them
-    if (R > 1) __syncthreads(); else __syncwarp(gm);
+    if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   }
-  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Cs);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Cs);
   if (active) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) Cs[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
+    for (int j = 0; j < V; ++j) Cs[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
   }
-  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   if (active) {
     cpair<T> *__restrict__ dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
     for (int k = q + TT * gr; k < Nh; k += TT * R) {
@@ -463,10 +488,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
 // Shared memory: [x C x (Rb+2) rows][d C x (Rb+1) rows][y~ C x Rb rows] (the
 // transpose tiles reuse it after a barrier), then per row y~ + i r and the
 // exchange buffer.
-template <typename T, int TT, int C, int R>
+template <typename T, int TT, int C, int R, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT;
+  constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, true)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh, Rb = Dp->Rb;
@@ -474,6 +499,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   const int r0 = blk * Rb, nr = min(Rb, M - r0);
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int bar = 1 + g;  // named barrier of a 64-thread group (group_bar)
   const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
@@ -487,8 +513,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)row_id * N;
   cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)C * Rb * N +
               (size_t)row_id * N;
-  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row;
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
 
   griddep_wait();
   for (int c = 0; c < C; ++c) {
@@ -512,7 +538,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   bool finite = true;
   if (active) {
 #pragma unroll 4
-    for (int m = 0; m < 32; ++m) {
+    for (int m = 0; m < V; ++m) {
       const int p = q + TT * m + L2 * gr;
       const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
       T s0 = T(0), sl = T(0), su = T(0), tv = T(0);
@@ -561,20 +587,20 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   }
   if (!finite) atomicOr(a.err, 1);
   __syncthreads();  // the transpose tiles below reuse the staged rows
-  cx<T> v[32];
+  cx<T> v[V];
   if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+    for (int m = 0; m < V; ++m) v[m] = Cs[R * (q + TT * m) + gr];
   }
   if (R > 1) __syncthreads();  // every group has read its inputs before outputs overwrite Cs
   cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
   const unsigned gm = group_mask(TT);
-  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, Ex);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Ex);
   if (active) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) Cs[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
+    for (int j = 0; j < V; ++j) Cs[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
   }
-  if (R > 1) __syncthreads(); else __syncwarp(gm);
+  if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   if (active) {
     cpair<T> *__restrict__ dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
     for (int k = q + TT * gr; k < Nh; k += TT * R) {
@@ -605,24 +631,25 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
 // place (their transpose tiles and exchange buffer are that column's
 // storage).  Shared memory: [2W columns of R tiles (+4 elements of padding,
 // which spreads the staging stores over the banks)][H^ tile M x w][sin^2 tables].
-template <typename T, int TT, int R, bool EXT>
+template <typename T, int TT, int R, bool EXT, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>(), L2 = 32 * TT, SR = R * GS + 4;
+  constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, SR = R * GS + 4;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, false)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh;
   const int local = wi - Dp->col_begin;
   const int ch = local / Dp->col_tiles, t = local - ch * Dp->col_tiles;
   const int k20 = t * Dp->W, w = min(Dp->W, Nh - k20);
-  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_col;
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_col;
+  const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_col : Dp->tw16_col);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_col : Dp->twab_col);
   const cx<T> *__restrict__ H = reinterpret_cast<const cx<T> *>(a.hhat) + Dp->hhat;
   const T *s2c = a.s2 + Dp->s2_col, *s2r = a.s2 + Dp->s2_row;
   cx<T> *St = reinterpret_cast<cx<T> *>(smem_raw);                  // [2W][SR]
   cx<T> *Hs = St + (size_t)2 * Dp->W * SR;                           // [M][w] H^ tile
   T *S2s = reinterpret_cast<T *>(Hs + (size_t)M * Dp->W);            // [M] column sin^2, then [W] row sin^2
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int bar = 1 + g;  // named barrier of a 64-thread group (group_bar)
   const unsigned gm = group_mask(TT);
   const int gr = g % R, sig = g / R;
   cx<T> *col = St + (size_t)sig * SR;  // this signal's column
@@ -647,17 +674,17 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
-  cx<T> v[32];
+  cx<T> v[V];
   const bool active = sig < 2 * w;
   if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = col[R * (q + TT * m) + gr];
+    for (int m = 0; m < V; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
-  if (R > 1) __syncthreads(); else __syncwarp(gm);
-  fft_mixed<T, TT, R, -1>(v, active, tile, q, gm, gr, tw2, tw3, col);
+  if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, col);
   if (active) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) col[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
+    for (int j = 0; j < V; ++j) col[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
   }
   __syncthreads();
   // EXT: a Tikhonov warm-start step (tikh > 0) or a per-image penalty.
@@ -705,13 +732,13 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   __syncthreads();
   if (active) {
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = col[R * (q + TT * m) + gr];
+    for (int m = 0; m < V; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
-  if (R > 1) __syncthreads(); else __syncwarp(gm);
-  fft_mixed<T, TT, R, +1>(v, active, tile, q, gm, gr, tw2, tw3, col);
+  if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
+  fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, col);
   if (active) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) col[q + TT * p2_slot<TT>(j) + L2 * gr] = v[j];
+    for (int j = 0; j < V; ++j) col[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
   }
   __syncthreads();
   if (lane_ok && scol < w) {

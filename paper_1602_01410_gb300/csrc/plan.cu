@@ -76,8 +76,15 @@ bool is_pow2_32(int L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
 
 // Register-FFT parameters of a length: L = r * 32 * tt with (tt, r) = (L/32, 1)
 // for powers of two 64..1024, or r in {3, 5} and 32 * tt in {128, 256, 512}.
-bool reg_fft_params(int L, int *tt, int *r) {
+bool reg_fft_params(int L, int *tt, int *r, int *v = nullptr, int vpref = 32) {
+  if (v) *v = 32;
   if (is_pow2_32(L)) {
+    if (v && vpref == 16) {  // 16 values per thread: L / 16 threads (4..64)
+      *v = 16;
+      *tt = L / 16;
+      *r = 1;
+      return true;
+    }
     *tt = L / 32;
     *r = 1;
     return true;
@@ -94,39 +101,55 @@ bool reg_fft_params(int L, int *tt, int *r) {
   return false;
 }
 
+// Register-FFT kernel class key: values per thread, threads per sub-transform, radix.
+int p2_key(int v, int tt, int r) { return (v == 16 ? 1000 : 0) + tt * 8 + r; }
+void p2_unkey(int key, int *v, int *tt, int *r) {
+  *v = key >= 1000 ? 16 : 32;
+  *tt = (key % 1000) / 8;
+  *r = key % 8;
+}
+int p2_group_stride_hv(int tt, int v) { return v == 16 ? v16_group_stride_h(tt) : p2_group_stride_h(tt); }
+
 // Register-FFT row passes (inverse and forward halves): rb rows per CTA, r
 // groups of tt threads per (channel, row), rounded up to whole warps.
 int p2_row_threads(int C, int rb, int tt, int r = 1) {
+  if (tt >= 32) return C * rb * r * tt;
   const int per_warp = 32 / tt;
   return (C * rb * r + per_warp - 1) / per_warp * per_warp * tt;
 }
 
 // Shared memory of one half of a register-FFT row pass (0: inverse, 1: forward).
-size_t p2_row_smem_half(int C, int N, int rb, int tt, size_t esz, int r, int stage, int half) {
-  const size_t region = (size_t)C * rb * r * p2_group_stride_h(tt) * 2 * esz;  // tiles / exchange per row
+size_t p2_row_smem_half(int C, int N, int rb, int tt, size_t esz, int r, int stage, int half, int v = 32) {
+  const size_t gs = (size_t)p2_group_stride_hv(tt, v);
+  const size_t region = (size_t)C * rb * r * gs * 2 * esz;  // tiles / exchange per row
   if (half == 0) return region + (size_t)C * rb * N * esz + (size_t)C * rb * (N / 32) * 4;  // + y~ rows, mask
   if (!stage) return region;
   // staged forward half: [x (rb+2) rows][d (rb+1) rows][y~ rb rows] (the tiles
   // reuse them), then y~ + i r and the exchange buffer per row
-  const size_t tiles = (size_t)(p2_row_threads(C, rb, tt, r) / tt) * p2_group_stride_h(tt) * 2 * esz;
+  const size_t tiles = (size_t)(p2_row_threads(C, rb, tt, r) / tt) * gs * 2 * esz;
   const size_t ex = r > 1 ? (size_t)C * rb * N * 2 * esz : 0;
   return std::max((size_t)C * ((rb + 2) + 2 * (rb + 1) + rb) * N * esz, tiles) + (size_t)C * rb * N * 2 * esz + ex;
 }
 
-size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz, int r = 1, int stage = 0) {
-  return std::max(p2_row_smem_half(C, N, rb, tt, esz, r, stage, 0), p2_row_smem_half(C, N, rb, tt, esz, r, stage, 1));
+size_t p2_row_smem(int C, int N, int rb, int tt, size_t esz, int r = 1, int stage = 0, int v = 32) {
+  return std::max(p2_row_smem_half(C, N, rb, tt, esz, r, stage, 0, v),
+                  p2_row_smem_half(C, N, rb, tt, esz, r, stage, 1, v));
 }
 
 // Column pass: one column of r transpose tiles (+4 padding) per signal, H^ tile, sin^2 tables.
-size_t p2_col_smem(int M, int w, int tt, size_t esz, int r = 1) {
-  return (size_t)2 * w * (r * p2_group_stride_h(tt) + 4) * 2 * esz + (size_t)M * w * 2 * esz +
+size_t p2_col_smem(int M, int w, int tt, size_t esz, int r = 1, int v = 32) {
+  return (size_t)2 * w * (r * p2_group_stride_hv(tt, v) + 4) * 2 * esz + (size_t)M * w * 2 * esz +
          (size_t)((M + w + 3) & ~3) * esz;
 }
 
 int p2_col_threads(int w, int tt, int r = 1) {
+  if (tt >= 32) return 2 * w * r * tt;
   const int per_warp = 32 / tt;
   return (2 * w * r + per_warp - 1) / per_warp * per_warp * tt;
 }
+
+// Groups of 64 threads synchronise on named barriers 1..15: at most 15 per CTA.
+bool p2_groups_ok(int threads, int tt) { return tt < 64 || threads / tt <= 15; }
 
 // Row-block height and column-tile width for one image under CTA size nt.
 bool fit_image(int M, int N, int C, int nt, size_t esz, int rb_pref, int w_pref, int *Rb, int *W) {
@@ -189,19 +212,25 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
   std::vector<int> row_key(L.B, 0), col_key(L.B, 0);
   long long g_rows = 0, g_cols = 0;
   std::map<int, long long> p2_rows, p2_cols;
+  // Values per thread of the power-of-two register transforms: 16 (twice the
+  // threads, so twice the resident warps) unless the tuning asks for 32.
+  // Defaults: rows of one channel 16 (their parallelism is the row count),
+  // three channels and columns 32 (measured on GB300).
+  const int vrow = (tune && tune->fft_values > 0) ? tune->fft_values : env_int("DECONV_FFT_VALUES", L.C == 1 ? 16 : 32);
+  const int vcol = (tune && tune->col_fft_values > 0) ? tune->col_fft_values : env_int("DECONV_COL_FFT_VALUES", 32);
   for (int j = 0; j < L.B; ++j) {
     const int M = d->rows[j], N = d->cols[j];
-    int tt, r;
-    if (allow_p2 && reg_fft_params(N, &tt, &r) && p2_row_threads(L.C, 1, tt, r) <= maxthr &&
-        p2_row_smem(L.C, N, 1, tt, L.esz, r, L.C == 1) <= kMaxSmem) {
-      row_key[j] = tt * 8 + r;
+    int tt, r, v;
+    if (allow_p2 && reg_fft_params(N, &tt, &r, &v, vrow) && p2_row_threads(L.C, 1, tt, r) <= maxthr &&
+        p2_groups_ok(p2_row_threads(L.C, 1, tt, r), tt) && p2_row_smem(L.C, N, 1, tt, L.esz, r, L.C == 1, v) <= kMaxSmem) {
+      row_key[j] = p2_key(v, tt, r);
       p2_rows[row_key[j]] += M;
     } else {
       g_rows += M;
     }
-    if (allow_p2 && reg_fft_params(M, &tt, &r) && p2_col_threads(1, tt, r) <= maxthr &&
-        p2_col_smem(M, 1, tt, L.esz, r) <= kMaxSmem) {
-      col_key[j] = tt * 8 + r;
+    if (allow_p2 && reg_fft_params(M, &tt, &r, &v, vcol) && p2_col_threads(1, tt, r) <= maxthr &&
+        p2_col_smem(M, 1, tt, L.esz, r, v) <= kMaxSmem) {
+      col_key[j] = p2_key(v, tt, r);
       p2_cols[col_key[j]] += (long long)L.C * (N / 2 + 1);
     } else {
       g_cols += (long long)L.C * (N / 2 + 1);
@@ -240,12 +269,14 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
       (L.C == 1 && p2_rows.size() == 1 && g_rows == 0) ? env_int("DECONV_ROW_STAGE", 1) : env_int("DECONV_ROW_STAGE", 0);
   if (tune && tune->row_stage >= 0) row_stage = L.C == 1 ? (tune->row_stage ? 1 : 0) : 0;
   for (const auto &kv : p2_rows) {
-    const int tt = kv.first / 8, r = kv.first % 8, N = r * 32 * tt;
+    int v, tt, r;
+    p2_unkey(kv.first, &v, &tt, &r);
+    const int N = r * v * tt;
     const int rtarget = (tune && tune->row_ctas > 0) ? tune->row_ctas : env_int("DECONV_P2_ROW_CTAS", 152);
     int rb = (int)std::max<long long>(1, (kv.second + rtarget - 1) / rtarget);
     rb = env_int("DECONV_P2_ROW_BLOCK", rb);
-    while (rb > 1 && (p2_row_threads(L.C, rb, tt, r) > maxthr ||
-                      p2_row_smem(L.C, N, rb, tt, L.esz, r, row_stage) > kMaxSmem))
+    while (rb > 1 && (p2_row_threads(L.C, rb, tt, r) > maxthr || !p2_groups_ok(p2_row_threads(L.C, rb, tt, r), tt) ||
+                      p2_row_smem(L.C, N, rb, tt, L.esz, r, row_stage, v) > kMaxSmem))
       --rb;
     p2_rb[kv.first] = rb;
   }
@@ -258,20 +289,26 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     p2w_all = env_int("DECONV_P2_COL_TILE", p2w_all);
   }
   for (const auto &kv : p2_cols) {
-    const int tt = kv.first / 8, r = kv.first % 8, M = r * 32 * tt;
+    int v, tt, r;
+    p2_unkey(kv.first, &v, &tt, &r);
+    const int M = r * v * tt;
     int w = std::min(p2w_all, 16);
-    while (w > 1 && (p2_col_threads(w, tt, r) > maxthr || p2_col_smem(M, w, tt, L.esz, r) > kMaxSmem)) --w;
+    while (w > 1 && (p2_col_threads(w, tt, r) > maxthr || !p2_groups_ok(p2_col_threads(w, tt, r), tt) ||
+                     p2_col_smem(M, w, tt, L.esz, r, v) > kMaxSmem))
+      --w;
     p2_w[kv.first] = w;
   }
 
   // Class lists (in order of first appearance).
   auto class_index = [](std::vector<Cls> &v, int kind, int key) {
-    const int tt = key / 8, r = key % 8;
+    int vv = 32, tt = 0, r = 0;
+    if (kind == KIND_P2) p2_unkey(key, &vv, &tt, &r);
     for (size_t k = 0; k < v.size(); ++k)
-      if (v[k].cfg.kind == kind && v[k].cfg.tt == tt && v[k].cfg.r == r) return (int)k;
+      if (v[k].cfg.kind == kind && v[k].cfg.tt == tt && v[k].cfg.r == r && v[k].cfg.v == vv) return (int)k;
     Cls c;
     std::memset(&c.cfg, 0, sizeof(c.cfg));
     c.cfg.kind = kind;
+    c.cfg.v = vv;
     c.cfg.tt = tt;
     c.cfg.r = r;
     v.push_back(c);
@@ -308,9 +345,10 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     if (row_key[j]) {
       rc.cfg.stage = row_stage;
       rc.cfg.nt = p2_row_threads(L.C, D.Rb, rc.cfg.tt, rc.cfg.r);
-      rc.cfg.smem = std::max(rc.cfg.smem, p2_row_smem_half(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r, row_stage, 0));
-      rc.cfg.smem_fwd =
-          std::max(rc.cfg.smem_fwd, p2_row_smem_half(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r, row_stage, 1));
+      rc.cfg.smem =
+          std::max(rc.cfg.smem, p2_row_smem_half(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r, row_stage, 0, rc.cfg.v));
+      rc.cfg.smem_fwd = std::max(
+          rc.cfg.smem_fwd, p2_row_smem_half(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r, row_stage, 1, rc.cfg.v));
     } else {
       rc.cfg.nt = L.nt;
       const size_t ldr = (size_t)((L.C * (D.Rb + 2)) | 1);
@@ -318,7 +356,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     }
     if (col_key[j]) {
       cc.cfg.nt = p2_col_threads(D.W, cc.cfg.tt, cc.cfg.r);
-      cc.cfg.smem = std::max(cc.cfg.smem, p2_col_smem(D.M, D.W, cc.cfg.tt, L.esz, cc.cfg.r));
+      cc.cfg.smem = std::max(cc.cfg.smem, p2_col_smem(D.M, D.W, cc.cfg.tt, L.esz, cc.cfg.r, cc.cfg.v));
     } else {
       cc.cfg.nt = L.nt;
       cc.cfg.smem = std::max(cc.cfg.smem, (size_t)D.M * (size_t)((2 * D.W) | 1) * 2 * L.esz);
@@ -366,6 +404,26 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     // [k1][t] tables of the power-of-two (sub-)lengths and [r][k2] tables of
     // the R * 2^k lengths share one array (tw2_off keyed by length, tw3 by -length).
     D.tw2_row = D.tw2_col = D.tw3_row = D.tw3_col = -1;
+    D.tw16_row = D.tw16_col = D.twab_row = D.twab_col = -1;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int len = pass ? D.M : D.N;
+      if (!is_pow2_32(len)) continue;
+      // 16 values per thread: [k1][q] table (key len + 2^20), and for L/16 > 16
+      // the [a][c] table of the L/16-point stage (key len + 2^21)
+      const int k16 = len + (1 << 20), kab = len + (1 << 21), tt16 = len / 16;
+      if (!L.tw2_off.count(k16)) {
+        L.tw2_off[k16] = (int)L.total_tw2;
+        L.total_tw2 += len;
+      }
+      (pass ? D.tw16_col : D.tw16_row) = L.tw2_off[k16];
+      if (tt16 > 16) {
+        if (!L.tw2_off.count(kab)) {
+          L.tw2_off[kab] = (int)L.total_tw2;
+          L.total_tw2 += tt16;
+        }
+        (pass ? D.twab_col : D.twab_row) = L.tw2_off[kab];
+      }
+    }
     for (int pass = 0; pass < 2; ++pass) {
       const int len = pass ? D.M : D.N;
       int tt, r;
@@ -430,9 +488,11 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
 // the staged or L1 forward row half.
 std::vector<deconv_tune> tune_candidates(int channels) {
   std::vector<deconv_tune> v;
-  for (int st : channels == 1 ? std::vector<int>{0, 1} : std::vector<int>{0})
-    for (int rc : {152, 304, 608})
-      for (int cc : {76, 152, 304, 608}) v.push_back(deconv_tune{rc, cc, st});
+  for (int fv : {16, 32})
+    for (int cfv : {16, 32})
+      for (int st : channels == 1 ? std::vector<int>{0, 1} : std::vector<int>{0})
+        for (int rc : {152, 608})
+          for (int cc : {152, 608}) v.push_back(deconv_tune{rc, cc, st, fv, cfv});
   return v;
 }
 
@@ -456,7 +516,7 @@ struct deconv_plan_s {
   deconv_dims dims{};
   std::vector<int32_t> rows, cols;
   size_t ws_bytes = 0;
-  deconv_tune tune{0, 0, -1};  // the per-image penalties and v were set by a fresh solve
+  deconv_tune tune{0, 0, -1, 0};  // the per-image penalties and v were set by a fresh solve
   cudaGraphExec_t gexec = nullptr;
   // While a graph is captured: the kernel classes of one pass (disjoint sets
   // of images) fan out over side streams, so their launches run concurrently.
@@ -817,7 +877,7 @@ deconv_status retune_t(deconv_plan_s *p, const deconv_tune *t) {
   CK(cudaStreamSynchronize(s));
   p->have_state = false;
   p->adapt_ready = false;
-  p->tune = t ? *t : deconv_tune{0, 0, -1};
+  p->tune = t ? *t : deconv_tune{0, 0, -1, 0, 0};
   return DECONV_OK;
 }
 
@@ -843,7 +903,23 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
   std::vector<T> tw2(2 * L.total_tw2);
   for (const auto &kv : L.tw2_off) {
     const int o = kv.second;
-    if (kv.first > 0) {
+    if (kv.first >= (1 << 21)) {  // [a][c] = exp(-2 pi i a c / TT), TT = L / 16 = A B
+      const int len = kv.first - (1 << 21), tt = len / 16, A = tt == 64 ? 8 : 4, B = tt / A;
+      for (int a = 0; a < A; ++a)
+        for (int c = 0; c < B; ++c) {
+          const double ang = 2.0 * M_PI * (double)(a * c) / (double)tt;
+          tw2[2 * (o + a * B + c)] = (T)std::cos(ang);
+          tw2[2 * (o + a * B + c) + 1] = (T)(-std::sin(ang));
+        }
+    } else if (kv.first >= (1 << 20)) {  // [k1][q] = exp(-2 pi i k1 q / L), k1 < 16, q < L / 16
+      const int len = kv.first - (1 << 20), tt = len / 16;
+      for (int k1 = 0; k1 < 16; ++k1)
+        for (int q = 0; q < tt; ++q) {
+          const double ang = 2.0 * M_PI * (double)(k1 * q) / (double)len;
+          tw2[2 * (o + k1 * tt + q)] = (T)std::cos(ang);
+          tw2[2 * (o + k1 * tt + q) + 1] = (T)(-std::sin(ang));
+        }
+    } else if (kv.first > 0) {
       const int len = kv.first, tt = len / 32;
       for (int k1 = 0; k1 < 32; ++k1)
         for (int t = 0; t < tt; ++t) {
@@ -950,7 +1026,7 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
   G->items = 0;
   for (const Cls &c : L.row_cls) {
     const ImageDesc &D0 = L.desc[c.imgs[0]];
-    const int tt = c.cfg.tt;
+    const int tt = D0.N / 32;  // the adjoint row kernel holds 32 values per thread
     int rb = D0.Rb;
     while (rb > 1 && (adj_smem(L.C, D0.N, rb, tt, L.esz) > kMaxSmem || p2_row_threads(L.C, rb, tt) > maxthr)) --rb;
     if (adj_smem(L.C, D0.N, rb, tt, L.esz) > kMaxSmem) return DECONV_EUNSUPPORTED;
@@ -1010,7 +1086,8 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
   auto at = [&](size_t off) { return gw + off; };
   CK(cudaMemcpyAsync(at(G.o_adjbeg), G.adj_begin.data(), G.adj_begin.size() * sizeof(int), cudaMemcpyHostToDevice,
                      s));
-  for (size_t c = 0; c < L.row_cls.size(); ++c) CK(prepare_adj<T>(L.row_cls[c].cfg.tt, L.C, G.smem[c]));
+  for (size_t c = 0; c < L.row_cls.size(); ++c)
+    CK(prepare_adj<T>(L.desc[L.row_cls[c].imgs[0]].N / 32, L.C, G.smem[c]));
 
   // 1. Forward with checkpoints of (y~, d, forward spectrum) every k iterations.
   st = init_state<T>(p, static_cast<const T *>(y), nullptr);
@@ -1096,7 +1173,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
         aa.relax = (T)p->relax;
         aa.lscale = (T)(2.0 / (double)npx);
         aa.tpart = reinterpret_cast<double *>(at(G.o_tpart)) + ci * G.items;
-        CK(launch_adj<T>(aa, cl.cfg.tt, L.C, G.grid[ci], G.nt[ci], G.smem[ci], s));
+        CK(launch_adj<T>(aa, L.desc[cl.imgs[0]].N / 32, L.C, G.grid[ci], G.nt[ci], G.smem[ci], s));
       }
       cur ^= 1;
       // taub of this step (all classes; unused partial slots stay zero) into res[1], fixed order.
@@ -1229,7 +1306,9 @@ deconv_status deconv_set_options(deconv_plan p, const deconv_options *o) {
 
 deconv_status deconv_retune(deconv_plan p, const deconv_tune *t) {
   if (!p) return DECONV_EINVAL;
-  if (t && (t->row_ctas < 0 || t->col_ctas < 0 || t->row_ctas > 65536 || t->col_ctas > 65536 || t->row_stage > 1))
+  if (t && (t->row_ctas < 0 || t->col_ctas < 0 || t->row_ctas > 65536 || t->col_ctas > 65536 || t->row_stage > 1 ||
+            (t->fft_values != 0 && t->fft_values != 16 && t->fft_values != 32) ||
+            (t->col_fft_values != 0 && t->col_fft_values != 16 && t->col_fft_values != 32)))
     return DECONV_EINVAL;
   return p->L.dtype == DECONV_F32 ? retune_t<float>(p, t) : retune_t<double>(p, t);
 }
@@ -1245,11 +1324,11 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   if (!p || !y || trial_iters < 1 || trial_iters > 100000) return DECONV_EINVAL;
   const bool f32 = p->L.dtype == DECONV_F32;
   std::vector<deconv_tune> cands = tune_candidates(p->L.C);
-  cands.insert(cands.begin(), deconv_tune{0, 0, -1});  // the defaults
+  cands.insert(cands.begin(), deconv_tune{0, 0, -1, 0, 0});  // the defaults
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  deconv_tune bt{0, 0, -1};
+  deconv_tune bt{0, 0, -1, 0};
   float bms = -1.f;
   deconv_status st = DECONV_OK;
   for (const deconv_tune &t : cands) {

@@ -187,7 +187,8 @@ def test_every_tuning_keeps_parity():
     dev = torch.device("cuda:0")
     y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=torch.float32, device=dev)
     from gpu_helpers import split
-    for t in [(152, 76, 0), (608, 608, 1), (304, 152, 1), (0, 0, -1)]:
+    for t in [(152, 76, 0, 32, 32), (608, 608, 1, 32, 16), (304, 152, 1, 16, 32), (152, 608, 0, 16, 16),
+              (0, 0, -1, 0, 0)]:
         plan.retune(*t)
         x = plan.solve(y, prob.iters)
         assert plan.sync() == 0
