@@ -326,9 +326,17 @@ template <int TT> __device__ __forceinline__ int v16_pos(int q, int r) {
   }
 }
 
+// Tile strides of the two-transpose path (complex elements), chosen so that
+// the 32 lanes of every transposing access spread over all 16 bank pairs:
+// first tile [k1][q] with row stride LD1 = TT + TT/16 (TT = 32: 34, 64: 68),
+// second tile [k1][c][a] with stride A + 1 for c and S1 = B (A + 1) + TT/16
+// for k1.
+__host__ __device__ constexpr int v16_ld1(int tt) { return tt + tt / 16; }
+__host__ __device__ constexpr int v16_s1(int tt) { return (tt == 64 ? 8 : 8) * ((tt == 64 ? 8 : 4) + 1) + tt / 16; }
+
 // Shared tile of one group (complex elements).
 __host__ __device__ constexpr int v16_group_stride_h(int tt) {
-  return tt <= 16 ? 16 * (tt + 1) + (tt < 16 ? tt : 0) : 16 * (tt / (tt == 64 ? 8 : 4)) * ((tt == 64 ? 8 : 4) + 1);
+  return tt <= 16 ? 16 * (tt + 1) + (tt < 16 ? tt : 0) : 16 * v16_s1(tt);
 }
 template <int TT> __host__ __device__ constexpr int v16_group_stride() { return v16_group_stride_h(TT); }
 
@@ -356,7 +364,7 @@ __device__ __forceinline__ void fft_v16(cx<T> (&v)[16], cx<T> *tile, int q, unsi
       }
       group_bar<TT>(gmask, bar);
     } else {
-      constexpr int A = v16_A<TT>(), B = TT / A, LD1 = TT + 1, LD2 = A + 1;
+      constexpr int A = v16_A<TT>(), B = TT / A, LD1 = v16_ld1(TT), LD2 = A + 1, S1 = v16_s1(TT);
       const int a = q % A, b = q / A;
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) tile[k1 * LD1 + q] = v[k1];
@@ -378,13 +386,13 @@ __device__ __forceinline__ void fft_v16(cx<T> (&v)[16], cx<T> *tile, int q, unsi
 #pragma unroll
       for (int i = 0; i < 16 / B; ++i)
 #pragma unroll
-        for (int c = 0; c < B; ++c) tile[((b * (16 / B) + i) * B + c) * LD2 + a] = v[i * B + c];
+        for (int c = 0; c < B; ++c) tile[(b * (16 / B) + i) * S1 + c * LD2 + a] = v[i * B + c];
       group_bar<TT>(gmask, bar);
       const int c2 = q % B, e = q / B;
 #pragma unroll
       for (int i = 0; i < 16 / A; ++i)
 #pragma unroll
-        for (int a2 = 0; a2 < A; ++a2) v[i * A + a2] = tile[((e * (16 / A) + i) * B + c2) * LD2 + a2];
+        for (int a2 = 0; a2 < A; ++a2) v[i * A + a2] = tile[(e * (16 / A) + i) * S1 + c2 * LD2 + a2];
       group_bar<TT>(gmask, bar);
 #pragma unroll
       for (int i = 0; i < 16 / A; ++i) Dft<T, A, SIGN>::run(&v[i * A]);
