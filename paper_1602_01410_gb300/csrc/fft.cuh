@@ -304,7 +304,7 @@ __device__ __forceinline__ void fft_mixed(cx<T> (&v)[32], bool active, cx<T> *ti
 // k1: for TT <= 16 one transpose through the group's tile and TT-point DFTs
 // in registers; for TT = A B (A = 4 or 8, B = TT / A) two transposes with a
 // B-point stage, the twiddle w_TT^(a c) ([a][c] table) and an A-point stage
-// (q = a + A b, k2 = c + B d).  Thread q enters with v[m] = x[q + TT m] and
+// (k2 = c + B d; the TT-point index splits as a + A b).  Thread q enters with v[m] = x[q + TT m] and
 // leaves with v[r] = X[v16_pos<TT>(q, r)].  Groups of 64 threads span two
 // warps and synchronise with the named barrier `bar` (1..15).
 template <int TT> __device__ __forceinline__ void group_bar(unsigned gmask, int bar) {
@@ -322,21 +322,20 @@ template <int TT> __device__ __forceinline__ int v16_pos(int q, int r) {
     return q + TT * (r / TT + (16 / TT) * (r % TT));
   } else {
     constexpr int A = v16_A<TT>(), B = TT / A;
-    return (q / B) * (16 / A) + r / A + 16 * (q % B + B * (r % A));
+    return q % 16 + 16 * ((q / 16) * (16 / A) + r / A + B * (r % A));
   }
 }
 
-// Tile strides of the two-transpose path (complex elements), chosen so that
-// the 32 lanes of every transposing access spread over all 16 bank pairs:
-// first tile [k1][q] with row stride LD1 = TT + TT/16 (TT = 32: 34, 64: 68),
-// second tile [k1][c][a] with stride A + 1 for c and S1 = B (A + 1) + TT/16
-// for k1.
-__host__ __device__ constexpr int v16_ld1(int tt) { return tt + tt / 16; }
-__host__ __device__ constexpr int v16_s1(int tt) { return (tt == 64 ? 8 : 8) * ((tt == 64 ? 8 : 4) + 1) + tt / 16; }
+// Tiles of the two-transpose path (complex elements), laid out so that the
+// 32 lanes of every transposing access spread over all 16 bank pairs: the
+// first [k1][q] with row stride LD1 (TT = 32: 36, 64: 72), the second
+// [c][a][k1] with strides L16 for a (32: 24, 64: 20) and A L16 for c.
+__host__ __device__ constexpr int v16_ld1(int tt) { return tt == 64 ? 72 : 36; }
+__host__ __device__ constexpr int v16_l16(int tt) { return tt == 64 ? 20 : 24; }
 
 // Shared tile of one group (complex elements).
 __host__ __device__ constexpr int v16_group_stride_h(int tt) {
-  return tt <= 16 ? 16 * (tt + 1) + (tt < 16 ? tt : 0) : 16 * v16_s1(tt);
+  return tt <= 16 ? 16 * (tt + 1) + (tt < 16 ? tt : 0) : tt * v16_l16(tt);  // B * (A * L16)
 }
 template <int TT> __host__ __device__ constexpr int v16_group_stride() { return v16_group_stride_h(TT); }
 
@@ -364,7 +363,9 @@ __device__ __forceinline__ void fft_v16(cx<T> (&v)[16], cx<T> *tile, int q, unsi
       }
       group_bar<TT>(gmask, bar);
     } else {
-      constexpr int A = v16_A<TT>(), B = TT / A, LD1 = v16_ld1(TT), LD2 = A + 1, S1 = v16_s1(TT);
+      // stage 2 takes (k1, a) = (b + B i, q mod A), stage 3 takes (k1, c) =
+      // (q mod 16, (q / 16) (16 / A) + i)
+      constexpr int A = v16_A<TT>(), B = TT / A, LD1 = v16_ld1(TT), L16 = v16_l16(TT), S2 = A * L16;
       const int a = q % A, b = q / A;
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) tile[k1 * LD1 + q] = v[k1];
@@ -372,7 +373,7 @@ __device__ __forceinline__ void fft_v16(cx<T> (&v)[16], cx<T> *tile, int q, unsi
 #pragma unroll
       for (int i = 0; i < 16 / B; ++i)
 #pragma unroll
-        for (int b2 = 0; b2 < B; ++b2) v[i * B + b2] = tile[(b * (16 / B) + i) * LD1 + a + A * b2];
+        for (int b2 = 0; b2 < B; ++b2) v[i * B + b2] = tile[(b + B * i) * LD1 + a + A * b2];
       group_bar<TT>(gmask, bar);
 #pragma unroll
       for (int i = 0; i < 16 / B; ++i) Dft<T, B, SIGN>::run(&v[i * B]);
@@ -386,13 +387,13 @@ __device__ __forceinline__ void fft_v16(cx<T> (&v)[16], cx<T> *tile, int q, unsi
 #pragma unroll
       for (int i = 0; i < 16 / B; ++i)
 #pragma unroll
-        for (int c = 0; c < B; ++c) tile[(b * (16 / B) + i) * S1 + c * LD2 + a] = v[i * B + c];
+        for (int c = 0; c < B; ++c) tile[c * S2 + a * L16 + b + B * i] = v[i * B + c];
       group_bar<TT>(gmask, bar);
-      const int c2 = q % B, e = q / B;
+      const int k1 = q % 16, f = q / 16;
 #pragma unroll
       for (int i = 0; i < 16 / A; ++i)
 #pragma unroll
-        for (int a2 = 0; a2 < A; ++a2) v[i * A + a2] = tile[(e * (16 / A) + i) * S1 + c2 * LD2 + a2];
+        for (int a2 = 0; a2 < A; ++a2) v[i * A + a2] = tile[(f * (16 / A) + i) * S2 + a2 * L16 + k1];
       group_bar<TT>(gmask, bar);
 #pragma unroll
       for (int i = 0; i < 16 / A; ++i) Dft<T, A, SIGN>::run(&v[i * A]);
