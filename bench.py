@@ -236,6 +236,12 @@ def subset_problem(prob, idx):
     return sub
 
 
+# DRAM bytes (read + write) per channel-pixel of one row pass (both halves),
+# from ncu captures of the current row kernels (profiles/row_col_pass_c2_1024_ncu_full.md,
+# profiles/traffic_c4_1536_rgb_ncu.md); None where no capture was taken.
+ROW_TRAFFIC_BYTES_PER_PX = {"c2": 29.60e6 / 1048576, "c4": 52.7}
+
+
 def measured_peak_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -474,7 +480,11 @@ def main():
         "e2e": {"value": e2e_value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": int(y_np.size * esz),
                 "d2h_bytes_per_step": int(y_np.size * esz)},
         "roofline": {"bound": "hbm", "kernel": f"{dom}_pass", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": (ROW_TRAFFIC_BYTES_PER_PX[args.config] * px
+                                 if dom == "row" and args.config in ROW_TRAFFIC_BYTES_PER_PX and not args.images
+                                 else None),
+                     "peak_kind": peak_kind,
                      "ms_per_launch": ms_dom, "bytes_per_px": per_px[dom],
                      "other_pass_ms": ms_col if dom == "row" else ms_row,
                      "algorithmic_bytes_per_px_iter": algorithmic_bytes_per_px(f_unobs, esz)},
