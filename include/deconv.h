@@ -145,15 +145,15 @@ deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
  * default (152, one per SM).  row_stage: -1 = default (the forward row half
  * stages its rows in shared memory for one-channel plans of one row class),
  * 0 = reads them through L1, 1 = stages them (one channel only).
- * fft_values: 16 gives a power-of-two row or column of length L to L/16
- * threads (more resident warps), 32 to L/32 threads (fewer barriers). */
+ * fft_values: 16 gives a row or column of length L to L/16 threads (more
+ * resident warps), 32 to L/32 threads (fewer transposes). */
 typedef struct {
   int32_t row_ctas;
   int32_t col_ctas;
   int32_t row_stage;
-  int32_t fft_values;     /* power-of-two row transforms: complex values per thread, 16 or 32; 0 = default
-                            (16 for one channel, 32 for three) */
-  int32_t col_fft_values; /* the same for the column transforms; 0 = default (32) */
+  int32_t fft_values;     /* register row transforms: complex values per thread, 16 or 32; 0 = default (16) */
+  int32_t col_fft_values; /* the same for the column transforms; 0 = default (32 for power-of-two
+                             lengths, 16 for 3 * 2^k and 5 * 2^k) */
 } deconv_tune;
 
 /* Re-lays out a plan for another tuning (t = NULL: the defaults).  The

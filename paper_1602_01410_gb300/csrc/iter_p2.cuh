@@ -66,14 +66,42 @@ template <int V, int TT> __device__ __forceinline__ int reg_pos(int q, int j) {
 template <int V, int TT> __host__ __device__ constexpr int reg_group_stride() {
   return V == 32 ? p2_group_stride<TT>() : v16_group_stride<TT>();
 }
+// tw2: the [k1][t] table of the sub-length (V = 32) or the [k1][q] table of
+// fft_v16 (V = 16); twab: fft_v16's [a][c] table; tw3: the [r][k2] table of
+// the radix-R combine (R > 1, both V).
 template <typename T, int V, int TT, int R, int SIGN>
 __device__ __forceinline__ void fft_reg(cx<T> (&v)[V], bool active, cx<T> *tile, int q, unsigned gm, int bar, int gr,
-                                        const cx<T> *__restrict__ tw2, const cx<T> *__restrict__ tw3, cx<T> *E) {
+                                        const cx<T> *__restrict__ tw2, const cx<T> *__restrict__ tw3,
+                                        const cx<T> *__restrict__ twab, cx<T> *E) {
   if constexpr (V == 32) {
     fft_mixed<T, TT, R, SIGN>(v, active, tile, q, gm, gr, tw2, tw3, E);
   } else {
-    static_assert(R == 1, "16 values per thread: power-of-two lengths only");
-    if (active) fft_v16<T, TT, SIGN>(v, tile, q, gm, bar, tw2, tw3);
+    if (active) fft_v16<T, TT, SIGN>(v, tile, q, gm, bar, tw2, twab);
+    if constexpr (R > 1) {  // radix-R combine of the R sub-transforms (as in fft_mixed)
+      constexpr int L2 = 16 * TT;
+      __syncthreads();  // E may overlay the transpose tiles of the other groups
+      if (active) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k2 = v16_pos<TT>(q, j);
+          cx<T> w = __ldg(&tw3[gr * L2 + k2]);
+          if (SIGN > 0) w.y = -w.y;
+          E[gr * L2 + k2] = cmul<T>(v[j], w);
+        }
+      }
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k2 = v16_pos<TT>(q, j);
+          cx<T> acc = E[k2];
+#pragma unroll
+          for (int r = 1; r < R; ++r) acc = cadd<T>(acc, cmul<T>(E[r * L2 + k2], root_r<T, R, SIGN>((r * gr) % R)));
+          v[j] = acc;
+        }
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -119,7 +147,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
   T *Ys = reinterpret_cast<T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)C * Rb * RS);  // [C][Rb][N]
   uint32_t *Ms = reinterpret_cast<uint32_t *>(Ys + (size_t)C * Rb * N);              // [C][Rb][N/32]
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *twab = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->twab_row;
 
   griddep_wait();
   if (!init && !adj) {
@@ -149,7 +178,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
       }
     }
   }
-  if (!init) fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Ex);
+  if (!init) fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Ex);
   cp_async_wait_all();
   __syncthreads();
   if (active && adj) {
@@ -216,7 +245,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kerne
   cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)row_id * RS;
   cx<T> *tile = Ex + gr * GS;
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *twab = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->twab_row;
   griddep_wait();
   cx<T> v[V];
   if (active) {
@@ -224,7 +254,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kerne
 #pragma unroll
     for (int m = 0; m < V; ++m) v[m] = mk<T>(yrow[R * (q + TT * m) + gr], T(0));
   }
-  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Ex);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Ex);
   if (active) {
     cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
 #pragma unroll
@@ -270,7 +300,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
   cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)row_id * RS;  // this row's region
   cx<T> *tile = Cs + gr * GS;
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *twab = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->twab_row;
   const unsigned gm = group_mask(TT);
 
   griddep_wait();
@@ -447,7 +478,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(
     // every group of the row has read its inputs before the tiles overwrite them
     if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   }
-  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Cs);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Cs);
   if (active) {
 #pragma unroll
     for (int j = 0; j < V; ++j) Cs[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
@@ -514,7 +545,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   cx<T> *Ex = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)C * Rb * N +
               (size_t)row_id * N;
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_row : Dp->twab_row);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
+  const cx<T> *twab = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->twab_row;
 
   griddep_wait();
   for (int c = 0; c < C; ++c) {
@@ -595,7 +627,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   if (R > 1) __syncthreads();  // every group has read its inputs before outputs overwrite Cs
   cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
   const unsigned gm = group_mask(TT);
-  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, Ex);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Ex);
   if (active) {
 #pragma unroll
     for (int j = 0; j < V; ++j) Cs[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
@@ -642,7 +674,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
   const int ch = local / Dp->col_tiles, t = local - ch * Dp->col_tiles;
   const int k20 = t * Dp->W, w = min(Dp->W, Nh - k20);
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_col : Dp->tw16_col);
-  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw3_col : Dp->twab_col);
+  const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_col;
+  const cx<T> *twab = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->twab_col;
   const cx<T> *__restrict__ H = reinterpret_cast<const cx<T> *>(a.hhat) + Dp->hhat;
   const T *s2c = a.s2 + Dp->s2_col, *s2r = a.s2 + Dp->s2_row;
   cx<T> *St = reinterpret_cast<cx<T> *>(smem_raw);                  // [2W][SR]
@@ -681,7 +714,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     for (int m = 0; m < V; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
-  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, col);
+  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, col);
   if (active) {
 #pragma unroll
     for (int j = 0; j < V; ++j) col[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
@@ -735,7 +768,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel
     for (int m = 0; m < V; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
-  fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, col);
+  fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, col);
   if (active) {
 #pragma unroll
     for (int j = 0; j < V; ++j) col[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];

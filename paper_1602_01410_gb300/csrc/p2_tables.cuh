@@ -40,7 +40,14 @@ static const void *p2_row_tt(int tt, int v, int half, int stage) {
       case 32: return p2_row_one<T, 32, C, R, 32>(half, stage);
     }
   } else {
-    if (v != 32) return nullptr;
+    if (v == 16) {
+      switch (tt) {
+        case 8: return p2_row_one<T, 8, C, R, 16>(half, stage);
+        case 16: return p2_row_one<T, 16, C, R, 16>(half, stage);
+        case 32: return p2_row_one<T, 32, C, R, 16>(half, stage);
+      }
+      return nullptr;
+    }
     switch (tt) {
       case 4: return p2_row_one<T, 4, C, R, 32>(half, stage);
       case 8: return p2_row_one<T, 8, C, R, 32>(half, stage);
@@ -74,7 +81,14 @@ template <typename T, int R, bool EXT> static const void *p2_col_tt(int tt, int 
       case 32: return (const void *)col_pass_p2_kernel<T, 32, R, EXT, 32>;
     }
   } else {
-    if (v != 32) return nullptr;
+    if (v == 16) {
+      switch (tt) {
+        case 8: return (const void *)col_pass_p2_kernel<T, 8, R, EXT, 16>;
+        case 16: return (const void *)col_pass_p2_kernel<T, 16, R, EXT, 16>;
+        case 32: return (const void *)col_pass_p2_kernel<T, 32, R, EXT, 16>;
+      }
+      return nullptr;
+    }
     switch (tt) {
       case 4: return (const void *)col_pass_p2_kernel<T, 4, R, EXT, 32>;
       case 8: return (const void *)col_pass_p2_kernel<T, 8, R, EXT, 32>;

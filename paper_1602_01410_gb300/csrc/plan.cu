@@ -93,7 +93,12 @@ bool reg_fft_params(int L, int *tt, int *r, int *v = nullptr, int vpref = 32) {
     if (L % rr == 0) {
       const int L2 = L / rr;
       if (L2 >= 128 && L2 <= 512 && (L2 & (L2 - 1)) == 0) {
-        *tt = L2 / 32;
+        if (v && vpref == 16) {
+          *v = 16;
+          *tt = L2 / 16;
+        } else {
+          *tt = L2 / 32;
+        }
         *r = rr;
         return true;
       }
@@ -214,10 +219,10 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
   std::map<int, long long> p2_rows, p2_cols;
   // Values per thread of the power-of-two register transforms: 16 (twice the
   // threads, so twice the resident warps) unless the tuning asks for 32.
-  // Defaults: rows of one channel 16 (their parallelism is the row count),
-  // three channels and columns 32 (measured on GB300).
-  const int vrow = (tune && tune->fft_values > 0) ? tune->fft_values : env_int("DECONV_FFT_VALUES", L.C == 1 ? 16 : 32);
-  const int vcol = (tune && tune->col_fft_values > 0) ? tune->col_fft_values : env_int("DECONV_COL_FFT_VALUES", 32);
+  // Defaults (measured on GB300): rows 16; columns 32 for power-of-two
+  // lengths, 16 for 3 * 2^k and 5 * 2^k.
+  const int vrow = (tune && tune->fft_values > 0) ? tune->fft_values : env_int("DECONV_FFT_VALUES", 16);
+  const int vcol_set = (tune && tune->col_fft_values > 0) ? tune->col_fft_values : env_int("DECONV_COL_FFT_VALUES", 0);
   for (int j = 0; j < L.B; ++j) {
     const int M = d->rows[j], N = d->cols[j];
     int tt, r, v;
@@ -228,6 +233,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     } else {
       g_rows += M;
     }
+    const int vcol = vcol_set ? vcol_set : (is_pow2_32(M) ? 32 : 16);
     if (allow_p2 && reg_fft_params(M, &tt, &r, &v, vcol) && p2_col_threads(1, tt, r) <= maxthr &&
         p2_col_smem(M, 1, tt, L.esz, r, v) <= kMaxSmem) {
       col_key[j] = p2_key(v, tt, r);
@@ -406,8 +412,9 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     D.tw2_row = D.tw2_col = D.tw3_row = D.tw3_col = -1;
     D.tw16_row = D.tw16_col = D.twab_row = D.twab_col = -1;
     for (int pass = 0; pass < 2; ++pass) {
-      const int len = pass ? D.M : D.N;
-      if (!is_pow2_32(len)) continue;
+      int tt0, r0;
+      if (!reg_fft_params(pass ? D.M : D.N, &tt0, &r0)) continue;
+      const int len = 32 * tt0;  // the power-of-two (sub-)length
       // 16 values per thread: [k1][q] table (key len + 2^20), and for L/16 > 16
       // the [a][c] table of the L/16-point stage (key len + 2^21)
       const int k16 = len + (1 << 20), kab = len + (1 << 21), tt16 = len / 16;
