@@ -4,25 +4,35 @@
 namespace dcv {
 
 template <typename T, int C>
-static const void *adj_ptr_c(int tt) {
-  switch (tt) {
-    case 2: return (const void *)row_adj_p2_kernel<T, 2, C>;
-    case 4: return (const void *)row_adj_p2_kernel<T, 4, C>;
-    case 8: return (const void *)row_adj_p2_kernel<T, 8, C>;
-    case 16: return (const void *)row_adj_p2_kernel<T, 16, C>;
-    case 32: return (const void *)row_adj_p2_kernel<T, 32, C>;
+static const void *adj_ptr_c(int N, int v) {
+  if (v == 16) {
+    switch (N / 16) {
+      case 4: return (const void *)row_adj_p2_kernel<T, 4, C, 16>;
+      case 8: return (const void *)row_adj_p2_kernel<T, 8, C, 16>;
+      case 16: return (const void *)row_adj_p2_kernel<T, 16, C, 16>;
+      case 32: return (const void *)row_adj_p2_kernel<T, 32, C, 16>;
+      case 64: return (const void *)row_adj_p2_kernel<T, 64, C, 16>;
+    }
+    return nullptr;
+  }
+  switch (N / 32) {
+    case 2: return (const void *)row_adj_p2_kernel<T, 2, C, 32>;
+    case 4: return (const void *)row_adj_p2_kernel<T, 4, C, 32>;
+    case 8: return (const void *)row_adj_p2_kernel<T, 8, C, 32>;
+    case 16: return (const void *)row_adj_p2_kernel<T, 16, C, 32>;
+    case 32: return (const void *)row_adj_p2_kernel<T, 32, C, 32>;
   }
   return nullptr;
 }
 
 template <typename T>
-static const void *adj_ptr(int tt, int C) {
-  return C == 3 ? adj_ptr_c<T, 3>(tt) : adj_ptr_c<T, 1>(tt);
+static const void *adj_ptr(int N, int v, int C) {
+  return C == 3 ? adj_ptr_c<T, 3>(N, v) : adj_ptr_c<T, 1>(N, v);
 }
 
 template <typename T>
-cudaError_t launch_adj(const AdjArgs<T> &a, int tt, int C, int grid, int nt, size_t smem, cudaStream_t s) {
-  const void *fn = adj_ptr<T>(tt, C);
+cudaError_t launch_adj(const AdjArgs<T> &a, int N, int v, int C, int grid, int nt, size_t smem, cudaStream_t s) {
+  const void *fn = adj_ptr<T>(N, v, C);
   if (!fn) return cudaErrorInvalidValue;
   if (grid <= 0) return cudaSuccess;
   void *args[] = {const_cast<AdjArgs<T> *>(&a)};
@@ -30,8 +40,8 @@ cudaError_t launch_adj(const AdjArgs<T> &a, int tt, int C, int grid, int nt, siz
 }
 
 template <typename T>
-cudaError_t prepare_adj(int tt, int C, size_t smem) {
-  const void *fn = adj_ptr<T>(tt, C);
+cudaError_t prepare_adj(int N, int v, int C, size_t smem) {
+  const void *fn = adj_ptr<T>(N, v, C);
   if (!fn) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -68,8 +78,8 @@ cudaError_t launch_taps(const ImageDesc *desc, int img, int M, int N, int C, int
 }
 
 #define INST(T)                                                                                                 \
-  template cudaError_t launch_adj<T>(const AdjArgs<T> &, int, int, int, int, size_t, cudaStream_t);           \
-  template cudaError_t prepare_adj<T>(int, int, size_t);                                                       \
+  template cudaError_t launch_adj<T>(const AdjArgs<T> &, int, int, int, int, int, size_t, cudaStream_t);      \
+  template cudaError_t prepare_adj<T>(int, int, int, size_t);                                                  \
   template cudaError_t launch_sqerr<T>(const T *, const T *, long long, double *, int, cudaStream_t);          \
   template cudaError_t launch_taps<T>(const ImageDesc *, int, int, int, int, int, const void *, double *, void *, \
                                       int, cudaStream_t);

@@ -31,10 +31,11 @@ __device__ __forceinline__ int find_adj(const ImageDesc *desc, const int *imgs, 
   return imgs[lo];
 }
 
-template <typename T, int TT, int C>
+// V complex values per thread (32: fft_p2, 16: fft_v16), TT = N / V threads per row.
+template <typename T, int TT, int C, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(AdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = p2_group_stride<TT>();
+  constexpr int GS = reg_group_stride<V, TT>();
   const int wi = blockIdx.x;
   const int img = find_adj<T>(a.desc, a.cls_imgs, a.adj_begin, a.nimg, wi);
   const ImageDesc *Dp = &a.desc[img];
@@ -43,6 +44,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
   const int r0 = blk * Rb, nr = min(Rb, M - r0);
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
+  const int bar = 1 + g;  // named barrier of a 64-thread group (group_bar)
   const int ch = g / Rb, hh = g - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
   if (active) {
     const long long rowp = px0 + ch * P + (long long)i * N;
     const uint32_t *mrow = a.mask + Dp->mask + ch * Dp->mask_plane + (long long)i * (N / 32);
-    for (int m = 0; m < 32; ++m) {
+    for (int m = 0; m < V; ++m) {
       const int p = q + TT * m;
       const int pm = (p == 0) ? N - 1 : p - 1;
       const T yb = start ? T(0) : a.ybar[rowp + p];
@@ -148,15 +150,19 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
   }
   __syncthreads();  // tiles below reuse the staged rows
   if (active) {
-    cx<T> v[32];
+    cx<T> v[V];
 #pragma unroll
-    for (int m = 0; m < 32; ++m) v[m] = Cs[q + TT * m];
+    for (int m = 0; m < V; ++m) v[m] = Cs[q + TT * m];
     cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
     const unsigned gm = group_mask(TT);
-    fft_p2<T, TT, -1>(v, tile, q, gm, reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw2_row);
+    const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw2);
+    if constexpr (V == 32)
+      fft_p2<T, TT, -1>(v, tile, q, gm, tw + Dp->tw2_row);
+    else
+      fft_v16<T, TT, -1>(v, tile, q, gm, bar, tw + Dp->tw16_row, tw + Dp->twab_row);
 #pragma unroll
-    for (int r = 0; r < 32; ++r) tile[q + TT * p2_slot<TT>(r)] = v[r];
-    __syncwarp(gm);
+    for (int r = 0; r < V; ++r) tile[reg_pos<V, TT>(q, r)] = v[r];
+    group_bar<TT>(gm, bar);
     cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
     for (int k = q; k < Nh; k += TT) {
       const cx<T> c1 = tile[k], c2 = tile[k == 0 ? 0 : N - k];

@@ -148,10 +148,11 @@ template <typename T> struct AdjArgs {
 };
 
 
+// Reverse-pass row kernel for rows of length N with v complex values per thread (16 or 32).
 template <typename T>
-cudaError_t launch_adj(const AdjArgs<T> &a, int tt, int C, int grid, int nt, size_t smem, cudaStream_t s);
+cudaError_t launch_adj(const AdjArgs<T> &a, int N, int v, int C, int grid, int nt, size_t smem, cudaStream_t s);
 template <typename T>
-cudaError_t prepare_adj(int tt, int C, size_t smem);
+cudaError_t prepare_adj(int N, int v, int C, size_t smem);
 template <typename T>
 cudaError_t launch_row_half(const RowArgs<T> &a, const LaunchCfg &c, int half, cudaStream_t s);
 template <typename T>

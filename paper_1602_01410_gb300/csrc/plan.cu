@@ -1003,6 +1003,7 @@ namespace {
 // Reverse-pass workspace (caller-owned, separate from the plan workspace).
 struct GradLayout {
   int k = 1, nck = 0, items = 0;
+  int v = 16;                         // values per thread of the adjoint row kernel
   std::vector<int> rb, grid, nt;      // per row class
   std::vector<size_t> smem;
   std::vector<int> adj_begin;         // per image
@@ -1012,10 +1013,10 @@ struct GradLayout {
 
 constexpr int kLossBlocks = 256;
 
-size_t adj_smem(int C, int N, int rb, int tt, size_t esz) {
+size_t adj_smem(int C, int N, int rb, int tt, size_t esz, int v = 32) {
   const size_t staged = (size_t)C * (2 * (rb + 2) + 4 * (rb + 1)) * N * esz;
   const int groups = p2_row_threads(C, rb, tt) / tt;
-  const size_t tiles = (size_t)groups * p2_group_stride_h(tt) * 2 * esz;
+  const size_t tiles = (size_t)groups * p2_group_stride_hv(tt, v) * 2 * esz;
   return std::max(staged, tiles) + (size_t)groups * N * 2 * esz;
 }
 
@@ -1026,6 +1027,7 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
   for (const auto *v : {&L.row_cls, &L.col_cls})
     for (const Cls &c : *v)
       if (c.cfg.kind != KIND_P2 || c.cfg.r != 1) return DECONV_EUNSUPPORTED;  // reverse pass: powers of two only
+  G->v = env_int("DECONV_ADJ_VALUES", 16) == 32 ? 32 : 16;
   G->k = std::min(k, iters);
   G->nck = (iters + G->k - 1) / G->k;
   const int maxthr = L.esz == 4 ? 512 : 256;
@@ -1033,10 +1035,12 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
   G->items = 0;
   for (const Cls &c : L.row_cls) {
     const ImageDesc &D0 = L.desc[c.imgs[0]];
-    const int tt = D0.N / 32;  // the adjoint row kernel holds 32 values per thread
+    const int v = G->v, tt = D0.N / v;  // the adjoint row kernel: v values per thread
     int rb = D0.Rb;
-    while (rb > 1 && (adj_smem(L.C, D0.N, rb, tt, L.esz) > kMaxSmem || p2_row_threads(L.C, rb, tt) > maxthr)) --rb;
-    if (adj_smem(L.C, D0.N, rb, tt, L.esz) > kMaxSmem) return DECONV_EUNSUPPORTED;
+    while (rb > 1 && (adj_smem(L.C, D0.N, rb, tt, L.esz, v) > kMaxSmem || p2_row_threads(L.C, rb, tt) > maxthr ||
+                      !p2_groups_ok(p2_row_threads(L.C, rb, tt), tt)))
+      --rb;
+    if (adj_smem(L.C, D0.N, rb, tt, L.esz, v) > kMaxSmem) return DECONV_EUNSUPPORTED;
     int grid = 0;
     for (int j : c.imgs) {
       G->adj_begin[j] = grid;
@@ -1045,7 +1049,7 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
     G->rb.push_back(rb);
     G->grid.push_back(grid);
     G->nt.push_back(p2_row_threads(L.C, rb, tt));
-    G->smem.push_back(adj_smem(L.C, D0.N, rb, tt, L.esz));
+    G->smem.push_back(adj_smem(L.C, D0.N, rb, tt, L.esz, v));
     G->items = std::max(G->items, grid);
   }
   const size_t px = L.total_px * L.esz, spec = L.total_spec * 4 * L.esz;
@@ -1094,7 +1098,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
   CK(cudaMemcpyAsync(at(G.o_adjbeg), G.adj_begin.data(), G.adj_begin.size() * sizeof(int), cudaMemcpyHostToDevice,
                      s));
   for (size_t c = 0; c < L.row_cls.size(); ++c)
-    CK(prepare_adj<T>(L.desc[L.row_cls[c].imgs[0]].N / 32, L.C, G.smem[c]));
+    CK(prepare_adj<T>(L.desc[L.row_cls[c].imgs[0]].N, G.v, L.C, G.smem[c]));
 
   // 1. Forward with checkpoints of (y~, d, forward spectrum) every k iterations.
   st = init_state<T>(p, static_cast<const T *>(y), nullptr);
@@ -1180,7 +1184,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
         aa.relax = (T)p->relax;
         aa.lscale = (T)(2.0 / (double)npx);
         aa.tpart = reinterpret_cast<double *>(at(G.o_tpart)) + ci * G.items;
-        CK(launch_adj<T>(aa, L.desc[cl.imgs[0]].N / 32, L.C, G.grid[ci], G.nt[ci], G.smem[ci], s));
+        CK(launch_adj<T>(aa, L.desc[cl.imgs[0]].N, G.v, L.C, G.grid[ci], G.nt[ci], G.smem[ci], s));
       }
       cur ^= 1;
       // taub of this step (all classes; unused partial slots stay zero) into res[1], fixed order.
