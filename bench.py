@@ -487,7 +487,10 @@ def main():
                      "peak_kind": peak_kind,
                      "ms_per_launch": ms_dom, "bytes_per_px": per_px[dom],
                      "other_pass_ms": ms_col if dom == "row" else ms_row,
-                     "algorithmic_bytes_per_px_iter": algorithmic_bytes_per_px(f_unobs, esz)},
+                     "algorithmic_bytes_per_px_iter": algorithmic_bytes_per_px(f_unobs, esz),
+                     # whole step: the method's own bytes per pixel and iteration at the measured rate
+                     "step_achieved_gbs": value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world,
+                     "step_frac": value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world / peak},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
