@@ -316,7 +316,7 @@ def main():
                     help="override the workload's iteration count (profiling runs; recorded in config)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch tuning (the autotuner runs at plan set-up, outside the timing)")
-    ap.add_argument("--tune-iters", type=int, default=20)
+    ap.add_argument("--tune-iters", type=int, default=30)
     ap.add_argument("--images", type=str, default="",
                     help="comma-separated image indices of the batch to keep (small profiling cases)")
     ap.add_argument("--timed-only", action="store_true",

@@ -163,8 +163,9 @@ typedef struct {
 deconv_status deconv_retune(deconv_plan plan, const deconv_tune *t);
 deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
 
-/* Autotuner: times trial_iters iterations (after a fresh solve of y that
- * builds the CUDA graph; the plan's options apply) under the default tuning
+/* Autotuner: times trial_iters iterations three times (after a fresh solve
+ * of y that builds the CUDA graph; the plan's options apply; the fastest
+ * repetition counts) under the default tuning
  * and each candidate (row_ctas and col_ctas in {152, 608}, fft_values and
  * col_fft_values in {16, 32}, and for one channel row_stage in {0, 1}), keeps
  * the fastest

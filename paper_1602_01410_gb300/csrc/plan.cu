@@ -1344,10 +1344,10 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   deconv_status st = DECONV_OK;
   for (const deconv_tune &t : cands) {
     if (deconv_retune(p, &t) != DECONV_OK) continue;  // a tuning this plan cannot take
-    // fresh solve (builds the CUDA graph), then two timed warm continuations
+    // fresh solve (builds the CUDA graph), then three timed warm continuations (fastest kept)
     st = f32 ? solve_t<float>(p, y, nullptr, trial_iters, 0, nullptr) : solve_t<double>(p, y, nullptr, trial_iters, 0, nullptr);
     float ms = -1.f;
-    for (int rep = 0; rep < 2 && st == DECONV_OK; ++rep) {
+    for (int rep = 0; rep < 3 && st == DECONV_OK; ++rep) {
       if (cudaEventRecord(e0, p->stream) != cudaSuccess) st = DECONV_ECUDA;
       if (st == DECONV_OK)
         st = f32 ? solve_t<float>(p, nullptr, nullptr, trial_iters, 1, nullptr)
