@@ -77,6 +77,12 @@ typedef struct {
   int32_t kernel_per_image;
   int32_t dtype; /* DECONV_F32 or DECONV_F64 */
   float relax;
+  /* Uneven kernel supports in one batch: NULL, or host[batch], the odd
+   * support 2b_j+1 <= ksize of image j's kernel (kernel_per_image must be 1).
+   * h still holds ksize x ksize taps per image, image j's kernel centred in
+   * them and zero outside its support (the blur is unchanged by the zero
+   * taps); b_j sets image j's boundary band for the initial fill (Sec. III-B). */
+  const int32_t *ksizes;
 } deconv_dims;
 
 /* Bytes of device workspace a plan for `dims` needs (under any tuning the

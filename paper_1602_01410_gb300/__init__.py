@@ -45,7 +45,8 @@ class deconv_dims(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("rows", ctypes.POINTER(ctypes.c_int32)), ("cols", ctypes.POINTER(ctypes.c_int32)),
                 ("ksize", ctypes.c_int32), ("kernel_per_image", ctypes.c_int32),
-                ("dtype", ctypes.c_int32), ("relax", ctypes.c_float)]
+                ("dtype", ctypes.c_int32), ("relax", ctypes.c_float),
+                ("ksizes", ctypes.POINTER(ctypes.c_int32))]
 
 
 class deconv_options(ctypes.Structure):
@@ -103,12 +104,16 @@ def load() -> ctypes.CDLL:
 
 
 def make_dims(rows: Sequence[int], cols: Sequence[int], ksize: int, channels: int = 1,
-              dtype: int = DECONV_F32, relax: float = 2.0, kernel_per_image: int = 0):
-    """Build a deconv_dims; returns (dims, keepalive) - keep both referenced."""
+              dtype: int = DECONV_F32, relax: float = 2.0, kernel_per_image: int = 0,
+              ksizes: Optional[Sequence[int]] = None):
+    """Build a deconv_dims; returns (dims, keepalive) - keep both referenced.
+    ksizes: per-image kernel supports (uneven supports in one batch)."""
     r = (ctypes.c_int32 * len(rows))(*rows)
     c = (ctypes.c_int32 * len(cols))(*cols)
-    d = deconv_dims(len(rows), channels, r, c, ksize, kernel_per_image, dtype, relax)
-    return d, (r, c)
+    k = (ctypes.c_int32 * len(ksizes))(*ksizes) if ksizes is not None else None
+    d = deconv_dims(len(rows), channels, r, c, ksize, kernel_per_image, dtype, relax,
+                    k if k is not None else ctypes.POINTER(ctypes.c_int32)())
+    return d, (r, c, k)
 
 
 def _check(status: int, where: str) -> None:
@@ -287,7 +292,7 @@ class Plan:
     with the right number of elements)."""
 
     def __init__(self, shapes, h, mask, lam: float, mu: float, channels: int = 1, relax: float = 2.0,
-                 stream=None):
+                 stream=None, ksizes=None):
         import torch
         self._torch = torch
         self.dtype = h.dtype
@@ -297,7 +302,7 @@ class Plan:
         self.shapes = [tuple(s) for s in shapes]
         self.channels = channels
         self.dims, self._keep = make_dims([s[0] for s in shapes], [s[1] for s in shapes], K, channels, dt,
-                                          relax, kpi)
+                                          relax, kpi, ksizes)
         self.workspace_bytes = deconv_workspace_size(self.dims)
         dev = h.device
         self.workspace = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=dev)

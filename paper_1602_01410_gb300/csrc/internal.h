@@ -13,6 +13,7 @@ namespace dcv {
 // array they index (see Plan in plan.cu for the arrays).
 struct ImageDesc {
   int M, N, Nh, C;       // extended rows, cols, N/2+1, channels
+  int kb;                // half support b of the image's kernel (boundary band of the initial fill)
   int Rb;                // rows owned by one row-pass CTA
   int W;                 // spectral columns (k2) per column-pass CTA
   int row_blocks;        // ceil(M / Rb)

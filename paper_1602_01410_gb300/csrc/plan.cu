@@ -192,6 +192,11 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
   if (d->dtype != DECONV_F32 && d->dtype != DECONV_F64) return DECONV_EINVAL;
   if (!(d->relax >= 1.0f && d->relax <= 2.0f)) return DECONV_EINVAL;
   if (d->kernel_per_image != 0 && d->kernel_per_image != 1) return DECONV_EINVAL;
+  if (d->ksizes) {
+    if (!d->kernel_per_image) return DECONV_EINVAL;
+    for (int j = 0; j < d->batch; ++j)
+      if (d->ksizes[j] < 1 || d->ksizes[j] % 2 == 0 || d->ksizes[j] > d->ksize) return DECONV_EINVAL;
+  }
   Layout &L = *Lo;
   L.B = d->batch;
   L.C = d->channels;
@@ -330,6 +335,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     D.N = d->cols[j];
     D.Nh = D.N / 2 + 1;
     D.C = L.C;
+    D.kb = (d->ksizes ? d->ksizes[j] : d->ksize) / 2;
     int grb = 0, gw = 0;
     if (!(row_key[j] && col_key[j])) fit_image(D.M, D.N, L.C, L.nt, L.esz, rb_pref, w_pref, &grb, &gw);
     D.Rb = row_key[j] ? p2_rb[row_key[j]] : grb;
@@ -521,7 +527,7 @@ struct deconv_plan_s {
   bool adapt_ready = false;
   // Creation arguments kept for re-tuning (deconv_retune / deconv_autotune).
   deconv_dims dims{};
-  std::vector<int32_t> rows, cols;
+  std::vector<int32_t> rows, cols, ksizes;
   size_t ws_bytes = 0;
   deconv_tune tune{0, 0, -1, 0};  // the per-image penalties and v were set by a fresh solve
   cudaGraphExec_t gexec = nullptr;
@@ -1284,6 +1290,10 @@ deconv_status deconv_plan_create(deconv_plan *out, const deconv_dims *dims, cons
   p->cols.assign(dims->cols, dims->cols + dims->batch);
   p->dims.rows = p->rows.data();
   p->dims.cols = p->cols.data();
+  if (dims->ksizes) {
+    p->ksizes.assign(dims->ksizes, dims->ksizes + dims->batch);
+    p->dims.ksizes = p->ksizes.data();
+  }
   p->lambda = lambda;
   p->mu = mu;
   p->relax = dims->relax;

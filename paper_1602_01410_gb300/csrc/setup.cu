@@ -177,7 +177,7 @@ __global__ void init_fill_kernel(const ImageDesc *desc, int nimg, const long lon
     if (y != yt) yt[e] = y[e];
     return;
   }
-  const int b = K / 2;
+  const int b = D.kb;  // the image's own half support (K / 2 unless supports differ)
   T v = (T)means[(long long)lo * D.C + ch];  // every image of a plan has the same channel count
   const bool band = i < b || i >= D.M - b || j < b || j >= D.N - b;
   if (band) {

@@ -212,3 +212,42 @@ def test_autotune_picks_a_candidate_and_keeps_parity():
     from gpu_helpers import split
     for a, b in zip(split(x.double().cpu().numpy(), prob), xo):
         assert rel_l2([a], [b]) <= 3e-5
+
+
+# ------------------------------------------------- uneven kernel supports ---
+
+def test_uneven_kernel_supports_in_one_batch():
+    # images blurred by 3x3, 7x7 and 11x11 kernels in one plan: the kernels
+    # are zero-padded to 11x11, each image keeps its own boundary band
+    import dataclasses
+    import torch
+    import paper_1602_01410_gb300 as pkg
+    from gpu_helpers import split
+    import oracle
+    parts = [inputs.random_problem(81 + k, [s], k, mask_kind="random", frac=0.3, iters=1)
+             for k, s in ((3, (96, 128)), (7, (128, 256)), (11, (384, 384)))]
+    K = 11
+    hs = []
+    for pr in parts:
+        k = pr.ksize
+        pad = (K - k) // 2
+        hs.append(np.pad(pr.h, pad))
+    dev = torch.device("cuda:0")
+    shapes = [pr.shapes[0] for pr in parts]
+    h = torch.tensor(np.stack(hs), dtype=torch.float32, device=dev)
+    mask = torch.tensor(np.concatenate([pr.mask[0].ravel() for pr in parts]), dtype=torch.uint8, device=dev)
+    y = torch.tensor(np.concatenate([pr.y[0].ravel() for pr in parts]), dtype=torch.float32, device=dev)
+    plan = pkg.Plan(shapes, h, mask, parts[0].lam, parts[0].mu, ksizes=[pr.ksize for pr in parts])
+    merged = dataclasses.replace(parts[0], y=[pr.y[0] for pr in parts], mask=[pr.mask[0] for pr in parts],
+                                 x_true=[pr.x_true[0] for pr in parts])
+    for iters, tol in ((0, 0.0), (1, 1e-5), (10, 1e-4)):
+        x = plan.solve(y, iters)
+        assert plan.sync() == 0
+        xg = split(x.double().cpu().numpy(), merged)
+        for j, pr in enumerate(parts):
+            if iters == 0:
+                want = oracle.init_ytilde(pr.y[0][0], pr.mask[0][0], pr.ksize, round_f32=True)
+                assert np.array_equal(xg[j][0], want.astype(np.float32).astype(np.float64))
+            else:
+                xo, _, _ = oracle.admm(pr.y[0], pr.mask[0], pr.h, pr.lam, pr.mu, iters, relax=pr.relax)
+                assert rel_l2([xg[j]], [xo]) <= tol

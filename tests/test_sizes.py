@@ -60,3 +60,13 @@ def test_enlarge_and_crop():
     assert np.array_equal(pkg.crop(y2, (13, 17)), y) and np.array_equal(pkg.crop(m2, (13, 17)), m)
     assert not m2[:, 13:, :].any() and not m2[:, :, 17:].any()
     assert not y2[:, 13:, :].any() and not y2[:, :, 17:].any()
+
+
+def test_uneven_kernel_supports_validated():
+    ok, _ = pkg.make_dims([32, 40], [32, 48], 9, kernel_per_image=1, ksizes=[9, 5])
+    assert pkg.deconv_workspace_size(ok) > 0
+    for kpi, ks in ((1, [9, 4]), (1, [11, 5]), (0, [9, 5]), (1, [9, 0])):
+        d, _ = pkg.make_dims([32, 40], [32, 48], 9, kernel_per_image=kpi, ksizes=ks)
+        with pytest.raises(pkg.DeconvError) as e:
+            pkg.deconv_workspace_size(d)
+        assert e.value.status == pkg.DECONV_EINVAL
