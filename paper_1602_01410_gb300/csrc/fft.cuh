@@ -1,4 +1,7 @@
-// Shared-memory mixed-radix FFT used by the row and column passes.
+// FFTs of the row and column passes: register-resident transforms (fft_p2,
+// fft_mixed, fft_v16, further below) for lengths 2^k, 3 * 2^k and 5 * 2^k,
+// and a shared-memory mixed-radix Stockham transform for any other
+// 2^a 3^b 5^c length (first part of this file).
 //
 // The 2-D DFT that diagonalises T~^T T~ + mu D^T D (Sec. II-B, the paragraph
 // after the over-relaxed z-update) is computed as 1-D transforms along rows

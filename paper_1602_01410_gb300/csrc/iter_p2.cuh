@@ -1,15 +1,18 @@
-// Row and column passes for power-of-two lengths L = 32 TT (64 .. 1024),
-// built on the register-resident transform fft_p2 (fft.cuh).  Same
-// arithmetic as the generic passes in iter_kernels.cuh (see the comment
-// there for the iteration), different work decomposition:
+// Row and column passes for the register-transform lengths L = R V TT
+// (R in {1, 3, 5}; V = 32 values per thread with fft_p2 / fft_mixed, or
+// V = 16 with fft_v16; see fft.cuh).  Same arithmetic as the generic passes
+// in iter_kernels.cuh (see the comment there for the iteration), different
+// work decomposition:
 //
-//   row pass:    one group of TT threads per (channel, row) of the block,
-//                rows r0-1 .. r1 (halo included); blockDim = C (Rb+2) TT.
-//                Each thread owns the pixels q + TT m of its row, in
-//                registers across the whole pass.
-//   column pass: one group of TT threads per signal (Y or R of one spectral
-//                column); the column tile is staged through shared memory
-//                with coalesced row loads and stores.
+//   row pass:    R groups of TT threads per (channel, row) of the block; each
+//                thread owns the pixels q + TT m (+ L/R of its sub-transform)
+//                of its row, in registers through the transform.  Inverse
+//                half (row_inv_p2_kernel) and forward half (row_fwd_p2_kernel,
+//                or its staged variant) are separate kernels, so the forward
+//                half's stencil sees the x rows of its neighbours.
+//   column pass: R groups per signal (Y or R of one spectral column); the
+//                column tile is staged through shared memory with coalesced
+//                row loads and stores and transformed in place.
 #pragma once
 
 #include "fft.cuh"
