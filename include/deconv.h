@@ -173,7 +173,8 @@ deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
  * of y that builds the CUDA graph; the plan's options apply; the fastest
  * repetition counts) under the default tuning
  * and each candidate (row_ctas and col_ctas in {152, 608}, fft_values and
- * col_fft_values in {16, 32}, and for one channel row_stage in {0, 1}), keeps
+ * col_fft_values in {16, 32}, and for one channel and one row class
+ * row_stage in {0, 1}), keeps
  * the fastest
  * (best, best_ms_per_iter: nullable host outputs) and leaves the plan in it
  * with no iteration state.  y: device, batch layout.  Synchronous. */

@@ -1344,7 +1344,13 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
                               float *best_ms_per_iter) {
   if (!p || !y || trial_iters < 1 || trial_iters > 100000) return DECONV_EINVAL;
   const bool f32 = p->L.dtype == DECONV_F32;
-  std::vector<deconv_tune> cands = tune_candidates(p->L.C);
+  std::vector<deconv_tune> cands;
+  // The staged forward half (188 KB of shared memory per CTA at 1024) keeps
+  // the kernel classes of a batch from running side by side; it is tried for
+  // plans of one row class only.
+  const bool one_class = p->L.row_cls.size() == 1;
+  for (const deconv_tune &t : tune_candidates(p->L.C))
+    if (t.row_stage != 1 || one_class) cands.push_back(t);
   cands.insert(cands.begin(), deconv_tune{0, 0, -1, 0, 0});  // the defaults
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
