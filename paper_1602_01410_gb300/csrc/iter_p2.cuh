@@ -52,12 +52,6 @@ __device__ __forceinline__ void copy_async(E *sdst, const E *gsrc, int n, int ti
   }
 }
 
-// Register r of fft_p2's output holds position q + TT * p2_slot(r); the
-// register holding position q + TT * m is p2_unslot(m).
-template <int TT> __device__ __forceinline__ constexpr int p2_unslot(int m) {
-  return (m % (32 / TT)) * TT + m / (32 / TT);
-}
-
 // Register-transform helpers for V = 32 (fft_p2 / fft_mixed) or V = 16
 // (fft_v16, R = 1) values per thread.
 template <int V, int TT> __device__ __forceinline__ int reg_pos(int q, int j) {
