@@ -11,6 +11,17 @@ tensor and passes torch tensors' data pointers and the current CUDA stream.
 The library must be built first (``paper_1602_01410_gb300.build.build()`` or
 ``__graft_entry__.build()``); importing the functions fails loudly when it is
 missing.  There is no CPU fallback.
+
+Typical use (device tensors; y and mask in the batch layout of deconv.h)::
+
+    plan = Plan([(M, N)], h, mask, lam, mu)          # extended grid M x N, K x K kernel
+    plan.set_options(bgs_passes=K // 2, tikh_iters=100, adapt_t=3.0)   # optional variants
+    plan.autotune(y)                                 # optional: launch shapes for this GPU
+    x = plan.solve(y, iters)                         # x^{iters}
+    loss, dlam, dh = plan.grad(y, x_true, iters)     # gradient of the unrolled solve (defaults only)
+
+For sizes with a prime factor above 5, ``deconv_fast_shape`` and ``enlarge``
+give a supported grid with the added pixels unobserved.
 """
 from __future__ import annotations
 
