@@ -7,7 +7,10 @@ namespace dcv {
 // H^(k1, k2) = sum_{p,q=-b..b} h[p+b][q+b] exp(-2 pi i (k1 p / M + k2 q / N)),
 // the DFT of the kernel placed with its origin at grid index (0, 0) (the
 // eigenvalues of the BCCB matrix T~ of Eq. (4)).  Evaluated directly in
-// double precision with exact integer phase reduction, then rounded once.
+// double precision: the phases of the first tap in each direction are
+// reduced exactly in integers, the following taps' twiddles come from
+// multiplying by exp(-2 pi i k / L) (about (2b+1) ulp of drift in double),
+// then the sum is rounded once.
 template <typename T>
 __global__ void hhat_kernel(const HhatJob *jobs, int njobs, const long long *job_begin, long long total,
                             const T *h, cx<T> *hhat) {
@@ -22,22 +25,32 @@ __global__ void hhat_kernel(const HhatJob *jobs, int njobs, const long long *job
   const long long loc = e - job_begin[lo];
   const int k1 = (int)(loc / J.Nh), k2 = (int)(loc - (long long)k1 * J.Nh);
   const int b = J.K / 2;
+  // exp(-2 pi i k n / L) at n = -b (exact phase) and the step exp(-2 pi i k / L)
+  auto root = [](long long k, long long n, long long L, double *c, double *s) {
+    const long long ph = (((k * n) % L) + L) % L;
+    sincospi(-2.0 * (double)ph / (double)L, s, c);
+  };
+  double cq0, sq0, cqs, sqs, cp, sp, cps, sps;
+  root(k2, -b, J.N, &cq0, &sq0);
+  root(k2, 1, J.N, &cqs, &sqs);
+  root(k1, -b, J.M, &cp, &sp);
+  root(k1, 1, J.M, &cps, &sps);
   double re = 0.0, im = 0.0;
   for (int p = -b; p <= b; ++p) {
-    double rr = 0.0, ri = 0.0;
+    double rr = 0.0, ri = 0.0, c = cq0, s = sq0;
     for (int q = -b; q <= b; ++q) {
-      const long long ph = ((long long)k2 * q) % J.N;
-      double s, c;
-      sincospi(-2.0 * (double)ph / (double)J.N, &s, &c);
       const double hv = (double)h[J.h + (long long)(p + b) * J.K + (q + b)];
       rr += hv * c;
       ri += hv * s;
+      const double cn = c * cqs - s * sqs;
+      s = c * sqs + s * cqs;
+      c = cn;
     }
-    const long long ph = ((long long)k1 * p) % J.M;
-    double s, c;
-    sincospi(-2.0 * (double)ph / (double)J.M, &s, &c);
-    re += rr * c - ri * s;
-    im += rr * s + ri * c;
+    re += rr * cp - ri * sp;
+    im += rr * sp + ri * cp;
+    const double cn = cp * cps - sp * sps;
+    sp = cp * sps + sp * cps;
+    cp = cn;
   }
   hhat[J.out + loc] = mk<T>((T)re, (T)im);
 }
