@@ -171,11 +171,9 @@ deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
 
 /* Autotuner: times trial_iters iterations three times (after a fresh solve
  * of y that builds the CUDA graph; the plan's options apply; the fastest
- * repetition counts) under the default tuning
- * and each candidate (row_ctas and col_ctas in {152, 608}, fft_values and
- * col_fft_values in {16, 32}, and for one channel and one row class
- * row_stage in {0, 1}), keeps
- * the fastest
+ * repetition counts) under the default tuning and each candidate (row_ctas
+ * and col_ctas in {152, 608}, fft_values and col_fft_values in {16, 32}, and
+ * for one channel and one row class row_stage in {0, 1}), keeps the fastest
  * (best, best_ms_per_iter: nullable host outputs) and leaves the plan in it
  * with no iteration state.  y: device, batch layout.  Synchronous. */
 deconv_status deconv_autotune(deconv_plan plan, const void *y, int32_t trial_iters, deconv_tune *best,
@@ -197,8 +195,8 @@ deconv_status deconv_fast_shape(int32_t M, int32_t N, int32_t channels, int32_t 
 /* The penalty mu each image's next iteration uses (mu_host: host, batch
  * doubles).  With adaptation off, or before the first fresh solve after it
  * was switched on, every entry is the plan's mu.  Synchronises the stream.
- * Under adaptation a warm solve (warm = 1) needs a fresh solve first
- * (DECONV_EINVAL otherwise); state blobs do not carry mu or v. */
+ * Under adaptation a warm solve (warm = 1) needs a fresh solve first, or a
+ * state blob saved under adaptation (DECONV_EINVAL otherwise). */
 deconv_status deconv_get_mu(deconv_plan plan, double *mu_host);
 
 /* Same as deconv_solve with warm = 0 and no statistics, but y_host and
@@ -260,10 +258,16 @@ deconv_status deconv_profile_passes(deconv_plan plan, int32_t iters, float *ms_h
  * from one iteration to the next is y~ = [y; z], the scaled dual d_x and the
  * right-hand side of the next x-step).  The state is exported as an opaque
  * device blob of deconv_state_bytes() bytes (caller-owned, 16-byte aligned)
- * holding y~, d_x and the plan's forward row spectra; deconv_state_set
- * restores it into a plan of the same geometry, after which
- * deconv_solve(warm = 1) continues exactly where the saved plan stood.
- * Asynchronous device-to-device copies on the plan's stream. */
+ * holding y~, d_x, the plan's forward row spectra and, for penalty
+ * adaptation (Eq. (varying_penalty)), each image's current and previous mu,
+ * the d rescaling and v_x, with a flag saying whether those were live;
+ * deconv_state_set restores it into a plan of the same geometry, after which
+ * deconv_solve(warm = 1) continues exactly where the saved plan stood (with
+ * adaptation on in the restoring plan, only from a blob saved under
+ * adaptation; otherwise the warm solve returns DECONV_EINVAL).
+ * deconv_state_get queues device-to-device copies on the plan's stream and
+ * writes the flag from host memory (which waits for the stream's earlier
+ * work); deconv_state_set synchronises the stream. */
 deconv_status deconv_state_bytes(deconv_plan plan, size_t *bytes);
 deconv_status deconv_state_get(deconv_plan plan, void *blob);
 deconv_status deconv_state_set(deconv_plan plan, const void *blob);

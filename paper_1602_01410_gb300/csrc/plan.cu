@@ -1467,9 +1467,10 @@ deconv_status deconv_solve_host(deconv_plan p, const void *y_host, void *x_host,
 
 deconv_status deconv_profile_passes(deconv_plan p, int32_t iters, float *ms_host) {
   if (!p || iters < 1 || !ms_host || !p->have_state) return DECONV_EINVAL;
-  std::vector<cudaEvent_t> ev(4 * (size_t)iters);
-  for (auto &e : ev) CK(cudaEventCreate(&e));
+  std::vector<cudaEvent_t> ev(4 * (size_t)iters, nullptr);
   deconv_status st = DECONV_OK;
+  for (auto &e : ev)
+    if (st == DECONV_OK && cudaEventCreate(&e) != cudaSuccess) st = DECONV_ECUDA;
   for (int it = 0; it < iters && st == DECONV_OK; ++it) {
     cudaError_t e = cudaEventRecord(ev[4 * it], p->stream);
     const bool f32 = p->L.dtype == DECONV_F32;
@@ -1495,7 +1496,8 @@ deconv_status deconv_profile_passes(deconv_plan p, int32_t iters, float *ms_host
     col += a;
     row += b;
   }
-  for (auto &e : ev) cudaEventDestroy(e);
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
   if (st != DECONV_OK) return st;
   ms_host[0] = (float)(col / iters);
   ms_host[1] = (float)(row / iters);
@@ -1522,42 +1524,74 @@ deconv_status deconv_plan_destroy(deconv_plan p) {
   return DECONV_OK;
 }
 
-static size_t state_parts(const deconv_plan_s *p, size_t *yt, size_t *d, size_t *sa) {
-  *yt = p->L.total_px * p->L.esz;
-  *d = 2 * *yt;
-  *sa = p->L.total_spec * 4 * p->L.esz;
-  return *yt + *d + *sa;
+// State blob: y~ | d | forward row spectra | per-image mu, mu_prev, d scale |
+// v | flag (int32, padded to 16 bytes).  The penalties and v are the state of
+// penalty adaptation; the flag is 1 when they were live in the saving plan.
+struct StateParts {
+  size_t yt, d, sa, mu, v, total;
+};
+
+static StateParts state_parts(const deconv_plan_s *p) {
+  StateParts s;
+  s.yt = p->L.total_px * p->L.esz;
+  s.d = 2 * s.yt;
+  s.sa = p->L.total_spec * 4 * p->L.esz;
+  s.mu = 3 * (size_t)p->L.B * sizeof(double);
+  s.v = 2 * s.yt;
+  s.total = s.yt + s.d + s.sa + s.mu + s.v + 16;
+  return s;
 }
 
 deconv_status deconv_state_bytes(deconv_plan p, size_t *bytes) {
   if (!p || !bytes) return DECONV_EINVAL;
-  size_t a, b, c;
-  *bytes = state_parts(p, &a, &b, &c);
+  *bytes = state_parts(p).total;
   return DECONV_OK;
 }
 
 deconv_status deconv_state_get(deconv_plan p, void *blob) {
   if (!p || !blob || (reinterpret_cast<uintptr_t>(blob) & 15)) return DECONV_EINVAL;
   if (!p->have_state) return DECONV_EINVAL;
-  size_t a, b, c;
-  state_parts(p, &a, &b, &c);
+  const StateParts s = state_parts(p);
+  const Layout &L = p->L;
   char *o = static_cast<char *>(blob);
-  CK(cudaMemcpyAsync(o, p->ws + p->L.o_yt, a, cudaMemcpyDeviceToDevice, p->stream));
-  CK(cudaMemcpyAsync(o + a, p->ws + (p->parity ? p->L.o_d1 : p->L.o_d0), b, cudaMemcpyDeviceToDevice, p->stream));
-  CK(cudaMemcpyAsync(o + a + b, p->ws + p->L.o_Sa, c, cudaMemcpyDeviceToDevice, p->stream));
+  const int32_t flag[4] = {p->adapt_t > 0.0 && p->adapt_ready ? 1 : 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(o, p->ws + L.o_yt, s.yt, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.yt;
+  CK(cudaMemcpyAsync(o, p->ws + (p->parity ? L.o_d1 : L.o_d0), s.d, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.d;
+  CK(cudaMemcpyAsync(o, p->ws + L.o_Sa, s.sa, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.sa;
+  CK(cudaMemcpyAsync(o, p->ws + L.o_mu, s.mu, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.mu;
+  CK(cudaMemcpyAsync(o, p->ws + L.o_v, s.v, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.v;
+  // From pageable memory: the call returns once the 16 bytes are staged.
+  CK(cudaMemcpyAsync(o, flag, sizeof(flag), cudaMemcpyHostToDevice, p->stream));
   return DECONV_OK;
 }
 
 deconv_status deconv_state_set(deconv_plan p, const void *blob) {
   if (!p || !blob || (reinterpret_cast<uintptr_t>(blob) & 15)) return DECONV_EINVAL;
-  size_t a, b, c;
-  state_parts(p, &a, &b, &c);
+  const StateParts s = state_parts(p);
+  const Layout &L = p->L;
   const char *o = static_cast<const char *>(blob);
-  CK(cudaMemcpyAsync(p->ws + p->L.o_yt, o, a, cudaMemcpyDeviceToDevice, p->stream));
-  CK(cudaMemcpyAsync(p->ws + p->L.o_d0, o + a, b, cudaMemcpyDeviceToDevice, p->stream));
-  CK(cudaMemcpyAsync(p->ws + p->L.o_Sa, o + a + b, c, cudaMemcpyDeviceToDevice, p->stream));
+  int32_t flag[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(p->ws + L.o_yt, o, s.yt, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.yt;
+  CK(cudaMemcpyAsync(p->ws + L.o_d0, o, s.d, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.d;
+  CK(cudaMemcpyAsync(p->ws + L.o_Sa, o, s.sa, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.sa;
+  CK(cudaMemcpyAsync(p->ws + L.o_mu, o, s.mu, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.mu;
+  CK(cudaMemcpyAsync(p->ws + L.o_v, o, s.v, cudaMemcpyDeviceToDevice, p->stream));
+  o += s.v;
+  CK(cudaMemcpyAsync(flag, o, sizeof(flag), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
   p->parity = 0;
   p->have_state = true;
+  // A blob without a live adaptive state leaves a warm solve under adaptation refused.
+  p->adapt_ready = p->adapt_t > 0.0 && flag[0] == 1;
   return DECONV_OK;
 }
 

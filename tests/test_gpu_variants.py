@@ -11,7 +11,7 @@ import pytest
 
 from paper_1602_01410_gb300 import inputs
 
-from gpu_helpers import gpu_solve, oracle_solve, rel_l2
+from gpu_helpers import gpu_solve, oracle_solve, rel_l2, torch_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -138,6 +138,34 @@ def test_adaptive_warm_continuation_needs_a_fresh_solve():
     plan2.set_options(adapt_t=3.0)
     with pytest.raises(pkg.DeconvError) as e:
         plan2.solve(None, 3, warm=True)
+    assert e.value.status == pkg.DECONV_EINVAL
+
+
+def test_adaptive_checkpoint_resumes_in_another_plan():
+    # The blob carries each image's penalties and v: a fresh plan continues
+    # the adapted run bit for bit; a blob saved without adaptation is refused.
+    import paper_1602_01410_gb300 as pkg
+    torch, dev = torch_dev()
+    prob = inputs.random_problem(56, [(64, 64), (48, 60)], 5, mask_kind="random", frac=0.3, iters=9, mu=1.0)
+    full, _, pf = gpu_solve(prob, adapt_t=3.0)
+    _, _, plan = gpu_solve(prob, iters=5, adapt_t=3.0)
+    blob = plan.state_get()
+    h = torch.tensor(prob.h, dtype=torch.float32, device=dev)
+    mask = torch.tensor(np.concatenate([m.ravel() for m in prob.mask]), dtype=torch.uint8, device=dev)
+    plan2 = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu)
+    plan2.set_options(adapt_t=3.0)
+    plan2.state_set(blob)
+    assert plan2.get_mu() == plan.get_mu()
+    x = plan2.solve(None, 4, warm=True)
+    assert plan2.sync() == 0
+    assert np.array_equal(x.double().cpu().numpy(), np.concatenate([a.ravel() for a in full]))
+    assert plan2.get_mu() == pf.get_mu()
+    _, _, plain = gpu_solve(prob, iters=5)
+    plan3 = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu)
+    plan3.set_options(adapt_t=3.0)
+    plan3.state_set(plain.state_get())
+    with pytest.raises(pkg.DeconvError) as e:
+        plan3.solve(None, 2, warm=True)
     assert e.value.status == pkg.DECONV_EINVAL
 
 
