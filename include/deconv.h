@@ -54,7 +54,7 @@ typedef enum {
   DECONV_EUNSUPPORTED = 2, /* a length with a prime factor > 5, or above the largest schedule */
   DECONV_ENOMEM = 3,       /* workspace smaller than deconv_workspace_size() */
   DECONV_ECUDA = 4,        /* a CUDA runtime call failed */
-  DECONV_ETIMEOUT = 5,     /* a bounded device wait expired */
+  DECONV_ETIMEOUT = 5,     /* a bounded device wait expired (reserved: no kernel waits on another) */
   DECONV_ENONFINITE = 6    /* a NaN or Inf reached the iterate */
 } deconv_status;
 
@@ -279,7 +279,11 @@ deconv_status deconv_kernel_launches(deconv_plan plan, int32_t iters, int32_t mo
                                      int64_t *count);
 
 /* Wait for the plan's stream and report device-side errors recorded since
- * the last call (DECONV_ENONFINITE, DECONV_ETIMEOUT), then clear them. */
+ * the last call, then clear them.  DECONV_ENONFINITE: a NaN or Inf reached
+ * the iterate (the kernels flag it and carry on; nothing traps).
+ * DECONV_ETIMEOUT is reserved for a bounded device wait: no kernel of the
+ * library spins on a flag or on another block (launches are ordered by the
+ * stream and programmatic dependent launch), so it is not returned now. */
 deconv_status deconv_sync(deconv_plan plan);
 
 /* Release the plan's host resources (and its cached CUDA graph).  The

@@ -660,8 +660,11 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
 // place (their transpose tiles and exchange buffer are that column's
 // storage).  Shared memory: [2W columns of R tiles (+4 elements of padding,
 // which spreads the staging stores over the banks)][H^ tile M x w][sin^2 tables].
+// FP32 with 16 values per thread: at most 80 registers, so two CTAs of up to
+// 384 threads fit one SM (at 86-94 registers the wide column tiles ran one).
 template <typename T, int TT, int R, bool EXT, int V>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) col_pass_p2_kernel(ColArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((V == 16 && sizeof(T) == 4) ? 80 : 128)
+    col_pass_p2_kernel(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, SR = R * GS + 4;
   const int wi = blockIdx.x;
