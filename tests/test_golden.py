@@ -1,0 +1,82 @@
+"""Pins of the oracle against worked examples derived by hand from the
+paper's definitions (`tests/golden/*.txt`, each file citing the equation or
+section it follows).  None of the stored values comes from the oracle or the
+CUDA path; fractions are written exactly and parsed with `fractions`."""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load(name):
+    """Blocks of a fixture: {block name: list of rows of floats}."""
+    blocks, cur = {}, None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("@"):
+                cur = blocks.setdefault(line[1:], [])
+                continue
+            cur.append([float(Fraction(tok)) for tok in line.split()])
+    return blocks
+
+
+def mat(rows):
+    return np.array(rows, dtype=np.float64)
+
+
+def test_fixtures_present_and_cited():
+    names = sorted(os.listdir(GOLDEN))
+    assert len(names) >= 6
+    for n in names:
+        head = open(os.path.join(GOLDEN, n)).read().split("@", 1)[0]
+        assert "Eq." in head or "Sec." in head, n
+
+
+@pytest.mark.parametrize("case", sorted(load("vsoft_worked.txt")))
+def test_vector_soft_threshold_worked(case):
+    tau, a, v = load("vsoft_worked.txt")[case]
+    got = oracle.vsoft(np.array(a).reshape(-1, 1), tau[0]).ravel()
+    assert np.allclose(got, v, rtol=0, atol=1e-15), (got, v)
+
+
+def test_circular_convolution_and_adjoint_of_an_impulse():
+    g = load("conv_impulse_4x5.txt")
+    h, x = mat(g["h"]), mat(g["x"])
+    assert np.array_equal(oracle.conv_circ(x, h), mat(g["conv"]))
+    assert np.array_equal(oracle.conv_circ_adj(x, h), mat(g["corr"]))
+
+
+def test_valid_convolution_worked():
+    g = load("conv_valid_4x4.txt")
+    assert np.array_equal(oracle.conv_valid(mat(g["x"]), mat(g["h"])), mat(g["valid"]))
+
+
+def test_periodic_differences_and_dtd_worked():
+    g = load("diff_3x4.txt")
+    x = mat(g["x"])
+    dh, dv = oracle.diff_fwd(x)
+    assert np.array_equal(dh, mat(g["dh"]))
+    assert np.array_equal(dv, mat(g["dv"]))
+    assert np.array_equal(oracle.diff_adj(dh, dv), mat(g["dtd"]))
+
+
+def test_x_step_closed_form_on_a_3x3_grid():
+    g = load("xstep_3x3_uniform.txt")
+    x = oracle.solve_x(mat(g["rhs"]), mat(g["h"]), g["mu"][0][0])
+    assert np.allclose(x, mat(g["x"]), rtol=0, atol=1e-14), x
+
+
+@pytest.mark.parametrize("case", ["1", "2"])
+def test_initial_fill_worked(case):
+    g = load("init_fill_5x5.txt")
+    y, m = mat(g["y" + case]), mat(g["mask" + case]).astype(np.uint8)
+    yt = oracle.init_ytilde(y, m, 3, round_f32=False)
+    assert np.allclose(yt, mat(g["yt" + case]), rtol=0, atol=1e-15), yt
