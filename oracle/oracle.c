@@ -16,8 +16,9 @@
  * (naive DFT and numpy.fft for the FFT, scipy convolution for the blurs,
  * adjoint identities, brute-force prox, normal equations, Lemma 3
  * monotonicity, the lambda = 0 closed form and a dense standard-ADMM run).
- * The gradient (reverse pass) is pinned by central finite differences and a
- * dot-product test.
+ * The gradient (reverse pass) is pinned by central finite differences of
+ * the forward oracle: per parameter (lambda and every kernel tap) and along
+ * random directions of (lambda, h), one and three channels, relax 1 and 2.
  */
 #include <complex.h>
 #include <math.h>

@@ -1,6 +1,7 @@
 """Pins of the oracle's reverse pass (the gradient of the unrolled partial
 ADMM) against central finite differences of the oracle's forward pass, for
-lambda and every kernel tap, one and three channels (no GPU)."""
+lambda and every kernel tap and along random directions of (lambda, h), one
+and three channels, relax 1 and 2 (no GPU)."""
 import numpy as np
 import pytest
 
@@ -52,3 +53,22 @@ def test_gradient_zero_iterations_and_lambda_zero():
     eps = 1e-7
     fd = (oracle.loss_only(y, m, h, eps, 2e-2, 4, xt, round_f32=False) - L) / eps  # one-sided at the lambda >= 0 edge
     assert abs(fd - dlam) <= 1e-4 * abs(dlam) + 1e-10
+
+
+@pytest.mark.parametrize("C,relax", [(1, 2.0), (3, 1.0)])
+def test_gradient_along_random_directions(C, relax):
+    # <grad L, (u_lambda, U_h)> against the central difference of L along
+    # random directions of (lambda, h), over a longer unrolled run.
+    y, m, h, xt = problem(C, 60 + C)
+    lam, mu, iters = 2e-3, 3e-2, 15
+    L, dlam, dh, _ = oracle.admm_grad(y, m, h, lam, mu, iters, xt, relax=relax, round_f32=False)
+    rng = np.random.default_rng(9)
+    for _ in range(3):
+        ul = rng.standard_normal() * lam
+        uh = rng.standard_normal(h.shape) * h.std()
+        eps = 1e-6
+        fp = oracle.loss_only(y, m, h + eps * uh, lam + eps * ul, mu, iters, xt, relax=relax, round_f32=False)
+        fm = oracle.loss_only(y, m, h - eps * uh, lam - eps * ul, mu, iters, xt, relax=relax, round_f32=False)
+        fd = (fp - fm) / (2 * eps)
+        an = dlam * ul + float(np.sum(dh * uh))
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-14, (fd, an)
