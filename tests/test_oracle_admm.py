@@ -203,3 +203,21 @@ def test_vectorial_tv_couples_channels():
     x1, _, _ = oracle.admm(y[None], m[None], h, lam / np.sqrt(3.0), mu, 40)
     for c in range(3):
         assert np.max(np.abs(x3[c] - x1[0])) < 1e-12
+
+
+def test_stats_are_the_stated_norms():
+    # Each statistics row is [||d^{i+1} - d^i||^2, ||z^{i+1} - z^i||^2,
+    # mu ||v^{i+1} - v^i||^2, J(x^{i+1})] (the residuals of Eq. (varying_penalty)
+    # and the objective of Eq. (problem_xz) over z), recomputed here from the
+    # states before and after one iteration.
+    x_true, y, m, h, lam, mu = small_problem(21, M=12, N=10, K=3)
+    rng = np.random.default_rng(22)
+    M, N = y.shape
+    st = oracle.State(rng.standard_normal((1, M, N)), rng.standard_normal((1, 2, M, N)),
+                      rng.standard_normal((1, 2, M, N)))
+    st.yt[0][m != 0] = y[m != 0]
+    x1, st1, s = oracle.admm(y[None], m[None], h, lam, mu, 1, state=st, stats=True)
+    assert np.isclose(s[0, 0], np.sum((st1.d - st.d) ** 2), rtol=1e-12)
+    assert np.isclose(s[0, 1], np.sum((st1.yt - st.yt) ** 2), rtol=1e-12)
+    assert np.isclose(s[0, 2], mu * np.sum((st1.v - st.v) ** 2), rtol=1e-12)
+    assert np.isclose(s[0, 3], objective(x1[0], y, m, h, lam), rtol=1e-12)
