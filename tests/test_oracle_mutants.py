@@ -1,8 +1,10 @@
 """The oracle's pins catch plausible mistakes (no GPU).  Each case plants one
 mistake in a copy of oracle/oracle.c: a transposed operand, a wrong
-neighbour index, a dropped term, a flipped sign, a wrong normalisation.  It
-then runs the oracle's pin suites against the mutated copy and expects them
-to fail.  The real oracle is never modified."""
+neighbour index, a dropped term, a flipped sign, a wrong normalisation, in
+the iteration, its variants (BGS passes, Tikhonov warm start, penalty
+adaptation, vectorial TV) and the reverse pass.  It then runs the oracle's
+pin suites against the mutated copy and expects them to fail.  The real
+oracle is never modified."""
 import os
 import shutil
 import subprocess
@@ -36,6 +38,21 @@ MUTANTS = [
     ("dft_conjugated_roots",
      "double a = sign * 2.0 * M_PI * (double)k / (double)L;",
      "double a = -sign * 2.0 * M_PI * (double)k / (double)L;"),
+    ("tv_separate_per_channel",
+     "or_vsoft(a, (int)P, 2 * C, lambda / mu, vn);",
+     "for (int c = 0; c < C; ++c) or_vsoft(a + 2 * c * P, (int)P, 2, lambda / mu, vn + 2 * c * P);"),
+    ("bgs_passes_ignored",
+     "for (int pass = 0; pass < passes; ++pass) {", "for (int pass = 0; pass < 1; ++pass) {"),
+    ("tikhonov_tau_doubled",
+     "for (size_t i = 0; i < P; ++i) s[i] = a[i] + tau * e[i];",
+     "for (size_t i = 0; i < P; ++i) s[i] = a[i] + 2.0 * tau * e[i];"),
+    ("penalty_rule_branches_swapped",
+     "if (nd > adapt_t * nv) f = 2.0;\n      else if (nv > adapt_t * nd) f = 0.5;",
+     "if (nd > adapt_t * nv) f = 0.5;\n      else if (nv > adapt_t * nd) f = 2.0;"),
+    ("d_rescaled_the_wrong_way",
+     "for (size_t i = 0; i < 2 * C * P; ++i) d[i] /= f;", "for (size_t i = 0; i < 2 * C * P; ++i) d[i] *= f;"),
+    ("reverse_pass_drops_relax",
+     "tb[c * P + i] = obs ? 0.0 : relax * yv;", "tb[c * P + i] = obs ? 0.0 : yv;"),
 ]
 
 
