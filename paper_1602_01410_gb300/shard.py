@@ -10,6 +10,8 @@ all-to-all transposes per iteration); those workloads run as replicas.
 For the differentiation workload each rank returns the loss and gradients
 of the mean over ITS pixels; `combine_grad` re-weights them by the pixel
 share and sums them across ranks (one all-reduce of 2 + K*K numbers).
+After a sharded solve `gather_batch` reassembles the whole batch of x on
+every rank (one all-gather, outside the iterations).
 """
 from __future__ import annotations
 
@@ -40,3 +42,35 @@ def combine_grad(loss: float, dlam: float, dh, local_px: int, total_px: int, gro
     if dist.is_available() and dist.is_initialized():
         dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=group)
     return float(buf[0]), float(buf[1]), buf[2:].reshape(dh.shape)
+
+
+def gather_batch(x_local, pixels: Sequence[int], group=None):
+    """Reassemble a sharded batch on every rank.
+
+    x_local: the rank's images (those `partition(pixels, world)` gave it, in
+    increasing index order) concatenated in the batch layout, a 1-D torch
+    tensor; pixels[j]: elements of image j (channels x rows x cols).  Returns
+    the whole batch in the original image order, on x_local's device.  One
+    all-gather of equal-length (zero-padded) buffers; with no process group
+    initialised it returns x_local unchanged (one rank holds everything)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x_local
+    world = dist.get_world_size(group)
+    parts = partition(pixels, world)
+    longest = max(sum(pixels[j] for j in p) for p in parts)
+    buf = torch.zeros(longest, dtype=x_local.dtype, device=x_local.device)
+    buf[:x_local.numel()] = x_local.reshape(-1)
+    bufs = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(bufs, buf, group=group)
+    begin = [0]
+    for n in pixels:
+        begin.append(begin[-1] + n)
+    out = torch.empty(begin[-1], dtype=x_local.dtype, device=x_local.device)
+    for r, p in enumerate(parts):
+        o = 0
+        for j in p:
+            out[begin[j]:begin[j + 1]] = bufs[r][o:o + pixels[j]]
+            o += pixels[j]
+    return out

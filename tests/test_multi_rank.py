@@ -81,3 +81,33 @@ def test_sharded_gradient_equals_full_batch():
         assert p.exitcode == 0
     assert abs(Lc - L) < 1e-14 and abs(dlc - dl) < 1e-12 * abs(dl)
     assert np.max(np.abs(dhc - dh)) < 1e-12 * np.max(np.abs(dh))
+
+
+def _gather_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    pixels = [3 * 16 * 16, 20 * 24, 64 * 64, 8 * 8, 3 * 32 * 48]
+    full = torch.arange(sum(pixels), dtype=torch.float64)
+    begin = np.concatenate([[0], np.cumsum(pixels)])
+    mine = shard.partition(pixels, world)[rank]
+    local = torch.cat([full[begin[j]:begin[j + 1]] for j in mine])
+    got = shard.gather_batch(local, pixels)
+    out.put((rank, bool(torch.equal(got, full))))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gather_batch_reassembles_the_sharded_batch():
+    assert shard.gather_batch(torch.ones(3), [3]).tolist() == [1.0, 1.0, 1.0]  # no process group
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert res == {0: True, 1: True}
