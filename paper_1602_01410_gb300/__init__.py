@@ -16,7 +16,7 @@ Typical use (device tensors; y and mask in the batch layout of deconv.h)::
 
     plan = Plan([(M, N)], h, mask, lam, mu)          # extended grid M x N, K x K kernel
     plan.set_options(bgs_passes=K // 2, tikh_iters=100, adapt_t=3.0)   # optional variants
-    plan.autotune(y)                                 # optional: launch shapes for this GPU
+    plan.autotune(y, cache="tunes.json")            # optional: launch shapes for this GPU, cached
     x = plan.solve(y, iters)                         # x^{iters}
     loss, dlam, dh = plan.grad(y, x_true, iters)     # gradient of the unrolled solve (defaults only)
 
@@ -295,6 +295,71 @@ def deconv_plan_destroy(plan: int) -> None:
 # ------------------------------------------------------- torch convenience
 
 
+def _source_digest() -> str:
+    """Digest of the library's source (CUDA, C++ and the C header): a cached
+    tuning is reused only by the build it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(_HERE, "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if not name.endswith((".cu", ".cuh", ".h")):
+            continue
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    with open(os.path.join(os.path.dirname(_HERE), "include", "deconv.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def tune_key(shapes, channels: int, ksize: int, dtype: int, relax: float, kernel_per_image: int, ksizes,
+             options, device: str) -> str:
+    """Key of a cached launch tuning: everything that changes which tuning is
+    fastest (the batch geometry, element type, iteration variant and GPU)
+    plus the library source it was measured with."""
+    import json
+    return json.dumps({"shapes": [list(map(int, s)) for s in shapes], "channels": int(channels),
+                       "ksize": int(ksize), "dtype": int(dtype), "relax": float(relax),
+                       "kernel_per_image": int(kernel_per_image),
+                       "ksizes": None if ksizes is None else [int(k) for k in ksizes],
+                       "options": [float(v) for v in options], "device": device,
+                       "source": _source_digest()}, sort_keys=True)
+
+
+class TuneCache:
+    """Launch tunings chosen by deconv_autotune, kept in a JSON file so that
+    later plans of the same key skip the timing runs.  A missing or
+    unreadable file reads as empty; writes replace the file atomically."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def _read(self) -> dict:
+        import json
+        try:
+            with open(self.path) as f:
+                data = json.load(f)
+            return data if isinstance(data, dict) else {}
+        except (OSError, ValueError):
+            return {}
+
+    def get(self, key: str):
+        hit = self._read().get(key)
+        if not isinstance(hit, dict) or "tune" not in hit:
+            return None
+        return hit
+
+    def put(self, key: str, tune: dict, ms_per_iter: float) -> None:
+        import json
+        import tempfile
+        data = self._read()
+        data[key] = {"tune": dict(tune), "ms_per_iter": float(ms_per_iter)}
+        d = os.path.dirname(os.path.abspath(self.path))
+        fd, tmp = tempfile.mkstemp(dir=d, prefix=".tune_cache")
+        with os.fdopen(fd, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
 class Plan:
     """A plan whose workspace is a torch CUDA tensor.
 
@@ -312,6 +377,9 @@ class Plan:
         kpi = 1 if h.dim() == 3 else 0
         self.shapes = [tuple(s) for s in shapes]
         self.channels = channels
+        self.ksize, self.kernel_per_image, self.relax, self._dt = K, kpi, float(relax), dt
+        self.ksizes = None if ksizes is None else [int(k) for k in ksizes]
+        self.options = (1, 0, 1e-3, 0.0)
         self.dims, self._keep = make_dims([s[0] for s in shapes], [s[1] for s in shapes], K, channels, dt,
                                           relax, kpi, ksizes)
         self.workspace_bytes = deconv_workspace_size(self.dims)
@@ -349,10 +417,29 @@ class Plan:
                     adapt_t: float = 0.0) -> None:
         """BGS passes per iteration, Tikhonov warm start, penalty adaptation (see deconv.h)."""
         deconv_set_options(self.handle, bgs_passes, tikh_iters, tikh_tau, adapt_t)
+        self.options = (bgs_passes, tikh_iters, tikh_tau, adapt_t)
 
-    def autotune(self, y, trial_iters: int = 20):
-        """Pick the fastest launch tuning for this plan (see deconv_autotune)."""
-        return deconv_autotune(self.handle, y.data_ptr(), trial_iters)
+    def autotune(self, y, trial_iters: int = 20, cache: Optional[str] = None):
+        """Pick the fastest launch tuning for this plan (see deconv_autotune).
+        With `cache` (a JSON file path), a tuning stored for the same key
+        (`tune_key`) is applied with deconv_retune instead of timing the
+        candidates again, and a new choice is stored.  Either way the plan is
+        left with no iteration state.  Returns (tuning, ms per iteration)."""
+        if cache is None:
+            return deconv_autotune(self.handle, y.data_ptr(), trial_iters)
+        torch = self._torch
+        dev = self.workspace.device
+        props = torch.cuda.get_device_properties(dev)
+        key = tune_key(self.shapes, self.channels, self.ksize, self._dt, self.relax, self.kernel_per_image,
+                       self.ksizes, self.options, f"{props.name} / {props.multi_processor_count} SMs")
+        store = TuneCache(cache)
+        hit = store.get(key)
+        if hit is not None:
+            self.retune(**hit["tune"])
+            return dict(hit["tune"]), float(hit["ms_per_iter"])
+        best, ms = deconv_autotune(self.handle, y.data_ptr(), trial_iters)
+        store.put(key, best, ms)
+        return best, ms
 
     def retune(self, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
                col_fft_values: int = 0) -> None:
