@@ -80,3 +80,19 @@ def test_initial_fill_worked(case):
     y, m = mat(g["y" + case]), mat(g["mask" + case]).astype(np.uint8)
     yt = oracle.init_ytilde(y, m, 3, round_f32=False)
     assert np.allclose(yt, mat(g["yt" + case]), rtol=0, atol=1e-15), yt
+
+
+@pytest.mark.parametrize("relax", [2, 1])
+def test_one_iteration_worked_on_a_2x2_grid(relax):
+    g = load("admm_one_iteration_2x2.txt")
+    mu, lam = g["mu_lambda"][0]
+    y, m = mat(g["y"]), mat(g["mask"]).astype(np.uint8)
+    st = oracle.State(mat(g["yt0"])[None].copy(), np.zeros((1, 2, 2, 2)), np.zeros((1, 2, 2, 2)))
+    x, st1, s = oracle.admm(y[None], m[None], np.ones((1, 1)), lam, mu, 1, relax=float(relax), state=st,
+                            stats=True)
+    tol = dict(rtol=0, atol=1e-14)
+    assert np.allclose(x[0], mat(g["x1"]), **tol), x
+    assert np.allclose(st1.yt[0], mat(g[f"yt1_relax{relax}"]), **tol), st1.yt
+    assert np.allclose(st1.v[0], np.stack([mat(g["v1_h"]), mat(g["v1_v"])]), **tol), st1.v
+    assert np.allclose(st1.d[0], np.stack([mat(g["d1_h"]), mat(g["d1_v"])]), **tol), st1.d
+    assert np.allclose(s[0], g[f"stats_relax{relax}"][0], rtol=1e-14, atol=0), s
