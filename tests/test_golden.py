@@ -96,3 +96,17 @@ def test_one_iteration_worked_on_a_2x2_grid(relax):
     assert np.allclose(st1.v[0], np.stack([mat(g["v1_h"]), mat(g["v1_v"])]), **tol), st1.v
     assert np.allclose(st1.d[0], np.stack([mat(g["d1_h"]), mat(g["d1_v"])]), **tol), st1.d
     assert np.allclose(s[0], g[f"stats_relax{relax}"][0], rtol=1e-14, atol=0), s
+
+
+def test_penalty_adaptation_worked_on_a_2x2_grid():
+    g = load("admm_one_iteration_2x2.txt")
+    mu, lam = g["mu_lambda"][0]
+    y, m = mat(g["y"]), mat(g["mask"]).astype(np.uint8)
+    d1 = np.stack([mat(g["d1_h"]), mat(g["d1_v"])])
+    for t, mu_after, scale in g["adapt"]:
+        st = oracle.State(mat(g["yt0"])[None].copy(), np.zeros((1, 2, 2, 2)), np.zeros((1, 2, 2, 2)))
+        st.mu = mu
+        x, st1, _ = oracle.admm(y[None], m[None], np.ones((1, 1)), lam, mu, 1, state=st, adapt_t=t)
+        assert st1.mu == mu_after, (t, st1.mu)
+        assert np.allclose(st1.d[0], scale * d1, rtol=0, atol=1e-14), (t, st1.d)
+        assert np.allclose(x[0], mat(g["x1"]), rtol=0, atol=1e-14)
