@@ -14,8 +14,10 @@ solves its own replica (weak scaling, no data-path collective).
 Timing: W untimed warm-up steps, then K steps, each preceded by an L2 flush
 (a 512 MB device write, outside the timed events) and bracketed by CUDA
 events on the plan's stream; a barrier and a device synchronise on both
-sides; the max over ranks.  `e2e` times the same step through
-deconv_solve_host (pinned host y in, host x out, copies included).
+sides; the max over ranks.  `e2e` times the same step from host buffers:
+deconv_solve_host (pinned host y in, host x out, copies included), or for
+the gradient workload pinned y and x_true copied in, deconv_grad, and the
+loss and gradients read back.
 `roofline` reports the dominant kernel (the row or column pass) from CUDA
 events around its launches (deconv_profile_passes) and its compulsory bytes.
 `cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
@@ -438,17 +440,43 @@ def main():
             dist.destroy_process_group()
         return
 
-    # End to end through the host-buffer entry point (forward solve).
+    # End to end through the public API, host buffers in and out.
     y_host = torch.tensor(y_np, dtype=dt).pin_memory()
-    x_host = torch.empty_like(y_host).pin_memory()
-    plan.solve_host(y_host, x_host, prob.iters)
+    if grad_mode:
+        # the gradient step: pinned y and x_true copied in on the plan's stream,
+        # deconv_grad (returns loss and dL/dlambda on the host), dL/dh read back
+        xt_host = x_true.cpu().pin_memory()
+        dh_host = torch.empty(tuple(dh.shape), dtype=dt).pin_memory()
+        y_dev, xt_dev = torch.empty_like(y), torch.empty_like(x_true)
+        e2e_in = (y_host.numel() + xt_host.numel()) * esz
+        e2e_out = dh_host.numel() * esz + 16
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                y_dev.copy_(y_host, non_blocking=True)
+                xt_dev.copy_(xt_host, non_blocking=True)
+                loss, dlam = pkg.deconv_grad(plan.handle, y_dev.data_ptr(), xt_dev.data_ptr(), prob.iters, 10,
+                                             gptr, gws_n, dh.data_ptr(), x.data_ptr())
+                if sharded:
+                    from paper_1602_01410_gb300 import shard
+                    shard.combine_grad(loss, dlam, dh, prob.pixels(), total_px_all)
+                dh_host.copy_(dh, non_blocking=True)
+            stream.synchronize()
+    else:
+        # the forward solve through deconv_solve_host (copies inside the call)
+        x_host = torch.empty_like(y_host).pin_memory()
+        e2e_in = e2e_out = int(y_np.size * esz)
+
+        def e2e_step():
+            plan.solve_host(y_host, x_host, prob.iters)
+    e2e_step()
     barrier()
     e2e_ms = 0.0
     for k in range(args.steps):
         flush.fill_(float(k))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        plan.solve_host(y_host, x_host, prob.iters)
+        e2e_step()
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -477,8 +505,8 @@ def main():
                    "parallelism": ("images sharded across ranks" if sharded else "replicas") if world > 1
                    else "single GPU",
                    "tune": tune if tune is not None else "default launch tuning"},
-        "e2e": {"value": e2e_value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": int(y_np.size * esz),
-                "d2h_bytes_per_step": int(y_np.size * esz)},
+        "e2e": {"value": e2e_value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": int(e2e_in),
+                "d2h_bytes_per_step": int(e2e_out)},
         "roofline": {"bound": "hbm", "kernel": f"{dom}_pass", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (ROW_TRAFFIC_BYTES_PER_PX[args.config] * px
@@ -497,7 +525,8 @@ def main():
     if grad_mode:
         out["config"]["step"] = ("deconv_grad: forward with checkpoints every 10 iterations, loss, reverse pass "
                                  "(dL/dlambda, dL/dh); value counts forward iterations")
-        out["e2e"]["note"] = "e2e times the forward solve through deconv_solve_host"
+        out["e2e"]["note"] = ("e2e times the gradient step: pinned y and x_true in, deconv_grad, loss, "
+                              "dL/dlambda and dL/dh out")
     if args.compare_plain:
         n_it = min(prob.iters, args.plain_iters)
         for _ in range(2):
