@@ -379,7 +379,7 @@ void or_tikhonov(int M, int N, int K, const double *h, const uint8_t *mask, int 
  * component), v = v_x with the same layout; *mu_io = mu in, the final mu out.
  * Initial state (init == 1): y~^0 = or_init_ytilde (then the warm start, if
  * any), d^0 = 0, v^0 = D x^0 with x^0 = y~^0, or the warm start's x.
- * Output x = x^{iters}.  stats (nullable) receives per iteration
+ * Output x = x^{iters} (x^0 when iters = 0 from the initial state).  stats (nullable) receives per iteration
  *   [ ||d^{i+1}-d^i||^2, ||z^{i+1}-z^i||^2, mu ||v^{i+1}-v^i||^2, J(x^{i+1}) ]
  * (z change and x of the last pass; d^{i+1} before the rescaling; mu = mu^i)
  * with J(x) = 1/2 sum_obs (y - T~x)^2 + lambda sum_j ||(Dx)_j||, the
@@ -406,7 +406,8 @@ int or_admm_ex(int C, int M, int N, int K, const double *h, const double *y, con
         or_tikhonov(M, N, K, h, mask + c * P, tikh_iters, tikh_tau, yt + c * P, x + c * P);
         or_diff_fwd(x + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P); /* v0 = D x0, x0 = warm-start x */
       } else {
-        or_diff_fwd(yt + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P); /* v0 = D x0, x0 = y~0 */
+        memcpy(x + c * P, yt + c * P, P * sizeof(double));                  /* x0 = y~0 */
+        or_diff_fwd(yt + c * P, M, N, v + 2 * c * P, v + (2 * c + 1) * P); /* v0 = D x0 */
       }
     }
     memset(d, 0, 2 * C * P * sizeof(double));

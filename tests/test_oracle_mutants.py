@@ -53,6 +53,9 @@ MUTANTS = [
      "for (size_t i = 0; i < 2 * C * P; ++i) d[i] /= f;", "for (size_t i = 0; i < 2 * C * P; ++i) d[i] *= f;"),
     ("reverse_pass_drops_relax",
      "tb[c * P + i] = obs ? 0.0 : relax * yv;", "tb[c * P + i] = obs ? 0.0 : yv;"),
+    ("fill_uses_the_first_plane_mask",
+     "or_init_ytilde(y + c * P, mask + c * P, M, N, K, round_f32, yt + c * P);",
+     "or_init_ytilde(y + c * P, mask, M, N, K, round_f32, yt + c * P);"),
 ]
 
 

@@ -17,6 +17,7 @@ from scipy.optimize import minimize
 from scipy.signal import convolve2d
 
 import oracle
+from paper_1602_01410_gb300 import inputs
 
 
 def naive_dft(x, sign=-1):
@@ -157,6 +158,32 @@ def test_vector_soft_threshold_edge_cases():
     assert np.allclose(v[:, 2], [2.7, 3.6], atol=1e-15)
 
 
+def brute_force_fill(y, mask, K):
+    M, N = y.shape
+    b = K // 2
+    mean = y[mask != 0].mean()
+    out = np.empty_like(y)
+    for i in range(M):
+        for j in range(N):
+            ic, jc = min(max(i, b), M - b - 1), min(max(j, b), N - b - 1)
+            inband = not (b <= i < M - b and b <= j < N - b)
+            out[i, j] = y[i, j] if mask[i, j] else (y[ic, jc] if (inband and mask[ic, jc]) else mean)
+    return out
+
+
+def test_initial_state_of_every_channel_plane():
+    # Three channels with their own Bayer planes: zero iterations return
+    # x^0 = y~^0, each plane filled from its own mask and mean (Sec. III-B,
+    # Sec. III-C).
+    rng = np.random.default_rng(19)
+    M, N, K = 12, 14, 3
+    m = inputs.mask_bayer_rggb(M, N, K // 2)
+    y = np.where(m, rng.random((3, M, N)), 0.0)
+    x, _, _ = oracle.admm(y, m, np.full((K, K), 1.0 / K ** 2), 1e-3, 1e-2, 0, round_f32=False)
+    for c in range(3):
+        assert np.allclose(x[c], brute_force_fill(y[c], m[c], K), rtol=0, atol=1e-15), c
+
+
 def test_init_ytilde_brute_force():
     rng = np.random.default_rng(9)
     M, N, K = 14, 17, 5
@@ -166,6 +193,7 @@ def test_init_ytilde_brute_force():
     mask[b:M - b, b:N - b] = rng.random((M - 2 * b, N - 2 * b)) > 0.35
     y = np.where(mask, y, 0.0)
     got = oracle.init_ytilde(y, mask, K, round_f32=False)
+    assert np.allclose(got, brute_force_fill(y, mask, K), rtol=0, atol=1e-15)
     mean = y[mask != 0].mean()
     for i in range(M):
         for j in range(N):
