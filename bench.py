@@ -225,7 +225,7 @@ def plain_grad(prob, iters, dev, dt):
         xt = torch.tensor(prob.x_true[j], dtype=dt, device=dev)
         loss = loss + ((x - xt) ** 2).sum() / n_all
     loss.backward()
-    return float(loss), float(lam.grad), hk.grad.detach()
+    return float(loss.detach()), float(lam.grad), hk.grad.detach()
 
 
 def subset_problem(prob, idx):
