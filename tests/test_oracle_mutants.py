@@ -72,6 +72,13 @@ MUTANTS = [
      "yb[c * P + i] = obs ? yv : -(relax - 1.0) * yv;", "yb[c * P + i] = obs ? yv : (relax - 1.0) * yv;"),
     ("vertical_difference_adjoint_sign",
      "+ uv[(size_t)wrap(i - 1, M) * N + j] - uv[o];", "- uv[(size_t)wrap(i - 1, M) * N + j] + uv[o];"),
+    ("band_clamp_off_by_one",
+     "int ic = i < b ? b : (i >= M - b ? M - b - 1 : i);", "int ic = i < b ? b : (i >= M - b ? M - b : i);"),
+    ("prox_norm_misses_the_last_plane",
+     "for (int c = 0; c < dim; ++c) s += a[(size_t)c * n + j] * a[(size_t)c * n + j];",
+     "for (int c = 0; c + 1 < dim; ++c) s += a[(size_t)c * n + j] * a[(size_t)c * n + j];"),
+    ("dft_combine_twiddle_drops_the_block_offset",
+     "w->tw[(size_t)((r * (k + q * m)) % n) * step]", "w->tw[(size_t)((r * k) % n) * step]"),
 ]
 
 
