@@ -110,3 +110,17 @@ def test_penalty_adaptation_worked_on_a_2x2_grid():
         assert st1.mu == mu_after, (t, st1.mu)
         assert np.allclose(st1.d[0], scale * d1, rtol=0, atol=1e-14), (t, st1.d)
         assert np.allclose(x[0], mat(g["x1"]), rtol=0, atol=1e-14)
+
+
+def test_tikhonov_warm_start_worked_on_a_2x2_grid():
+    g = load("admm_one_iteration_2x2.txt")
+    mu, lam = g["mu_lambda"][0]
+    tau, steps = g["tikh_tau_steps"][0]
+    y, m = mat(g["y"]), mat(g["mask"]).astype(np.uint8)
+    x, st, _ = oracle.admm(y[None], m[None], np.ones((1, 1)), lam, mu, 0, tikh_iters=int(steps), tikh_tau=tau,
+                           round_f32=False)
+    tol = dict(rtol=0, atol=1e-14)
+    assert np.allclose(x[0], mat(g["tikh_x0"]), **tol), x
+    assert np.allclose(st.yt[0], mat(g["tikh_yt0"]), **tol), st.yt
+    assert np.allclose(st.v[0], np.stack([mat(g["tikh_v0_h"]), mat(g["tikh_v0_v"])]), **tol), st.v
+    assert np.all(st.d == 0.0)
