@@ -124,3 +124,14 @@ def test_tikhonov_warm_start_worked_on_a_2x2_grid():
     assert np.allclose(st.yt[0], mat(g["tikh_yt0"]), **tol), st.yt
     assert np.allclose(st.v[0], np.stack([mat(g["tikh_v0_h"]), mat(g["tikh_v0_v"])]), **tol), st.v
     assert np.all(st.d == 0.0)
+
+
+def test_two_bgs_passes_worked_on_a_2x2_grid():
+    g = load("admm_one_iteration_2x2.txt")
+    mu, lam = g["mu_lambda"][0]
+    y, m = mat(g["y"]), mat(g["mask"]).astype(np.uint8)
+    st = oracle.State(mat(g["yt0"])[None].copy(), np.zeros((1, 2, 2, 2)), np.zeros((1, 2, 2, 2)))
+    x, st1, s = oracle.admm(y[None], m[None], np.ones((1, 1)), lam, mu, 1, state=st, passes=2, stats=True)
+    assert np.allclose(x[0], mat(g["bgs2_x"]), rtol=0, atol=1e-14), x
+    assert np.allclose(st1.yt[0], mat(g["bgs2_yt"]), rtol=0, atol=1e-14), st1.yt
+    assert np.isclose(s[0, 1], g["bgs2_dz2"][0][0], rtol=1e-13, atol=0), s
