@@ -203,7 +203,8 @@ def admm(y: np.ndarray, mask: np.ndarray, h: np.ndarray, lam: float, mu: float, 
     y, mask: (C, M, N).  passes: BGS passes per iteration; adapt_t > 0: the
     penalty adaptation of Eq. (varying_penalty) with threshold t; tikh_iters
     > 0 (fresh start only): Tikhonov warm start of z with tau = tikh_tau.
-    Returns (x, state, stats) where x is (C, M, N) = x^{iters}, state the
+    Returns (x, state, stats) where x is (C, M, N) = x^{iters} (x^0 of the
+    initial state for a fresh start with iters = 0), state the
     final State and stats an (iters, 4) array of [||dd||^2, ||dz||^2,
     mu ||dv||^2, J] (or None); with mu_hist=True a fourth item, the (iters,)
     penalties the iterations used."""
