@@ -80,3 +80,18 @@ def test_plan_create_rejects_bad_scalars_without_a_gpu(lib):
 def test_solve_rejects_null_plan(lib):
     assert lib.deconv_solve(None, None, None, 1, 0, None) == pkg.DECONV_EINVAL
     assert lib.deconv_plan_destroy(None) == pkg.DECONV_EINVAL
+
+
+def test_header_is_plain_c(tmp_path):
+    # The boundary is a C ABI: the header compiles as C99 and C11 with every
+    # warning an error, and a C caller can take the address of each entry point.
+    import subprocess
+    names = declared()
+    src = tmp_path / "use.c"
+    src.write_text('#include "deconv.h"\ntypedef void (*entry)(void);\nentry entry_points[] = {\n' +
+                   "".join(f"  (entry){n},\n" for n in names) + "};\n")
+    for std in ("c99", "c11"):
+        r = subprocess.run(["gcc", f"-std={std}", "-Wall", "-Wextra", "-Werror", "-pedantic-errors",
+                            "-Wno-cast-function-type", "-I", os.path.join(ROOT, "include"), "-c", str(src),
+                            "-o", str(tmp_path / f"use_{std}.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
