@@ -524,12 +524,12 @@ struct deconv_plan_s {
   int tikh_iters = 0;
   double tikh_tau = 1e-3;
   double adapt_t = 0.0;
-  bool adapt_ready = false;
+  bool adapt_ready = false;  // the per-image penalties and v were set by a fresh solve (or a state blob)
   // Creation arguments kept for re-tuning (deconv_retune / deconv_autotune).
   deconv_dims dims{};
   std::vector<int32_t> rows, cols, ksizes;
   size_t ws_bytes = 0;
-  deconv_tune tune{0, 0, -1, 0};  // the per-image penalties and v were set by a fresh solve
+  deconv_tune tune{0, 0, -1, 0, 0};  // the launch tuning in force (deconv_get_tune)
   cudaGraphExec_t gexec = nullptr;
   // While a graph is captured: the kernel classes of one pass (disjoint sets
   // of images) fan out over side streams, so their launches run concurrently.
@@ -1355,7 +1355,7 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  deconv_tune bt{0, 0, -1, 0};
+  deconv_tune bt{0, 0, -1, 0, 0};
   float bms = -1.f;
   deconv_status st = DECONV_OK;
   for (const deconv_tune &t : cands) {
