@@ -2,7 +2,6 @@
 stated lattices, the boundary band is never observed (Eq. (4)), and the
 noise level matches the requested BSNR."""
 import numpy as np
-import pytest
 
 from paper_1602_01410_gb300 import inputs
 

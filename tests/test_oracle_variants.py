@@ -14,7 +14,6 @@
   the adapted run reaches the fixed-mu minimiser.
 """
 import numpy as np
-import pytest
 
 import oracle
 from paper_1602_01410_gb300 import inputs
