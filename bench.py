@@ -252,20 +252,22 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(name: str, budget_s: float = 20.0):
-    """FP64 oracle on the host cores: a bounded sample of the workload."""
+def cpu_baseline(name: str, budget_s: float = 20.0, options=(1, 0, 1e-3, 0.0)):
+    """FP64 oracle on the host cores: a bounded sample of the workload (with
+    the same iteration options: BGS passes, Tikhonov steps and tau, adaptation)."""
     import oracle
     prob = make_problem(name)
     j = 0
     y, m = prob.y[j], prob.mask[j]
     px = prob.channels * y.shape[-2] * y.shape[-1]
+    opts = dict(passes=options[0], tikh_iters=options[1], tikh_tau=options[2], adapt_t=options[3])
     t0 = time.perf_counter()
-    oracle.admm(y, m, prob.h, prob.lam, prob.mu, 1)
+    oracle.admm(y, m, prob.h, prob.lam, prob.mu, 1, **opts)
     t1 = time.perf_counter()
     per_iter = max(t1 - t0, 1e-3)
     n = max(2, min(prob.iters, int(budget_s / per_iter)))
     t0 = time.perf_counter()
-    oracle.admm(y, m, prob.h, prob.lam, prob.mu, n)
+    oracle.admm(y, m, prob.h, prob.lam, prob.mu, n, **opts)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": px * n / dt / 1e6, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
@@ -281,11 +283,12 @@ def run_reference(args, rank: int, world: int):
     y, m = prob.y[0], prob.mask[0]
     px = prob.channels * y.shape[-2] * y.shape[-1]
     sample_iters = max(1, min(prob.iters, args.ref_iters))
+    opts = dict(passes=args.bgs_passes, tikh_iters=args.tikh_iters, tikh_tau=args.tikh_tau, adapt_t=args.adapt_t)
     for _ in range(args.warmup):
-        oracle.admm(y, m, prob.h, prob.lam, prob.mu, 1)
+        oracle.admm(y, m, prob.h, prob.lam, prob.mu, 1, **opts)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.admm(y, m, prob.h, prob.lam, prob.mu, sample_iters)
+        oracle.admm(y, m, prob.h, prob.lam, prob.mu, sample_iters, **opts)
     dt = time.perf_counter() - t0
     value = px * sample_iters * args.steps / dt / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -294,7 +297,9 @@ def run_reference(args, rank: int, world: int):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded generator)",
            "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}",
-                      "sample": f"image 0, {sample_iters} iterations per step"},
+                      "sample": f"image 0, {sample_iters} iterations per step",
+                      "options": {"bgs_passes": args.bgs_passes, "tikh_iters": args.tikh_iters,
+                                  "tikh_tau": args.tikh_tau, "adapt_t": args.adapt_t}},
            "cpu_baseline": {"value": value, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
                             "sample": f"image 0 of the workload, {sample_iters} iterations per step, "
                                       f"{args.steps} steps"},
@@ -323,6 +328,11 @@ def main():
                     help="comma-separated image indices of the batch to keep (small profiling cases)")
     ap.add_argument("--timed-only", action="store_true",
                     help="skip the e2e, per-pass and CPU-baseline legs (profiling runs)")
+    ap.add_argument("--bgs-passes", type=int, default=1,
+                    help="BGS passes per iteration (Proposed-AD: (K - 1) / 2 for a K x K blur)")
+    ap.add_argument("--adapt-t", type=float, default=0.0, help="penalty adaptation threshold t (0: fixed mu)")
+    ap.add_argument("--tikh-iters", type=int, default=0, help="Tikhonov warm-start steps per solve")
+    ap.add_argument("--tikh-tau", type=float, default=1e-3)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -376,6 +386,12 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     grad_mode = args.config == "c5"
+    options = (args.bgs_passes, args.tikh_iters, args.tikh_tau, args.adapt_t)
+    variant = options != (1, 0, 1e-3, 0.0)
+    if variant:
+        if grad_mode:
+            raise SystemExit("the gradient workload runs the default iteration only")
+        plan.set_options(*options)
     tune = None
     if not args.no_autotune:  # timed on the forward iteration (the gradient step reuses its passes)
         with torch.cuda.stream(stream):
@@ -504,21 +520,26 @@ def main():
                          f"{plan.workspace_bytes / 2**20:.0f} MB workspace is reused across the step's iterations",
                    "parallelism": ("images sharded across ranks" if sharded else "replicas") if world > 1
                    else "single GPU",
-                   "tune": tune if tune is not None else "default launch tuning"},
+                   "tune": tune if tune is not None else "default launch tuning",
+                   "options": {"bgs_passes": args.bgs_passes, "tikh_iters": args.tikh_iters,
+                               "tikh_tau": args.tikh_tau, "adapt_t": args.adapt_t}},
         "e2e": {"value": e2e_value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": int(e2e_in),
                 "d2h_bytes_per_step": int(e2e_out)},
         "roofline": {"bound": "hbm", "kernel": f"{dom}_pass", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (ROW_TRAFFIC_BYTES_PER_PX[args.config] * px
                                  if dom == "row" and args.config in ROW_TRAFFIC_BYTES_PER_PX and not args.images
-                                 else None),
+                                 and not variant else None),
                      "peak_kind": peak_kind,
                      "ms_per_launch": ms_dom, "bytes_per_px": per_px[dom],
                      "other_pass_ms": ms_col if dom == "row" else ms_row,
                      "algorithmic_bytes_per_px_iter": algorithmic_bytes_per_px(f_unobs, esz),
                      # whole step: the method's own bytes per pixel and iteration at the measured rate
-                     "step_achieved_gbs": value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world,
-                     "step_frac": value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world / peak},
+                     # (counted for one BGS pass at fixed mu; not reported for the variants)
+                     "step_achieved_gbs": (None if variant else
+                                           value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world),
+                     "step_frac": (None if variant else
+                                   value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world / peak)},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
@@ -544,7 +565,7 @@ def main():
                         "what": ("torch.autograd through the unrolled per-image torch.fft iteration" if grad_mode
                                  else "per-image torch.fft (cuFFT) transforms and unfused torch ops")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.config)
+        out["cpu_baseline"] = cpu_baseline(args.config, options=options)
     if rank == 0:
         print(json.dumps(out))
     plan.close()
