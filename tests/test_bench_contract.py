@@ -36,3 +36,14 @@ def test_reference_arm_under_torchrun_prints_once():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [json.loads(v) for v in r.stdout.splitlines() if v.startswith("{")]
     assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["value"] > 0
+
+
+def test_reference_arm_runs_the_variants():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config", "c1",
+                        "--steps", "1", "--warmup", "1", "--ref-iters", "2", "--bgs-passes", "2", "--adapt-t", "3",
+                        "--tikh-iters", "2", "--tikh-tau", "0.01"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["config"]["options"] == {"bgs_passes": 2, "tikh_iters": 2, "tikh_tau": 0.01, "adapt_t": 3.0}
+    assert line["value"] > 0
