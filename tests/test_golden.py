@@ -135,3 +135,14 @@ def test_two_bgs_passes_worked_on_a_2x2_grid():
     assert np.allclose(x[0], mat(g["bgs2_x"]), rtol=0, atol=1e-14), x
     assert np.allclose(st1.yt[0], mat(g["bgs2_yt"]), rtol=0, atol=1e-14), st1.yt
     assert np.isclose(s[0, 1], g["bgs2_dz2"][0][0], rtol=1e-13, atol=0), s
+
+
+def test_observation_masks_drawn_by_hand():
+    from paper_1602_01410_gb300 import inputs
+    g = load("masks_7x8.txt")
+    M, N, b = 7, 8, 1
+    assert np.array_equal(inputs.mask_crop(M, N, b), mat(g["crop"]))
+    assert np.array_equal(inputs.mask_decimation(M, N, b, 2), mat(g["decimation2"]))
+    bayer = inputs.mask_bayer_rggb(M, N, b)
+    for c, name in enumerate(("bayer_r", "bayer_g", "bayer_b")):
+        assert np.array_equal(bayer[c], mat(g[name])), name
