@@ -6,10 +6,12 @@ times iterations, per second of device time), whole job over all ranks.
 
 A step is one deconv_solve call of the workload: the initial fill (border
 padding) and the workload's full iteration count, inputs resident in HBM.
-Default workload (N = 1): 1024 x 1024 FP32 image, 21 x 21 random-walk motion
-blur, 1004 x 1004 valid crop with 40% of the pixels missing, BSNR 40 dB,
-500 iterations.  Single-image work does not shard: under torchrun every rank
-solves its own replica (weak scaling, no data-path collective).
+Default workload (N = 1), the largest: 32 RGB FP32 frames with sides from
+{512, ..., 1536} (113 M channel-pixels), 13 x 13 Gaussian blur (sigma 2.5),
+RGGB Bayer mask, vectorial TV, BSNR 45 dB, 400 iterations.  Batches shard by
+image across ranks (strong scaling, no data-path collective); single-image
+work does not shard: under torchrun every rank solves its own replica (weak
+scaling).
 
 Timing: W untimed warm-up steps, then K steps, each preceded by an L2 flush
 (a 512 MB device write, outside the timed events) and bracketed by CUDA
@@ -18,8 +20,14 @@ sides; the max over ranks.  `e2e` times the same step from host buffers:
 deconv_solve_host (pinned host y in, host x out, copies included), or for
 the gradient workload pinned y and x_true copied in, deconv_grad, and the
 loss and gradients read back.
-`roofline` reports the dominant kernel (the row or column pass) from CUDA
-events around its launches (deconv_profile_passes) and its compulsory bytes.
+`roofline` is the whole iteration against the HBM roofline: the method's
+own bytes per channel-pixel and iteration (y~ read, z written, d read and
+written, H^ read, mask bits) times the measured rate, over the measured
+copy bandwidth.  Its `passes` split one iteration into column and row
+passes with CUDA events captured between the passes of the CUDA graph, in
+one profiled replay right after the timed steps (same plan, stream and
+tuning).  `plain` times the unfused per-image cuFFT path with CUDA events
+over the same iteration count (torch.autograd for the gradient workload).
 `cpu_baseline` times the FP64 oracle on the host cores on a bounded sample.
 `--impl reference` times the oracle itself as the reference arm.
 """
@@ -58,20 +66,22 @@ def make_problem(name: str):
             "c4": inputs.config_c4, "c5": inputs.config_c5}[name]()
 
 
-# Compulsory bytes per pixel of one launch of each pass (FP32, two-pass
-# design): column pass = read (Y_row, R_row) 8 + read H^ 4 + write (X_row,
-# HX_row) 8; row pass = read (X_row, HX_row) 8 + y~ 4 + d 8 (read) + d 8
-# (write) + z 4f (write, f = unobserved fraction) + mask 1/8 + write
-# (Y_row, R_row) 8.
-def pass_bytes_per_px(f_unobs: float, esz: int = 4):
+# The method's own bytes per channel-pixel and iteration (FP32; FP64
+# doubles the values): what one iteration must read and write whatever the
+# design.  Row pass: y~ read 4, z written 4f (f = unobserved fraction),
+# d = (d_h, d_v) read 8 and written 8, mask bits 1/8.  Column pass: the
+# H^ half-spectrum 4.  The row-spectral intermediates the two-pass design
+# writes and reads (about 8 B each way per pass) are design traffic, not
+# counted here.
+def algorithmic_bytes(f_unobs: float, esz: int = 4):
     s = esz / 4.0
-    return {"col": 20.0 * s, "row": (36.0 + 4.0 * f_unobs) * s + 0.125}
+    row = (20.0 + 4.0 * f_unobs) * s + 0.125
+    col = 4.0 * s
+    return {"row": row, "col": col, "iter": row + col}
 
 
 def algorithmic_bytes_per_px(f_unobs: float, esz: int = 4) -> float:
-    """Bytes one iteration must move by the method itself: y~ 4, z 4f,
-    d read+write 16, H^ half-spectrum 4, mask 1/8 (FP32)."""
-    return (24.0 + 4.0 * f_unobs) * esz / 4.0 + 0.125
+    return algorithmic_bytes(f_unobs, esz)["iter"]
 
 
 class ClockSampler:
@@ -182,13 +192,23 @@ def plain_iterate(yt, d, v, y, m, H, den, lam, mu, relax, iters):
     return x, yt, d, v
 
 
-def plain_solve(prob, iters, dev, dt):
+def plain_prepare(prob, dev, dt):
+    """Per-image device inputs and spectra of the plain path (set-up, not timed)."""
     import torch
     out = []
     for j in range(len(prob.shapes)):
         H, den = plain_setup(prob, j, dev, dt)
         y = torch.tensor(prob.y[j], dtype=dt, device=dev)
         m = torch.tensor(prob.mask[j], device=dev)
+        out.append((H, den, y, m))
+    return out
+
+
+def plain_solve(prob, iters, dev, dt, prepared=None):
+    import torch
+    prepared = prepared or plain_prepare(prob, dev, dt)
+    out = []
+    for (H, den, y, m) in prepared:
         yt = plain_init(y, m, prob.ksize)
         v = torch.stack([torch.roll(yt, -1, 2) - yt, torch.roll(yt, -1, 1) - yt], 1)
         d = torch.zeros_like(v)
@@ -238,10 +258,12 @@ def subset_problem(prob, idx):
     return sub
 
 
-# DRAM bytes (read + write) per channel-pixel of one row pass (both halves),
-# from ncu captures of the current row kernels (profiles/row_col_pass_c2_1024_ncu_full.md,
-# profiles/traffic_c4_1536_rgb_ncu.md); None where no capture was taken.
-ROW_TRAFFIC_BYTES_PER_PX = {"c2": 29.60e6 / 1048576, "c4": 50.2}
+# DRAM bytes (read + write) per channel-pixel and iteration, all kernels of
+# one iteration, from an ncu capture of the kernels as they stand (file
+# named beside each figure; the capture's per-pixel figure is scaled to the
+# workload's pixels).  A workload without a capture of the current kernels
+# reports traffic null.
+ITER_TRAFFIC_BYTES_PER_PX = {}
 
 
 def measured_peak_hbm():
@@ -250,6 +272,19 @@ def measured_peak_hbm():
         with open(p) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def host_cores() -> int:
+    """Cores the oracle's OpenMP threads may use: the affinity mask, capped by
+    OMP_NUM_THREADS when that is set."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    omp = os.environ.get("OMP_NUM_THREADS", "")
+    if omp.isdigit() and int(omp) > 0:
+        n = min(n, int(omp))
+    return n
 
 
 def cpu_baseline(name: str, budget_s: float = 20.0, options=(1, 0, 1e-3, 0.0)):
@@ -269,7 +304,7 @@ def cpu_baseline(name: str, budget_s: float = 20.0, options=(1, 0, 1e-3, 0.0)):
     t0 = time.perf_counter()
     oracle.admm(y, m, prob.h, prob.lam, prob.mu, n, **opts)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = host_cores()
     return {"value": px * n / dt / 1e6, "unit": "Mpx*iter/s", "cores": cores, "kind": "oracle",
             "sample": f"image 0 of the workload ({y.shape[-2]}x{y.shape[-1]}x{prob.channels}), {n} iterations "
                       f"incl. setup, FP64 C+OpenMP, {dt:.1f} s"}
@@ -291,7 +326,7 @@ def run_reference(args, rank: int, world: int):
         oracle.admm(y, m, prob.h, prob.lam, prob.mu, sample_iters, **opts)
     dt = time.perf_counter() - t0
     value = px * sample_iters * args.steps / dt / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = host_cores()
     out = {"impl": "reference", "metric": "Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": 0,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -313,12 +348,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="c4", choices=sorted(WORKLOADS))
     ap.add_argument("--ref-iters", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare-plain", action="store_true",
-                    help="also time the plain per-image cuFFT path (torch.autograd for c5)")
-    ap.add_argument("--plain-iters", type=int, default=20)
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain per-image cuFFT comparison (torch.autograd for c5)")
+    ap.add_argument("--plain-iters", type=int, default=0,
+                    help="iterations of the plain comparison (0: the workload's own count)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end (host buffer) leg")
     ap.add_argument("--iters", type=int, default=0,
                     help="override the workload's iteration count (profiling runs; recorded in config)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -383,6 +420,8 @@ def main():
     x = torch.empty_like(y)
     px = prob.pixels()
     f_unobs = float(1.0 - mask_np.mean())
+    alg = algorithmic_bytes(f_unobs, esz)
+    peak, peak_kind = measured_peak_hbm()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     grad_mode = args.config == "c5"
@@ -488,7 +527,8 @@ def main():
     e2e_step()
     barrier()
     e2e_ms = 0.0
-    for k in range(args.steps):
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    for k in range(e2e_steps):
         flush.fill_(float(k))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -497,17 +537,33 @@ def main():
     e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(e, op=dist.ReduceOp.MAX)
-    e2e_units = (total_px_all if sharded else px * world) * prob.iters * args.steps
+    e2e_units = (total_px_all if sharded else px * world) * prob.iters * e2e_steps
     e2e_value = e2e_units / (float(e.item()) / 1e3) / 1e6
 
-    # Dominant kernel: per-pass durations from CUDA events around launches.
-    prof_iters = min(prob.iters, 100)
-    ms_col, ms_row = plan.profile_passes(prof_iters)
-    per_px = pass_bytes_per_px(f_unobs, esz)
-    peak, peak_kind = measured_peak_hbm()
-    dom, ms_dom = ("row", ms_row) if ms_row >= ms_col else ("col", ms_col)
-    achieved = per_px[dom] * px / (ms_dom / 1e3) / 1e9
+    # Split of one iteration into its passes: one profiled replay of the
+    # captured loop (CUDA events between the passes), same plan and stream.
+    passes = None
+    if not grad_mode and prob.iters > 20:
+        plan.set_profiling(True)
+        with torch.cuda.stream(stream):
+            flush.fill_(0.0)
+            plan.solve(y, min(prob.iters, 41), x=x)
+        ms_col, ms_row, ms_it = plan.graph_pass_times()
+        plan.set_profiling(False)
+        passes = {}
+        for name, ms in (("col", ms_col), ("row", ms_row)):
+            b_px = alg[name]
+            gbs = b_px * px / (ms / 1e3) / 1e9 / world if ms > 0 else None
+            passes[name] = {"ms_per_iter": ms, "algorithmic_bytes_per_px": b_px, "achieved_gbs": gbs,
+                            "frac": (gbs / peak) if gbs else None}
+        passes["iteration_ms"] = ms_it
+        passes["dominant"] = "row" if ms_row >= ms_col else "col"
+        passes["how"] = ("CUDA events captured between the passes of the CUDA graph (20-iteration loop), "
+                         "one replay after the timed steps; the events replace the overlap of each pass's "
+                         "launch with the previous pass's tail")
     launches_per_step = pkg.deconv_kernel_launches(plan.handle, prob.iters, 1 if grad_mode else 0, 10)
+    step_gbs = value * 1e6 * alg["iter"] / 1e9 / world
+    traffic_px = ITER_TRAFFIC_BYTES_PER_PX.get(args.config) if not (args.images or variant) else None
 
     out = {
         "metric": "Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": world, "steps": args.steps,
@@ -524,22 +580,17 @@ def main():
                    "options": {"bgs_passes": args.bgs_passes, "tikh_iters": args.tikh_iters,
                                "tikh_tau": args.tikh_tau, "adapt_t": args.adapt_t}},
         "e2e": {"value": e2e_value, "unit": "Mpx*iter/s", "h2d_bytes_per_step": int(e2e_in),
-                "d2h_bytes_per_step": int(e2e_out)},
-        "roofline": {"bound": "hbm", "kernel": f"{dom}_pass", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (ROW_TRAFFIC_BYTES_PER_PX[args.config] * px
-                                 if dom == "row" and args.config in ROW_TRAFFIC_BYTES_PER_PX and not args.images
-                                 and not variant else None),
-                     "peak_kind": peak_kind,
-                     "ms_per_launch": ms_dom, "bytes_per_px": per_px[dom],
-                     "other_pass_ms": ms_col if dom == "row" else ms_row,
-                     "algorithmic_bytes_per_px_iter": algorithmic_bytes_per_px(f_unobs, esz),
-                     # whole step: the method's own bytes per pixel and iteration at the measured rate
-                     # (counted for one BGS pass at fixed mu; not reported for the variants)
-                     "step_achieved_gbs": (None if variant else
-                                           value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world),
-                     "step_frac": (None if variant else
-                                   value * 1e6 * algorithmic_bytes_per_px(f_unobs, esz) / 1e9 / world / peak)},
+                "d2h_bytes_per_step": int(e2e_out), "steps": e2e_steps},
+        # Whole iteration against HBM: the method's bytes per channel-pixel
+        # and iteration at the timed rate (counted for one BGS pass at fixed
+        # mu: not reported for the variants, nor for the gradient step).
+        "roofline": {"bound": "hbm", "kernel": "one iteration (column pass + row pass)",
+                     "achieved": None if (variant or grad_mode) else step_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": None if (variant or grad_mode) else step_gbs / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_px_iter": alg["iter"],
+                     "traffic": (traffic_px[0] * px if traffic_px else None),
+                     "traffic_source": (traffic_px[1] if traffic_px else None),
+                     "passes": passes},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
@@ -548,20 +599,26 @@ def main():
                                  "(dL/dlambda, dL/dh); value counts forward iterations")
         out["e2e"]["note"] = ("e2e times the gradient step: pinned y and x_true in, deconv_grad, loss, "
                               "dL/dlambda and dL/dh out")
-    if args.compare_plain:
-        n_it = min(prob.iters, args.plain_iters)
+    if not args.no_plain and not variant:
+        n_it = prob.iters if args.plain_iters <= 0 else min(prob.iters, args.plain_iters)
+        prepared = None if grad_mode else plain_prepare(prob, dev, dt)
         for _ in range(2):
-            (plain_grad(prob, 2, dev, dt) if grad_mode else plain_solve(prob, 2, dev, dt))
+            (plain_grad(prob, 2, dev, dt) if grad_mode else plain_solve(prob, 2, dev, dt, prepared))
         torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record()
         if grad_mode:
             plain_grad(prob, n_it, dev, dt)
         else:
-            plain_solve(prob, n_it, dev, dt)
+            plain_solve(prob, n_it, dev, dt, prepared)
+        e1.record()
         torch.cuda.synchronize(dev)
-        pt = time.perf_counter() - t0
+        pt = e0.elapsed_time(e1) / 1e3
         pv = px * n_it / pt / 1e6
         out["plain"] = {"value": pv, "unit": "Mpx*iter/s", "iterations": n_it, "speedup": value / pv,
+                        "timing": "CUDA events on the current stream, one run of the full iteration count "
+                                  "(per-image spectra and inputs prepared before the timed region)",
                         "what": ("torch.autograd through the unrolled per-image torch.fft iteration" if grad_mode
                                  else "per-image torch.fft (cuFFT) transforms and unfused torch ops")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

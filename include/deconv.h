@@ -152,7 +152,16 @@ deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
  * stages its rows in shared memory for one-channel plans of one row class),
  * 0 = reads them through L1, 1 = stages them (one channel only).
  * fft_values: 16 gives a row or column of length L to L/16 threads (more
- * resident warps), 32 to L/32 threads (fewer transposes). */
+ * resident warps), 32 to L/32 threads (fewer transposes).
+ * l2_group_mb: the images of a batch are independent problems, so the
+ * captured iteration loop runs them in groups, all iterations of one group
+ * before the next, each group's row-spectral intermediate (C x M x (N/2+1)
+ * complex pairs per image) at most l2_group_mb MiB so that it stays in the
+ * 126 MB L2 from one pass to the next (an image larger than that forms a
+ * group of its own); 0 = the default (48), -1 = one group (every pass over
+ * the whole batch).  generic: 1 runs every image through the shared-memory
+ * Stockham passes (the path of lengths without a register transform), 0 =
+ * register transforms wherever they apply. */
 typedef struct {
   int32_t row_ctas;
   int32_t col_ctas;
@@ -160,6 +169,8 @@ typedef struct {
   int32_t fft_values;     /* register row transforms: complex values per thread, 16 or 32; 0 = default (16) */
   int32_t col_fft_values; /* the same for the column transforms; 0 = default (32 for power-of-two
                              lengths, 16 for 3 * 2^k and 5 * 2^k) */
+  int32_t l2_group_mb;    /* image groups of the captured loop, MiB of intermediate per group; 0 = 48, -1 = off */
+  int32_t generic;        /* 1: Stockham passes for every image; 0: register transforms where they apply */
 } deconv_tune;
 
 /* Re-lays out a plan for another tuning (t = NULL: the defaults).  The
@@ -169,13 +180,16 @@ typedef struct {
 deconv_status deconv_retune(deconv_plan plan, const deconv_tune *t);
 deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
 
-/* Autotuner: times trial_iters iterations three times (after a fresh solve
- * of y that builds the CUDA graph; the plan's options apply; the fastest
- * repetition counts) under the default tuning and each candidate (row_ctas
- * and col_ctas in {152, 608}, fft_values and col_fft_values in {16, 32}, and
- * for one channel and one row class row_stage in {0, 1}), keeps the fastest
- * (best, best_ms_per_iter: nullable host outputs) and leaves the plan in it
- * with no iteration state.  y: device, batch layout.  Synchronous. */
+/* Autotuner: times trial_iters iterations (rounded up to a whole number of
+ * captured 20-iteration loops) three times (after a fresh solve of y that
+ * builds the CUDA graph; the plan's options apply; the fastest repetition
+ * counts) under the default tuning and each candidate (row_ctas and col_ctas
+ * in {152, 608}, fft_values and col_fft_values in {16, 32}, and for one
+ * channel and one row class row_stage in {0, 1}); then, for a batch, the
+ * image-group budgets l2_group_mb in {-1, 24, 48, 80} on the fastest of
+ * those.  Keeps the fastest (best, best_ms_per_iter: nullable host outputs)
+ * and leaves the plan in it with no iteration state.  y: device, batch
+ * layout.  Synchronous. */
 deconv_status deconv_autotune(deconv_plan plan, const void *y, int32_t trial_iters, deconv_tune *best,
                               float *best_ms_per_iter);
 
@@ -236,15 +250,30 @@ deconv_status deconv_grad(deconv_plan plan, const void *y, const void *x_true, i
  * Arguments are those of deconv_plan_create and deconv_solve (device h,
  * mask, y, x; host dims).  Returns DECONV_ENOMEM, before any launch, when
  * deconv_workspace_size(dims) exceeds 32 MiB (for example a single FP32
- * image up to about 700 x 700).  The first call on a device looks up the
- * array's device address, with that device current; make that first call
- * before any stream capture.  Every call on a device shares the one array
+ * image up to about 700 x 700).  Every call looks up the array's device
+ * address in the current device's context (so it stays valid after a
+ * context is recreated); it synchronises the stream, so make no call while
+ * that stream is being captured.  Every call on a device shares the one array
  * (plan creation clears what must start at zero), so calls whose work
  * overlaps on the GPU (other threads or streams) race: serialise them.
  * Synchronises `stream` and returns device-side errors like deconv_sync. */
 deconv_status deconv_solve_noalloc(const deconv_dims *dims, const void *h, const uint8_t *mask,
                                    const void *y, void *x, double lambda, double mu, int32_t iters,
                                    void *stream);
+
+/* Diagnostic timing inside the captured iteration loop (no counterpart in
+ * the paper).  deconv_set_profiling(plan, 1) makes the plan record a CUDA
+ * event on its stream before and after every column pass and every row pass
+ * of the CUDA graph it replays (the graph is re-captured; 0 turns it off).
+ * After a deconv_solve that replayed the graph, deconv_graph_pass_times
+ * returns, from the events of the last replay, the mean time per iteration
+ * of the column passes (ms_host[0]), of the row passes (ms_host[1]) and of
+ * the whole iteration (ms_host[2]) (HOST array of 3 floats; summed over
+ * image groups).  The events sit between passes, where they replace the
+ * overlap of a pass's launch with the tail of the one before it.
+ * Synchronises the stream.  DECONV_EINVAL if no profiled graph ran. */
+deconv_status deconv_set_profiling(deconv_plan plan, int32_t on);
+deconv_status deconv_graph_pass_times(deconv_plan plan, float *ms_host);
 
 /* Diagnostic timing (no counterpart in the paper): continue from the plan's
  * state for `iters` >= 1 iterations launched one kernel at a time, with a

@@ -42,7 +42,7 @@ EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "decon
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
            "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches",
            "deconv_set_options", "deconv_get_mu", "deconv_fast_shape", "deconv_retune", "deconv_get_tune",
-           "deconv_autotune")
+           "deconv_autotune", "deconv_set_profiling", "deconv_graph_pass_times")
 
 
 class DeconvError(RuntimeError):
@@ -67,7 +67,15 @@ class deconv_options(ctypes.Structure):
 
 class deconv_tune(ctypes.Structure):
     _fields_ = [("row_ctas", ctypes.c_int32), ("col_ctas", ctypes.c_int32), ("row_stage", ctypes.c_int32),
-                ("fft_values", ctypes.c_int32), ("col_fft_values", ctypes.c_int32)]
+                ("fft_values", ctypes.c_int32), ("col_fft_values", ctypes.c_int32),
+                ("l2_group_mb", ctypes.c_int32), ("generic", ctypes.c_int32)]
+
+
+TUNE_FIELDS = tuple(name for name, _ in deconv_tune._fields_)
+
+
+def _tune_dict(t: "deconv_tune") -> dict:
+    return {name: int(getattr(t, name)) for name in TUNE_FIELDS}
 
 
 _lib = None
@@ -87,6 +95,8 @@ def load() -> ctypes.CDLL:
         lib.deconv_solve.argtypes = [vp, vp, vp, i32, i32, vp]
         lib.deconv_solve_host.argtypes = [vp, vp, vp, i32]
         lib.deconv_profile_passes.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
+        lib.deconv_set_profiling.argtypes = [vp, i32]
+        lib.deconv_graph_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.deconv_sync.argtypes = [vp]
         lib.deconv_solve_noalloc.argtypes = [ctypes.POINTER(deconv_dims), vp, vp, vp, vp, dbl, dbl, i32, vp]
         lib.deconv_grad_workspace_size.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
@@ -173,6 +183,18 @@ def deconv_profile_passes(plan: int, iters: int):
     return float(out[0]), float(out[1])
 
 
+def deconv_set_profiling(plan: int, on: bool) -> None:
+    _check(load().deconv_set_profiling(plan, 1 if on else 0), "deconv_set_profiling")
+
+
+def deconv_graph_pass_times(plan: int):
+    """Mean (column passes, row passes, whole iteration) in ms per iteration,
+    from the CUDA events of the last replay of the profiled captured loop."""
+    out = (ctypes.c_float * 3)()
+    _check(load().deconv_graph_pass_times(plan, out), "deconv_graph_pass_times")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
 def deconv_sync(plan: int) -> int:
     """Returns the device-side status (DECONV_OK, DECONV_ENONFINITE, ...)."""
     return load().deconv_sync(plan)
@@ -236,25 +258,23 @@ def deconv_get_mu(plan: int, nimg: int):
 
 
 def deconv_retune(plan: int, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
-                  col_fft_values: int = 0) -> None:
-    t = deconv_tune(int(row_ctas), int(col_ctas), int(row_stage), int(fft_values), int(col_fft_values))
+                  col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0) -> None:
+    t = deconv_tune(int(row_ctas), int(col_ctas), int(row_stage), int(fft_values), int(col_fft_values),
+                    int(l2_group_mb), int(generic))
     _check(load().deconv_retune(plan, ctypes.byref(t)), "deconv_retune")
 
 
 def deconv_get_tune(plan: int) -> dict:
     t = deconv_tune()
     _check(load().deconv_get_tune(plan, ctypes.byref(t)), "deconv_get_tune")
-    return {"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage, "fft_values": t.fft_values,
-            "col_fft_values": t.col_fft_values}
+    return _tune_dict(t)
 
 
 def deconv_autotune(plan: int, y_ptr: int, trial_iters: int = 20):
     """Returns (best tuning as a dict, its ms per iteration)."""
     t, ms = deconv_tune(), ctypes.c_float(0.0)
     _check(load().deconv_autotune(plan, y_ptr, trial_iters, ctypes.byref(t), ctypes.byref(ms)), "deconv_autotune")
-    return ({"row_ctas": t.row_ctas, "col_ctas": t.col_ctas, "row_stage": t.row_stage, "fft_values": t.fft_values,
-            "col_fft_values": t.col_fft_values},
-            float(ms.value))
+    return _tune_dict(t), float(ms.value)
 
 
 def deconv_fast_shape(M: int, N: int, channels: int = 1, ksize: int = 3, dtype: int = DECONV_F32):
@@ -442,8 +462,8 @@ class Plan:
         return best, ms
 
     def retune(self, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
-               col_fft_values: int = 0) -> None:
-        deconv_retune(self.handle, row_ctas, col_ctas, row_stage, fft_values, col_fft_values)
+               col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0) -> None:
+        deconv_retune(self.handle, row_ctas, col_ctas, row_stage, fft_values, col_fft_values, l2_group_mb, generic)
 
     def get_mu(self):
         """Per-image penalty of the next iteration (list of floats)."""
@@ -454,6 +474,12 @@ class Plan:
 
     def profile_passes(self, iters: int):
         return deconv_profile_passes(self.handle, iters)
+
+    def set_profiling(self, on: bool) -> None:
+        deconv_set_profiling(self.handle, on)
+
+    def graph_pass_times(self):
+        return deconv_graph_pass_times(self.handle)
 
     def state_get(self):
         """Opaque device checkpoint of the iteration state (uint8 tensor)."""

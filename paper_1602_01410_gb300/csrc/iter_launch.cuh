@@ -3,8 +3,6 @@
 // register-FFT passes by threads per transform, radix and channel count).
 #pragma once
 
-#include <cstdlib>
-
 #include "iter_kernels.cuh"
 
 namespace dcv {
@@ -55,17 +53,9 @@ static const void *col_ptr(const LaunchCfg &c) {
   return nullptr;
 }
 
-// Programmatic dependent launch of the iteration kernels (DECONV_PDL=0 turns
-// it off): a kernel may start while its predecessor finishes, and waits in
-// griddep_wait() before it touches the state.
-static inline bool pdl_enabled() {
-  static const bool on = [] {
-    const char *v = std::getenv("DECONV_PDL");
-    return !(v && v[0] == '0');
-  }();
-  return on;
-}
-
+// The iteration kernels use programmatic dependent launch: a kernel may
+// start while its predecessor finishes, and waits in griddep_wait() before
+// it touches the state.
 template <typename A>
 static cudaError_t launch_ptr(const void *fn, const A &a, const LaunchCfg &c, cudaStream_t s) {
   if (!fn) return cudaErrorInvalidValue;
@@ -80,7 +70,7 @@ static cudaError_t launch_ptr(const void *fn, const A &a, const LaunchCfg &c, cu
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   lc.attrs = attr;
-  lc.numAttrs = pdl_enabled() ? 1 : 0;
+  lc.numAttrs = 1;
   return cudaLaunchKernelExC(&lc, fn, args);
 }
 
@@ -111,13 +101,22 @@ cudaError_t launch_row_half(const RowArgs<T> &a, const LaunchCfg &c, int half, c
   return launch_ptr(row_ptr<T>(c, half), a, row_half_cfg(c, half), s);
 }
 
-// Opt in to the dynamic shared memory a class needs (above 48 KB).
+// Opt in to the dynamic shared memory a class needs (above 48 KB), with
+// the largest shared-memory carve-out of the SM's unified L1/shared storage:
+// left to itself the driver may pick a carve-out that holds one CTA where
+// the registers would allow two.
+static inline cudaError_t opt_in_smem(const void *fn, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+}
+
 template <typename T>
 cudaError_t prepare_row(const LaunchCfg &c) {
   for (int half = 0; half < (c.kind == KIND_P2 ? 3 : 1); ++half) {
     const void *fn = row_ptr<T>(c, half);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_half_cfg(c, half).smem);
+    cudaError_t e = opt_in_smem(fn, row_half_cfg(c, half).smem);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -130,7 +129,7 @@ cudaError_t prepare_col(const LaunchCfg &c) {
     e.stage = ext;
     const void *fn = col_ptr<T>(e);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    cudaError_t r = opt_in_smem(fn, c.smem);
     if (r != cudaSuccess) return r;
   }
   return cudaSuccess;

@@ -15,35 +15,25 @@
 // calls cudaMalloc, cudaFree, cudaMallocAsync or any allocating library
 // routine, and it launches the iterations directly (in chunks short enough
 // that deconv_solve never instantiates a CUDA graph).
-#include <mutex>
-
 #include "deconv.h"
 
 namespace {
 
 constexpr size_t kScratchBytes = 32u << 20;  // 32 MiB
-constexpr int kMaxDevices = 64;
 constexpr int kChunk = 20;  // deconv_solve replays a graph only for runs longer than this
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device.  In host code the
-// symbol g_scratch names a host-side stand-in, never the device memory, so
-// the address must come from cudaGetSymbolAddress, once per device, with
-// that device current.
+// Device address of g_scratch in the current device's context.  In host
+// code the symbol g_scratch names a host-side stand-in, never the device
+// memory, so the address comes from cudaGetSymbolAddress with the device
+// current.  It is looked up on every call (the lookup is cheap): a cached
+// address would go stale if the context were torn down and recreated
+// (cudaDeviceReset), and a later call would launch on unmapped memory.
 deconv_status scratch_address(void **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DECONV_ECUDA;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return DECONV_ECUDA;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return DECONV_ECUDA;
+  *out = p;
   return DECONV_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 #include <tuple>
@@ -39,14 +40,13 @@ bool factor235(int L, FftSched *sc) {
   return true;
 }
 
-int env_int(const char *name, int dflt) {
-  const char *v = std::getenv(name);
-  return v ? std::atoi(v) : dflt;
-}
+constexpr int kDefaultGroupMiB = 48;      // image-group budget of the captured loop (deconv_tune.l2_group_mb)
 
-// One kernel class of a pass: the images launched together with one kernel.
+// One kernel class of a pass: the images of one image group launched
+// together with one kernel.
 struct Cls {
   LaunchCfg cfg;
+  int group = 0;
   std::vector<int> imgs;
   size_t o_imgs = 0;  // workspace offset of the image list
 };
@@ -54,6 +54,9 @@ struct Cls {
 struct Layout {
   int B = 0, C = 0, K = 0, dtype = 0, nt = 256, kernel_per_image = 0;
   std::vector<Cls> row_cls, col_cls;
+  // Image groups of the captured loop: the row and column classes of each.
+  int ngroups = 1;
+  std::vector<std::vector<int>> grp_row, grp_col;
   std::map<int, int> tw2_off;
   long long total_tw2 = 0;
   int total_row_items = 0;
@@ -215,26 +218,57 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     cols_total += (long long)L.C * (N / 2 + 1);
   }
   const int maxthr = L.esz == 4 ? 512 : 256;
-  const bool allow_p2 = env_int("DECONV_GENERIC", 0) == 0;
+  const bool allow_p2 = !(tune && tune->generic);
   // Kernel class of every image and pass: the register-FFT passes for the
   // lengths reg_fft_params accepts (key tt * 8 + r), the generic Stockham
   // passes otherwise (key 0).
+  // Image groups of the captured loop (first fit, largest intermediate
+  // first): each group's row-spectral intermediate within the budget, so
+  // that it stays in L2 from one pass to the next while the group runs.
+  std::vector<int> grp(L.B, 0);
+  {
+    const int mb = (tune && tune->l2_group_mb != 0) ? tune->l2_group_mb : kDefaultGroupMiB;
+    if (mb > 0) {
+      const long long budget = (long long)mb << 20;
+      std::vector<int> order(L.B);
+      std::vector<long long> sb(L.B);
+      for (int j = 0; j < L.B; ++j) {
+        order[j] = j;
+        sb[j] = (long long)L.C * d->rows[j] * (d->cols[j] / 2 + 1) * 4 * (long long)L.esz;
+      }
+      std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return sb[u] > sb[v]; });
+      std::vector<long long> used;
+      for (int j : order) {
+        size_t g = 0;
+        while (g < used.size() && used[g] + sb[j] > budget) ++g;
+        if (g == used.size()) used.push_back(0);
+        used[g] += sb[j];
+        grp[j] = (int)g;
+      }
+      L.ngroups = (int)used.size();
+    }
+  }
+  // Per-(group, kernel) keys: the kernel key (register-FFT class, 0 =
+  // generic) plus the group times kGroupKey.
+  constexpr int kGroupKey = 4096;
   std::vector<int> row_key(L.B, 0), col_key(L.B, 0);
   long long g_rows = 0, g_cols = 0;
   std::map<int, long long> p2_rows, p2_cols;
+  std::map<int, int> p2_row_keys;  // distinct register row kernels (any group)
   // Values per thread of the power-of-two register transforms: 16 (twice the
   // threads, so twice the resident warps) unless the tuning asks for 32.
   // Defaults (measured on GB300): rows 16; columns 32 for power-of-two
   // lengths, 16 for 3 * 2^k and 5 * 2^k.
-  const int vrow = (tune && tune->fft_values > 0) ? tune->fft_values : env_int("DECONV_FFT_VALUES", 16);
-  const int vcol_set = (tune && tune->col_fft_values > 0) ? tune->col_fft_values : env_int("DECONV_COL_FFT_VALUES", 0);
+  const int vrow = (tune && tune->fft_values > 0) ? tune->fft_values : 16;
+  const int vcol_set = (tune && tune->col_fft_values > 0) ? tune->col_fft_values : 0;
   for (int j = 0; j < L.B; ++j) {
     const int M = d->rows[j], N = d->cols[j];
     int tt, r, v;
     if (allow_p2 && reg_fft_params(N, &tt, &r, &v, vrow) && p2_row_threads(L.C, 1, tt, r) <= maxthr &&
         p2_groups_ok(p2_row_threads(L.C, 1, tt, r), tt) && p2_row_smem(L.C, N, 1, tt, L.esz, r, L.C == 1, v) <= kMaxSmem) {
       row_key[j] = p2_key(v, tt, r);
-      p2_rows[row_key[j]] += M;
+      p2_rows[grp[j] * kGroupKey + row_key[j]] += M;
+      p2_row_keys[row_key[j]] = 1;
     } else {
       g_rows += M;
     }
@@ -242,19 +276,17 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     if (allow_p2 && reg_fft_params(M, &tt, &r, &v, vcol) && p2_col_threads(1, tt, r) <= maxthr &&
         p2_col_smem(M, 1, tt, L.esz, r, v) <= kMaxSmem) {
       col_key[j] = p2_key(v, tt, r);
-      p2_cols[col_key[j]] += (long long)L.C * (N / 2 + 1);
+      p2_cols[grp[j] * kGroupKey + col_key[j]] += (long long)L.C * (N / 2 + 1);
     } else {
       g_cols += (long long)L.C * (N / 2 + 1);
     }
   }
-  const int target = env_int("DECONV_TARGET_CTAS", kTargetCtas);
-  const int rb_pref = env_int("DECONV_ROW_BLOCK", (int)std::max<long long>(2, (g_rows + target - 1) / target));
-  const int w_pref = env_int("DECONV_COL_TILE", (int)std::max<long long>(1, (g_cols + target - 1) / target));
+  const int target = kTargetCtas;
+  const int rb_pref = (int)std::max<long long>(2, (g_rows + target - 1) / target);
+  const int w_pref = (int)std::max<long long>(1, (g_cols + target - 1) / target);
   // Generic CTA size: 256 threads when every generic image fits, else 512 (FP32 only).
-  int nt_req = env_int("DECONV_NT", 0);
-  std::vector<int> cand = nt_req ? std::vector<int>{nt_req} : std::vector<int>{256, 512};
   bool ok = false;
-  for (int nt : cand) {
+  for (int nt : {256, 512}) {
     if (nt != 256 && !(nt == 512 && L.esz == 4)) continue;
     bool all = true;
     for (int j = 0; j < L.B && all; ++j) {
@@ -271,39 +303,36 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
   if (!ok) return DECONV_EUNSUPPORTED;
   // Class parameters: rows per CTA / columns per CTA aiming at one CTA per SM.
   std::map<int, int> p2_rb, p2_w;
-  // One channel and one row class: the forward row half stages its rows (x
+  // One channel and one row kernel: the forward row half stages its rows (x
   // with halo, d, y~) in shared memory.  Otherwise it reads them through L1:
   // the staged rows of three channels would leave room for one row per CTA,
   // and the classes of a batch run concurrently only while their CTAs fit on
   // the SMs side by side.
-  int row_stage =
-      (L.C == 1 && p2_rows.size() == 1 && g_rows == 0) ? env_int("DECONV_ROW_STAGE", 1) : env_int("DECONV_ROW_STAGE", 0);
+  int row_stage = (L.C == 1 && p2_row_keys.size() == 1 && g_rows == 0) ? 1 : 0;
   if (tune && tune->row_stage >= 0) row_stage = L.C == 1 ? (tune->row_stage ? 1 : 0) : 0;
   for (const auto &kv : p2_rows) {
     int v, tt, r;
-    p2_unkey(kv.first, &v, &tt, &r);
+    p2_unkey(kv.first % kGroupKey, &v, &tt, &r);
     const int N = r * v * tt;
-    const int rtarget = (tune && tune->row_ctas > 0) ? tune->row_ctas : env_int("DECONV_P2_ROW_CTAS", 152);
+    const int rtarget = (tune && tune->row_ctas > 0) ? tune->row_ctas : 152;
     int rb = (int)std::max<long long>(1, (kv.second + rtarget - 1) / rtarget);
-    rb = env_int("DECONV_P2_ROW_BLOCK", rb);
     while (rb > 1 && (p2_row_threads(L.C, rb, tt, r) > maxthr || !p2_groups_ok(p2_row_threads(L.C, rb, tt, r), tt) ||
                       p2_row_smem(L.C, N, rb, tt, L.esz, r, row_stage, v) > kMaxSmem))
       --rb;
     p2_rb[kv.first] = rb;
   }
-  int p2w_all = 1;
+  std::vector<int> p2w_all(L.ngroups, 1);
   {
-    long long tot = 0;
-    for (const auto &kv : p2_cols) tot += kv.second;
-    const int ctarget = (tune && tune->col_ctas > 0) ? tune->col_ctas : env_int("DECONV_P2_COL_CTAS", 152);
-    p2w_all = (int)std::max<long long>(1, (tot + ctarget - 1) / ctarget);
-    p2w_all = env_int("DECONV_P2_COL_TILE", p2w_all);
+    std::vector<long long> tot(L.ngroups, 0);
+    for (const auto &kv : p2_cols) tot[kv.first / kGroupKey] += kv.second;
+    const int ctarget = (tune && tune->col_ctas > 0) ? tune->col_ctas : 152;
+    for (int g = 0; g < L.ngroups; ++g) p2w_all[g] = (int)std::max<long long>(1, (tot[g] + ctarget - 1) / ctarget);
   }
   for (const auto &kv : p2_cols) {
     int v, tt, r;
-    p2_unkey(kv.first, &v, &tt, &r);
+    p2_unkey(kv.first % kGroupKey, &v, &tt, &r);
     const int M = r * v * tt;
-    int w = std::min(p2w_all, 16);
+    int w = std::min(p2w_all[kv.first / kGroupKey], 16);
     while (w > 1 && (p2_col_threads(w, tt, r) > maxthr || !p2_groups_ok(p2_col_threads(w, tt, r), tt) ||
                      p2_col_smem(M, w, tt, L.esz, r, v) > kMaxSmem))
       --w;
@@ -311,17 +340,19 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
   }
 
   // Class lists (in order of first appearance).
-  auto class_index = [](std::vector<Cls> &v, int kind, int key) {
+  auto class_index = [](std::vector<Cls> &v, int kind, int key, int group) {
     int vv = 32, tt = 0, r = 0;
     if (kind == KIND_P2) p2_unkey(key, &vv, &tt, &r);
     for (size_t k = 0; k < v.size(); ++k)
-      if (v[k].cfg.kind == kind && v[k].cfg.tt == tt && v[k].cfg.r == r && v[k].cfg.v == vv) return (int)k;
+      if (v[k].group == group && v[k].cfg.kind == kind && v[k].cfg.tt == tt && v[k].cfg.r == r && v[k].cfg.v == vv)
+        return (int)k;
     Cls c;
     std::memset(&c.cfg, 0, sizeof(c.cfg));
     c.cfg.kind = kind;
     c.cfg.v = vv;
     c.cfg.tt = tt;
     c.cfg.r = r;
+    c.group = group;
     v.push_back(c);
     return (int)v.size() - 1;
   };
@@ -338,12 +369,12 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     D.kb = (d->ksizes ? d->ksizes[j] : d->ksize) / 2;
     int grb = 0, gw = 0;
     if (!(row_key[j] && col_key[j])) fit_image(D.M, D.N, L.C, L.nt, L.esz, rb_pref, w_pref, &grb, &gw);
-    D.Rb = row_key[j] ? p2_rb[row_key[j]] : grb;
-    D.W = col_key[j] ? p2_w[col_key[j]] : gw;
+    D.Rb = row_key[j] ? p2_rb[grp[j] * kGroupKey + row_key[j]] : grb;
+    D.W = col_key[j] ? p2_w[grp[j] * kGroupKey + col_key[j]] : gw;
     D.row_blocks = (D.M + D.Rb - 1) / D.Rb;
     D.col_tiles = (D.Nh + D.W - 1) / D.W;
-    Cls &rc = L.row_cls[class_index(L.row_cls, row_key[j] ? KIND_P2 : KIND_GENERIC, row_key[j])];
-    Cls &cc = L.col_cls[class_index(L.col_cls, col_key[j] ? KIND_P2 : KIND_GENERIC, col_key[j])];
+    Cls &rc = L.row_cls[class_index(L.row_cls, row_key[j] ? KIND_P2 : KIND_GENERIC, row_key[j], grp[j])];
+    Cls &cc = L.col_cls[class_index(L.col_cls, col_key[j] ? KIND_P2 : KIND_GENERIC, col_key[j], grp[j])];
     D.row_begin = rc.cfg.grid;
     D.col_begin = cc.cfg.grid;
     rc.cfg.grid += D.row_blocks;
@@ -456,6 +487,10 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     factor235(D.N, &D.sched_row);
     factor235(D.M, &D.sched_col);
   }
+  L.grp_row.assign(L.ngroups, {});
+  L.grp_col.assign(L.ngroups, {});
+  for (size_t k = 0; k < L.row_cls.size(); ++k) L.grp_row[L.row_cls[k].group].push_back((int)k);
+  for (size_t k = 0; k < L.col_cls.size(); ++k) L.grp_col[L.col_cls[k].group].push_back((int)k);
   for (auto &c : L.row_cls) L.row_smem = std::max(L.row_smem, c.cfg.smem);
   for (auto &c : L.col_cls) L.col_smem = std::max(L.col_smem, c.cfg.smem);
   if (L.row_smem > kMaxSmem || L.col_smem > kMaxSmem) return DECONV_EUNSUPPORTED;
@@ -505,7 +540,7 @@ std::vector<deconv_tune> tune_candidates(int channels) {
     for (int cfv : {16, 32})
       for (int st : channels == 1 ? std::vector<int>{0, 1} : std::vector<int>{0})
         for (int rc : {152, 608})
-          for (int cc : {152, 608}) v.push_back(deconv_tune{rc, cc, st, fv, cfv});
+          for (int cc : {152, 608}) v.push_back(deconv_tune{rc, cc, st, fv, cfv, 0, 0});
   return v;
 }
 
@@ -537,6 +572,12 @@ struct deconv_plan_s {
   std::vector<cudaStream_t> fan_side;
   cudaEvent_t fan_fork = nullptr;
   std::vector<cudaEvent_t> fan_join;
+  // In-graph pass timing (deconv_set_profiling): events recorded before the
+  // first pass and after every pass of the captured loop, in order.
+  bool profile = false;
+  bool prof_ran = false;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_kind;  // per interval between consecutive events: 0 column pass, 1 row pass
 
   template <typename P> P *at(size_t off) const { return reinterpret_cast<P *>(ws + off); }
 };
@@ -618,11 +659,12 @@ template <typename T> T *dbuf(deconv_plan_s *p, int which) {
   return p->at<T>(which ? p->L.o_d1 : p->L.o_d0);
 }
 
-// Launches fn(class k, stream) for every class of a pass: on s in order, or,
-// while a graph is captured on fan_main, class k > 0 on side stream k-1
-// (forked from and joined back into s).
+// Launches fn(class k, stream) for the classes `idx` of a pass: on s in
+// order, or, while a graph is captured on fan_main, the n-th class (n > 0)
+// on side stream n-1 (forked from and joined back into s).
 template <typename F>
-cudaError_t each_class(deconv_plan_s *p, cudaStream_t s, size_t n, F fn) {
+cudaError_t each_class(deconv_plan_s *p, cudaStream_t s, const std::vector<int> &idx, F fn) {
+  const size_t n = idx.size();
   const bool fan = n > 1 && s == p->fan_main && p->fan_side.size() + 1 >= n;
   if (fan) {
     cudaError_t e = cudaEventRecord(p->fan_fork, s);
@@ -635,7 +677,7 @@ cudaError_t each_class(deconv_plan_s *p, cudaStream_t s, size_t n, F fn) {
       cudaError_t e = cudaStreamWaitEvent(sk, p->fan_fork, 0);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = fn(k, sk);
+    cudaError_t e = fn((size_t)idx[k], sk);
     if (e != cudaSuccess) return e;
     if (fan && k > 0) {
       e = cudaEventRecord(p->fan_join[k - 1], sk);
@@ -650,13 +692,24 @@ cudaError_t each_class(deconv_plan_s *p, cudaStream_t s, size_t n, F fn) {
   return cudaSuccess;
 }
 
+// Class indices of a pass: those of image group g, or every class (g < 0).
+const std::vector<int> &pass_classes(const deconv_plan_s *p, bool row, int g, std::vector<int> &all) {
+  const Layout &L = p->L;
+  if (g >= 0) return row ? L.grp_row[g] : L.grp_col[g];
+  all.resize(row ? L.row_cls.size() : L.col_cls.size());
+  for (size_t k = 0; k < all.size(); ++k) all[k] = (int)k;
+  return all;
+}
+
 // One iteration (column pass then row pass), d ping-pong by plan parity.
 // tikh > 0: a Tikhonov warm-start step (denominator |H|^2 + tikh, R ignored).
+// g >= 0: the classes of image group g only.
 template <typename T>
-cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s, double tikh = 0.0) {
+cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s, double tikh = 0.0, int g = -1) {
   const auto &cl = p->L.col_cls;
   const int ext = (tikh > 0.0 || p->adapt_t > 0.0) ? 1 : 0;  // the column variant with those terms
-  return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+  std::vector<int> all;
+  return each_class(p, s, pass_classes(p, false, g, all), [&](size_t k, cudaStream_t sk) {
     LaunchCfg c = cl[k].cfg;
     c.stage = ext;
     return launch_col<T>(col_args<T>(p, cl[k], tikh), c, sk);
@@ -668,8 +721,10 @@ cudaError_t col_pass(deconv_plan_s *p, cudaStream_t s, double tikh = 0.0) {
 // spectrum of y~ alone (row_yspec_p2_kernel).
 template <typename T>
 cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, T *d_out, T *x_out,
-                     double *partials, double relax = -1.0) {
+                     double *partials, double relax = -1.0, int g = -1) {
   const auto &cl = p->L.row_cls;
+  std::vector<int> all;
+  const std::vector<int> &idx = pass_classes(p, true, g, all);
   const double rx = relax < 0.0 ? p->relax : relax;
   const bool adapt = p->adapt_t > 0.0;
   auto cfg_of = [&](size_t k) {
@@ -681,7 +736,7 @@ cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, 
     // Penalty adaptation, Eq. (varying_penalty): z-update and residual norms,
     // the per-image rule, then the forward half with mu^{i+1} and d rescaled.
     const Layout &L = p->L;
-    cudaError_t e = each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+    cudaError_t e = each_class(p, s, idx, [&](size_t k, cudaStream_t sk) {
       const LaunchCfg c = cfg_of(k);
       if (c.kind != KIND_P2)
         return launch_row<T>(row_args<T>(p, cl[k], ROW_NORMS, d_in, d_out, x_out, nullptr, rx), c, sk);
@@ -694,14 +749,14 @@ cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, 
     e = launch_mu_update(p->at<ImageDesc>(L.o_desc), L.B, p->at<double>(L.o_apart), mu, mu + L.B, mu + 2 * L.B,
                          p->adapt_t, s);
     if (e != cudaSuccess) return e;
-    return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+    return each_class(p, s, idx, [&](size_t k, cudaStream_t sk) {
       const LaunchCfg c = cfg_of(k);
       const RowArgs<T> a = row_args<T>(p, cl[k], ROW_ITER, d_in, d_out, x_out, partials, rx);
       if (c.kind != KIND_P2) return launch_row<T>(a, c, sk);
       return launch_row_half<T>(a, c, 1, sk);
     });
   }
-  return each_class(p, s, cl.size(), [&](size_t k, cudaStream_t sk) {
+  return each_class(p, s, idx, [&](size_t k, cudaStream_t sk) {
     const RowArgs<T> a = row_args<T>(p, cl[k], mode, d_in, d_out, x_out, partials, rx);
     if (mode == ROW_INNER && cl[k].cfg.kind == KIND_P2) {
       cudaError_t e1 = launch_row_half<T>(a, cfg_of(k), 0, sk);  // z-update
@@ -711,18 +766,34 @@ cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, 
   });
 }
 
+// One iteration of every image (g < 0), or of image group g only (the
+// captured loop; the caller flips the d parity once all groups ran it).
+// prof: record the profiling events between passes (captured loop).
 template <typename T>
-deconv_status iterate(deconv_plan_s *p, cudaStream_t s, T *x_out, double *stats, int iters, int it) {
+deconv_status iterate(deconv_plan_s *p, cudaStream_t s, T *x_out, double *stats, int iters, int it, int g = -1,
+                      bool prof = false) {
   const Layout &L = p->L;
+  auto mark = [&](int kind) -> cudaError_t {
+    if (!prof) return cudaSuccess;
+    const size_t n = p->prof_kind.size() + 1;
+    if (n >= p->prof_ev.size()) return cudaErrorInvalidValue;
+    p->prof_kind.push_back(kind);
+    return cudaEventRecord(p->prof_ev[n], s);
+  };
   // Inner BGS passes: x- and z-steps with v and d (hence the R half of the
   // row-spectral intermediate) held fixed.
   for (int k = 0; k + 1 < p->passes; ++k) {
-    CK(col_pass<T>(p, s));
-    CK(row_pass<T>(p, s, ROW_INNER, nullptr, nullptr, nullptr, nullptr));
+    CK(col_pass<T>(p, s, 0.0, g));
+    CK(mark(0));
+    CK(row_pass<T>(p, s, ROW_INNER, nullptr, nullptr, nullptr, nullptr, -1.0, g));
+    CK(mark(1));
   }
-  CK(col_pass<T>(p, s));
+  CK(col_pass<T>(p, s, 0.0, g));
+  CK(mark(0));
   double *partials = stats ? p->at<double>(L.o_partials) : nullptr;
-  CK(row_pass<T>(p, s, ROW_ITER, dbuf<T>(p, p->parity), dbuf<T>(p, p->parity ^ 1), x_out, partials));
+  CK(row_pass<T>(p, s, ROW_ITER, dbuf<T>(p, p->parity), dbuf<T>(p, p->parity ^ 1), x_out, partials, -1.0, g));
+  CK(mark(1));
+  if (g >= 0) return DECONV_OK;
   p->parity ^= 1;
   if (stats) CK(launch_stats_reduce(p->at<ImageDesc>(L.o_desc), L.B, partials, stats, iters, it, p->at<int>(L.o_err), s));
   return DECONV_OK;
@@ -758,14 +829,27 @@ deconv_status init_state(deconv_plan_s *p, const T *y, T *x_out) {
   return DECONV_OK;
 }
 
+// The captured loop: kGraphIters iterations of every image.  With several
+// image groups (and a fixed penalty: the penalty rule's per-image kernel runs
+// over the whole batch) each group runs all its iterations before the next,
+// so that its intermediate stays in L2 between passes.
 template <typename T>
 deconv_status ensure_graph(deconv_plan_s *p) {
   if (p->gexec) return DECONV_OK;
+  const Layout &L = p->L;
+  const bool grouped = L.ngroups > 1 && !(p->adapt_t > 0.0);
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  const size_t nside = std::max(p->L.row_cls.size(), p->L.col_cls.size()) - 1;
+  size_t nside = 0;
+  if (grouped) {
+    for (int g = 0; g < L.ngroups; ++g)
+      nside = std::max(nside, std::max(L.grp_row[g].size(), L.grp_col[g].size()));
+  } else {
+    nside = std::max(L.row_cls.size(), L.col_cls.size());
+  }
+  nside = nside > 0 ? nside - 1 : 0;
   deconv_status st = DECONV_OK;
-  if (env_int("DECONV_FAN", 1) && nside > 0) {
+  if (nside > 0) {
     if (cudaEventCreateWithFlags(&p->fan_fork, cudaEventDisableTiming) != cudaSuccess) st = DECONV_ECUDA;
     for (size_t k = 0; k < nside && st == DECONV_OK; ++k) {
       cudaStream_t sk = nullptr;
@@ -777,12 +861,37 @@ deconv_status ensure_graph(deconv_plan_s *p) {
     }
     if (st == DECONV_OK) p->fan_main = cs;
   }
+  // Profiling events: one before the loop and one after every pass.
+  for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
+  p->prof_ev.clear();
+  p->prof_kind.clear();
+  p->prof_ran = false;
+  if (p->profile && st == DECONV_OK) {
+    const size_t n = (size_t)kGraphIters * (grouped ? L.ngroups : 1) * 2 * p->passes + 1;
+    for (size_t k = 0; k < n && st == DECONV_OK; ++k) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) st = DECONV_ECUDA;
+      else p->prof_ev.push_back(e);
+    }
+  }
   const int saved = p->parity;
   p->parity = 0;
   cudaGraph_t g = nullptr;
   if (st == DECONV_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     st = DECONV_ECUDA;
-  for (int k = 0; k < kGraphIters && st == DECONV_OK; ++k) st = iterate<T>(p, cs, nullptr, nullptr, 0, 0);
+  const bool prof = p->profile && st == DECONV_OK;
+  if (prof && cudaEventRecord(p->prof_ev[0], cs) != cudaSuccess) st = DECONV_ECUDA;
+  if (grouped) {
+    for (int gi = 0; gi < L.ngroups && st == DECONV_OK; ++gi) {
+      p->parity = 0;
+      for (int k = 0; k < kGraphIters && st == DECONV_OK; ++k) {
+        st = iterate<T>(p, cs, nullptr, nullptr, 0, 0, gi, prof);
+        p->parity ^= 1;
+      }
+    }
+  } else {
+    for (int k = 0; k < kGraphIters && st == DECONV_OK; ++k) st = iterate<T>(p, cs, nullptr, nullptr, 0, 0, -1, prof);
+  }
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   p->parity = saved;
   p->fan_main = nullptr;
@@ -821,6 +930,7 @@ deconv_status run_iters(deconv_plan_s *p, T *x, int iters, double *stats) {
       st = ensure_graph<T>(p);
       if (st != DECONV_OK) return st;
       CK(cudaGraphLaunch(p->gexec, p->stream));
+      p->prof_ran = p->profile;
       remaining -= kGraphIters;
     } else {
       st = iterate<T>(p, p->stream, nullptr, nullptr, 0, 0);
@@ -890,7 +1000,7 @@ deconv_status retune_t(deconv_plan_s *p, const deconv_tune *t) {
   CK(cudaStreamSynchronize(s));
   p->have_state = false;
   p->adapt_ready = false;
-  p->tune = t ? *t : deconv_tune{0, 0, -1, 0, 0};
+  p->tune = t ? *t : deconv_tune{0, 0, -1, 0, 0, 0, 0};
   return DECONV_OK;
 }
 
@@ -1033,7 +1143,7 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
   for (const auto *v : {&L.row_cls, &L.col_cls})
     for (const Cls &c : *v)
       if (c.cfg.kind != KIND_P2 || c.cfg.r != 1) return DECONV_EUNSUPPORTED;  // reverse pass: powers of two only
-  G->v = env_int("DECONV_ADJ_VALUES", 16) == 32 ? 32 : 16;
+  G->v = 16;
   G->k = std::min(k, iters);
   G->nck = (iters + G->k - 1) / G->k;
   const int maxthr = L.esz == 4 ? 512 : 256;
@@ -1258,11 +1368,18 @@ deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes) {
   deconv_status st = build_layout(dims, &L);
   if (st != DECONV_OK) return st;
   size_t total = L.total;
-  // room for every tuning the autotuner tries (they differ in the per-row-block arrays only)
-  for (const deconv_tune &t : tune_candidates(dims->channels)) {
-    Layout Lt;
-    if (build_layout(dims, &Lt, &t) == DECONV_OK) total = std::max(total, Lt.total);
-  }
+  // room for every tuning the autotuner tries and for the generic passes
+  // (they differ in the per-row-block arrays and the class lists only)
+  std::vector<deconv_tune> all = tune_candidates(dims->channels);
+  all.push_back(deconv_tune{0, 0, -1, 0, 0, 0, 0});
+  for (deconv_tune t : all)
+    for (int mb : {-1, 24, 0, 80})
+      for (int gen : {0, 1}) {
+        t.l2_group_mb = mb;
+        t.generic = gen;
+        Layout Lt;
+        if (build_layout(dims, &Lt, &t) == DECONV_OK) total = std::max(total, Lt.total);
+      }
   *bytes = total;
   return DECONV_OK;
 }
@@ -1329,7 +1446,8 @@ deconv_status deconv_retune(deconv_plan p, const deconv_tune *t) {
   if (!p) return DECONV_EINVAL;
   if (t && (t->row_ctas < 0 || t->col_ctas < 0 || t->row_ctas > 65536 || t->col_ctas > 65536 || t->row_stage > 1 ||
             (t->fft_values != 0 && t->fft_values != 16 && t->fft_values != 32) ||
-            (t->col_fft_values != 0 && t->col_fft_values != 16 && t->col_fft_values != 32)))
+            (t->col_fft_values != 0 && t->col_fft_values != 16 && t->col_fft_values != 32) ||
+            t->l2_group_mb < -1 || t->l2_group_mb > 65536 || (t->generic != 0 && t->generic != 1)))
     return DECONV_EINVAL;
   return p->L.dtype == DECONV_F32 ? retune_t<float>(p, t) : retune_t<double>(p, t);
 }
@@ -1344,40 +1462,51 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
                               float *best_ms_per_iter) {
   if (!p || !y || trial_iters < 1 || trial_iters > 100000) return DECONV_EINVAL;
   const bool f32 = p->L.dtype == DECONV_F32;
-  std::vector<deconv_tune> cands;
-  // The staged forward half (188 KB of shared memory per CTA at 1024) keeps
-  // the kernel classes of a batch from running side by side; it is tried for
-  // plans of one row class only.
-  const bool one_class = p->L.row_cls.size() == 1;
-  for (const deconv_tune &t : tune_candidates(p->L.C))
-    if (t.row_stage != 1 || one_class) cands.push_back(t);
-  cands.insert(cands.begin(), deconv_tune{0, 0, -1, 0, 0});  // the defaults
+  // Whole captured loops, so that the image-group schedule is what is timed.
+  const int iters = (trial_iters + kGraphIters - 1) / kGraphIters * kGraphIters + 1;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  deconv_tune bt{0, 0, -1, 0, 0};
+  deconv_tune bt{0, 0, -1, 0, 0, 0, 0};
   float bms = -1.f;
   deconv_status st = DECONV_OK;
-  for (const deconv_tune &t : cands) {
-    if (deconv_retune(p, &t) != DECONV_OK) continue;  // a tuning this plan cannot take
+  auto trial = [&](const deconv_tune &t) {
+    if (deconv_retune(p, &t) != DECONV_OK) return;  // a tuning this plan cannot take
     // fresh solve (builds the CUDA graph), then three timed warm continuations (fastest kept)
-    st = f32 ? solve_t<float>(p, y, nullptr, trial_iters, 0, nullptr) : solve_t<double>(p, y, nullptr, trial_iters, 0, nullptr);
+    st = f32 ? solve_t<float>(p, y, nullptr, iters, 0, nullptr) : solve_t<double>(p, y, nullptr, iters, 0, nullptr);
     float ms = -1.f;
     for (int rep = 0; rep < 3 && st == DECONV_OK; ++rep) {
       if (cudaEventRecord(e0, p->stream) != cudaSuccess) st = DECONV_ECUDA;
       if (st == DECONV_OK)
-        st = f32 ? solve_t<float>(p, nullptr, nullptr, trial_iters, 1, nullptr)
-                 : solve_t<double>(p, nullptr, nullptr, trial_iters, 1, nullptr);
+        st = f32 ? solve_t<float>(p, nullptr, nullptr, iters, 1, nullptr)
+                 : solve_t<double>(p, nullptr, nullptr, iters, 1, nullptr);
       float m = 0.f;
       if (st == DECONV_OK && (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                               cudaEventElapsedTime(&m, e0, e1) != cudaSuccess))
         st = DECONV_ECUDA;
       if (st == DECONV_OK && (ms < 0.f || m < ms)) ms = m;
     }
-    if (st != DECONV_OK) break;
-    if (bms < 0.f || ms < bms) {
+    if (st == DECONV_OK && ms >= 0.f && (bms < 0.f || ms < bms)) {
       bms = ms;
       bt = t;
+    }
+  };
+  // Launch shapes first.  The staged forward half (188 KB of shared memory
+  // per CTA at 1024) keeps the kernel classes of a batch from running side
+  // by side; it is tried for plans of one row class only.
+  const bool one_class = p->L.row_cls.size() == 1;
+  std::vector<deconv_tune> cands{deconv_tune{0, 0, -1, 0, 0, 0, 0}};  // the defaults
+  for (const deconv_tune &t : tune_candidates(p->L.C))
+    if (t.row_stage != 1 || one_class) cands.push_back(t);
+  for (size_t k = 0; k < cands.size() && st == DECONV_OK; ++k) trial(cands[k]);
+  // Then the image-group budget of the captured loop, for a batch.
+  if (st == DECONV_OK && bms >= 0.f && p->L.B > 1 && !(p->adapt_t > 0.0)) {
+    const deconv_tune shape = bt;
+    for (int mb : {-1, 24, 80}) {
+      if (st != DECONV_OK) break;
+      deconv_tune t = shape;
+      t.l2_group_mb = mb;
+      trial(t);
     }
   }
   cudaEventDestroy(e0);
@@ -1387,7 +1516,7 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   st = deconv_retune(p, &bt);
   if (st != DECONV_OK) return st;
   if (best) *best = bt;
-  if (best_ms_per_iter) *best_ms_per_iter = bms / (float)trial_iters;
+  if (best_ms_per_iter) *best_ms_per_iter = bms / (float)iters;
   return DECONV_OK;
 }
 
@@ -1465,6 +1594,35 @@ deconv_status deconv_solve_host(deconv_plan p, const void *y_host, void *x_host,
   return deconv_sync(p);
 }
 
+deconv_status deconv_set_profiling(deconv_plan p, int32_t on) {
+  if (!p || (on != 0 && on != 1)) return DECONV_EINVAL;
+  if ((on != 0) != p->profile && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);  // re-captured with (or without) the events
+    p->gexec = nullptr;
+  }
+  p->profile = on != 0;
+  p->prof_ran = false;
+  return DECONV_OK;
+}
+
+deconv_status deconv_graph_pass_times(deconv_plan p, float *ms_host) {
+  if (!p || !ms_host || !p->profile || !p->prof_ran || p->prof_ev.size() != p->prof_kind.size() + 1)
+    return DECONV_EINVAL;
+  CK(cudaStreamSynchronize(p->stream));
+  double t[2] = {0.0, 0.0};
+  for (size_t k = 0; k < p->prof_kind.size(); ++k) {
+    float m = 0.f;
+    CK(cudaEventElapsedTime(&m, p->prof_ev[k], p->prof_ev[k + 1]));
+    t[p->prof_kind[k]] += m;
+  }
+  float all = 0.f;
+  CK(cudaEventElapsedTime(&all, p->prof_ev.front(), p->prof_ev.back()));
+  ms_host[0] = (float)(t[0] / kGraphIters);
+  ms_host[1] = (float)(t[1] / kGraphIters);
+  ms_host[2] = all / (float)kGraphIters;
+  return DECONV_OK;
+}
+
 deconv_status deconv_profile_passes(deconv_plan p, int32_t iters, float *ms_host) {
   if (!p || iters < 1 || !ms_host || !p->have_state) return DECONV_EINVAL;
   std::vector<cudaEvent_t> ev(4 * (size_t)iters, nullptr);
@@ -1520,6 +1678,7 @@ deconv_status deconv_sync(deconv_plan p) {
 deconv_status deconv_plan_destroy(deconv_plan p) {
   if (!p) return DECONV_EINVAL;
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
   delete p;
   return DECONV_OK;
 }

@@ -13,9 +13,10 @@ def torch_dev():
     return torch, torch.device("cuda:0")
 
 
-def gpu_solve(prob: inputs.Problem, iters=None, stats=False, dtype=None, relax=None, **opts):
+def gpu_solve(prob: inputs.Problem, iters=None, stats=False, dtype=None, relax=None, tune=None, **opts):
     """Returns (list of (C, M, N) float64 arrays, stats array or None, plan).
-    opts: deconv_set_options keywords (bgs_passes, tikh_iters, tikh_tau, adapt_t)."""
+    tune: None or deconv_retune keywords; opts: deconv_set_options keywords
+    (bgs_passes, tikh_iters, tikh_tau, adapt_t)."""
     import paper_1602_01410_gb300 as pkg
     torch, dev = torch_dev()
     dt = dtype or (torch.float32 if prob.dtype == "f32" else torch.float64)
@@ -25,6 +26,8 @@ def gpu_solve(prob: inputs.Problem, iters=None, stats=False, dtype=None, relax=N
     y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=dt, device=dev)
     plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu, channels=prob.channels,
                     relax=prob.relax if relax is None else relax)
+    if tune:
+        plan.retune(**tune)
     if opts:
         plan.set_options(**opts)
     st = torch.zeros((len(prob.shapes), max(iters, 1), 3), dtype=torch.float64, device=dev) if stats else None

@@ -103,5 +103,6 @@ def test_autograd_function():
 
 
 def test_grad_fullsize_differentiation_workload():
+    # measured: loss 6e-5, dlambda 7e-5, dh 4e-4 relative to the FP64 oracle
     prob = inputs.config_c5(count=2)
-    check(prob, prob.iters, 10, 1e-2, ltol=1e-3)
+    check(prob, prob.iters, 10, 2e-3, ltol=1e-3)
