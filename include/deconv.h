@@ -158,8 +158,8 @@ deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
  * before the next, each group's row-spectral intermediate (C x M x (N/2+1)
  * complex pairs per image) at most l2_group_mb MiB so that it stays in the
  * 126 MB L2 from one pass to the next (an image larger than that forms a
- * group of its own); 0 = the default (48), -1 = one group (every pass over
- * the whole batch).  generic: 1 runs every image through the shared-memory
+ * group of its own); 0 = the default, one group (every pass over the whole
+ * batch), as is -1.  generic: 1 runs every image through the shared-memory
  * Stockham passes (the path of lengths without a register transform), 0 =
  * register transforms wherever they apply. */
 typedef struct {
@@ -169,7 +169,7 @@ typedef struct {
   int32_t fft_values;     /* register row transforms: complex values per thread, 16 or 32; 0 = default (16) */
   int32_t col_fft_values; /* the same for the column transforms; 0 = default (32 for power-of-two
                              lengths, 16 for 3 * 2^k and 5 * 2^k) */
-  int32_t l2_group_mb;    /* image groups of the captured loop, MiB of intermediate per group; 0 = 48, -1 = off */
+  int32_t l2_group_mb;    /* image groups of the captured loop, MiB of intermediate per group; 0 or -1 = off */
   int32_t generic;        /* 1: Stockham passes for every image; 0: register transforms where they apply */
 } deconv_tune;
 
@@ -186,7 +186,7 @@ deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
  * counts) under the default tuning and each candidate (row_ctas and col_ctas
  * in {152, 608}, fft_values and col_fft_values in {16, 32}, and for one
  * channel and one row class row_stage in {0, 1}); then, for a batch, the
- * image-group budgets l2_group_mb in {-1, 24, 48, 80} on the fastest of
+ * image-group budgets l2_group_mb in {24, 48, 80} on the fastest of
  * those.  Keeps the fastest (best, best_ms_per_iter: nullable host outputs)
  * and leaves the plan in it with no iteration state.  y: device, batch
  * layout.  Synchronous. */

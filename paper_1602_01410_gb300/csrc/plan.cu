@@ -40,7 +40,7 @@ bool factor235(int L, FftSched *sc) {
   return true;
 }
 
-constexpr int kDefaultGroupMiB = 48;      // image-group budget of the captured loop (deconv_tune.l2_group_mb)
+constexpr int kDefaultGroupMiB = -1;      // image groups of the captured loop by default: none (one group)
 
 // One kernel class of a pass: the images of one image group launched
 // together with one kernel.
@@ -778,7 +778,9 @@ deconv_status iterate(deconv_plan_s *p, cudaStream_t s, T *x_out, double *stats,
     const size_t n = p->prof_kind.size() + 1;
     if (n >= p->prof_ev.size()) return cudaErrorInvalidValue;
     p->prof_kind.push_back(kind);
-    return cudaEventRecord(p->prof_ev[n], s);
+    // External: a timed event record node of the graph (a plain record
+    // during capture only orders the capture's streams)
+    return cudaEventRecordWithFlags(p->prof_ev[n], s, cudaEventRecordExternal);
   };
   // Inner BGS passes: x- and z-steps with v and d (hence the R half of the
   // row-spectral intermediate) held fixed.
@@ -880,7 +882,7 @@ deconv_status ensure_graph(deconv_plan_s *p) {
   if (st == DECONV_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     st = DECONV_ECUDA;
   const bool prof = p->profile && st == DECONV_OK;
-  if (prof && cudaEventRecord(p->prof_ev[0], cs) != cudaSuccess) st = DECONV_ECUDA;
+  if (prof && cudaEventRecordWithFlags(p->prof_ev[0], cs, cudaEventRecordExternal) != cudaSuccess) st = DECONV_ECUDA;
   if (grouped) {
     for (int gi = 0; gi < L.ngroups && st == DECONV_OK; ++gi) {
       p->parity = 0;
@@ -951,20 +953,42 @@ deconv_status solve_t(deconv_plan_s *p, const void *y, void *x, int iters, int w
   return run_iters<T>(p, static_cast<T *>(x), iters, stats);
 }
 
-// Shared-memory opt-in of every kernel variant a plan may launch.
+// Shared-memory opt-in of every kernel variant a plan may launch.  Classes
+// of different image groups can share one kernel (same transform) with
+// different launch shapes: each kernel is opted in once, to the largest
+// shared memory any of its classes launches with.
+std::vector<LaunchCfg> merged_cfgs(const std::vector<Cls> &cls) {
+  std::vector<LaunchCfg> out;
+  for (const Cls &c : cls) {
+    bool found = false;
+    for (LaunchCfg &m : out) {
+      const LaunchCfg &a = c.cfg;
+      if (m.kind == a.kind && m.channels == a.channels && m.tt == a.tt && m.r == a.r && m.v == a.v &&
+          m.stage == a.stage && (a.kind == KIND_P2 || m.nt == a.nt)) {
+        m.smem = std::max(m.smem, a.smem);
+        m.smem_fwd = std::max(m.smem_fwd, a.smem_fwd);
+        found = true;
+        break;
+      }
+    }
+    if (!found) out.push_back(c.cfg);
+  }
+  return out;
+}
+
 template <typename T>
 cudaError_t prepare_all(const Layout &L) {
-  for (const Cls &c : L.row_cls) {
-    cudaError_t e = prepare_row<T>(c.cfg);
-    if (e == cudaSuccess && c.cfg.kind == KIND_P2) {  // the forward half with penalty adaptation
-      LaunchCfg d = c.cfg;
+  for (const LaunchCfg &c : merged_cfgs(L.row_cls)) {
+    cudaError_t e = prepare_row<T>(c);
+    if (e == cudaSuccess && c.kind == KIND_P2) {  // the forward half with penalty adaptation
+      LaunchCfg d = c;
       d.stage = 2;
       e = prepare_row<T>(d);
     }
     if (e != cudaSuccess) return e;
   }
-  for (const Cls &c : L.col_cls) {
-    cudaError_t e = prepare_col<T>(c.cfg);
+  for (const LaunchCfg &c : merged_cfgs(L.col_cls)) {
+    cudaError_t e = prepare_col<T>(c);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1213,8 +1237,16 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
   auto at = [&](size_t off) { return gw + off; };
   CK(cudaMemcpyAsync(at(G.o_adjbeg), G.adj_begin.data(), G.adj_begin.size() * sizeof(int), cudaMemcpyHostToDevice,
                      s));
-  for (size_t c = 0; c < L.row_cls.size(); ++c)
-    CK(prepare_adj<T>(L.desc[L.row_cls[c].imgs[0]].N, G.v, L.C, G.smem[c]));
+  {
+    // one opt-in per adjoint kernel (row length), to the largest shared
+    // memory of the classes (image groups) that launch it
+    std::map<int, size_t> adj_smem_of;
+    for (size_t c = 0; c < L.row_cls.size(); ++c) {
+      size_t &m = adj_smem_of[L.desc[L.row_cls[c].imgs[0]].N];
+      m = std::max(m, G.smem[c]);
+    }
+    for (const auto &kv : adj_smem_of) CK(prepare_adj<T>(kv.first, G.v, L.C, kv.second));
+  }
 
   // 1. Forward with checkpoints of (y~, d, forward spectrum) every k iterations.
   st = init_state<T>(p, static_cast<const T *>(y), nullptr);
@@ -1373,7 +1405,7 @@ deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes) {
   std::vector<deconv_tune> all = tune_candidates(dims->channels);
   all.push_back(deconv_tune{0, 0, -1, 0, 0, 0, 0});
   for (deconv_tune t : all)
-    for (int mb : {-1, 24, 0, 80})
+    for (int mb : {-1, 24, 48, 80})
       for (int gen : {0, 1}) {
         t.l2_group_mb = mb;
         t.generic = gen;
@@ -1502,7 +1534,7 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   // Then the image-group budget of the captured loop, for a batch.
   if (st == DECONV_OK && bms >= 0.f && p->L.B > 1 && !(p->adapt_t > 0.0)) {
     const deconv_tune shape = bt;
-    for (int mb : {-1, 24, 80}) {
+    for (int mb : {24, 48, 80}) {
       if (st != DECONV_OK) break;
       deconv_tune t = shape;
       t.l2_group_mb = mb;

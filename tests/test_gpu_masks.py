@@ -33,10 +33,11 @@ def built():
 
 
 CASES = [
-    # (mask kind, channels, K, sizes): ragged tiles, odd sides, several row blocks
+    # (mask kind, channels, K, sizes): ragged tiles, odd sides, several row
+    # blocks (2-3-5-smooth sides, the sizes the library runs as they are)
     ("crop", 1, 7, [(45, 75), (64, 96)]),
-    ("decim4", 1, 9, [(96, 96), (61, 53), (128, 80)]),
-    ("bayer", 3, 5, [(64, 80), (47, 58)]),
+    ("decim4", 1, 9, [(96, 96), (60, 54), (128, 80)]),
+    ("bayer", 3, 5, [(64, 80), (45, 50)]),
     ("random", 1, 5, [(96, 160), (30, 40)]),
 ]
 
