@@ -238,6 +238,17 @@ deconv_status deconv_grad_workspace_size(deconv_plan plan, int32_t iters, int32_
 deconv_status deconv_grad(deconv_plan plan, const void *y, const void *x_true, int32_t iters, int32_t ckpt_every,
                           void *grad_ws, size_t grad_ws_bytes, double *loss, double *dlambda, void *dh, void *x_out);
 
+/* Vector-Jacobian product of the unrolled iteration (the reverse pass of
+ * deconv_grad with its seed given): for any scalar loss L(x^{iters}) of the
+ * caller's, with xbar = dL/dx^{iters} (device, the batch layout, dtype),
+ * returns dL/dlambda (host double) and dL/dh (device, the shape of h), so
+ * the solve can sit under a loss of the caller's choice (the paper's
+ * parameters lambda and the blur h of Eq. (model1) learned end to end).  Same
+ * workspace, checkpointing, supported sizes and options as deconv_grad;
+ * x_out (nullable) receives x^{iters}.  Synchronises the stream. */
+deconv_status deconv_vjp(deconv_plan plan, const void *y, const void *xbar, int32_t iters, int32_t ckpt_every,
+                         void *grad_ws, size_t grad_ws_bytes, double *dlambda, void *dh, void *x_out);
+
 /* Allocation-free solve (the paper has no counterpart; this is a service of
  * the library).  For callers that may not allocate device memory: code
  * hosted inside a framework that owns the CUDA allocator, latency-critical

@@ -42,7 +42,7 @@ EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "decon
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
            "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches",
            "deconv_set_options", "deconv_get_mu", "deconv_fast_shape", "deconv_retune", "deconv_get_tune",
-           "deconv_autotune", "deconv_set_profiling", "deconv_graph_pass_times")
+           "deconv_autotune", "deconv_set_profiling", "deconv_graph_pass_times", "deconv_vjp")
 
 
 class DeconvError(RuntimeError):
@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
         lib.deconv_grad_workspace_size.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
         lib.deconv_grad.argtypes = [vp, vp, vp, i32, i32, vp, ctypes.c_size_t, ctypes.POINTER(dbl),
                                     ctypes.POINTER(dbl), vp, vp]
+        lib.deconv_vjp.argtypes = [vp, vp, vp, i32, i32, vp, ctypes.c_size_t, ctypes.POINTER(dbl), vp, vp]
         lib.deconv_plan_destroy.argtypes = [vp]
         lib.deconv_status_string.argtypes = [ctypes.c_int]
         lib.deconv_status_string.restype = ctypes.c_char_p
@@ -222,6 +223,15 @@ def deconv_grad(plan: int, y_ptr: int, xtrue_ptr: int, iters: int, ckpt_every: i
     _check(load().deconv_grad(plan, y_ptr, xtrue_ptr, int(iters), int(ckpt_every), gws_ptr, gws_bytes,
                               ctypes.byref(loss), ctypes.byref(dlam), dh_ptr, x_out_ptr), "deconv_grad")
     return loss.value, dlam.value
+
+
+def deconv_vjp(plan: int, y_ptr: int, xbar_ptr: int, iters: int, ckpt_every: int, gws_ptr: int, gws_bytes: int,
+               dh_ptr: int, x_out_ptr: Optional[int] = None) -> float:
+    """dL/dlambda for dL/dx^iters = xbar; dL/dh is written to dh_ptr (device)."""
+    dlam = ctypes.c_double(0)
+    _check(load().deconv_vjp(plan, y_ptr, xbar_ptr, int(iters), int(ckpt_every), gws_ptr, gws_bytes,
+                             ctypes.byref(dlam), dh_ptr, x_out_ptr), "deconv_vjp")
+    return dlam.value
 
 
 def deconv_kernel_launches(plan: int, iters: int, mode: int = 0, ckpt_every: int = 10) -> int:
@@ -433,6 +443,17 @@ class Plan:
                                  dh.data_ptr(), None if x_out is None else x_out.data_ptr())
         return loss, dlam, dh
 
+    def vjp(self, y, xbar, iters: int, ckpt_every: int = 10, x_out=None):
+        """(dL/dlambda, dL/dh) for a loss L with dL/dx^iters = xbar."""
+        torch = self._torch
+        n = deconv_grad_workspace_size(self.handle, iters, ckpt_every)
+        gws = torch.empty(n + 256, dtype=torch.uint8, device=self.workspace.device)
+        gptr = gws.data_ptr() + (-gws.data_ptr()) % 256
+        dh = torch.empty_like(self._h)
+        dlam = deconv_vjp(self.handle, y.data_ptr(), xbar.data_ptr(), iters, ckpt_every, gptr, n, dh.data_ptr(),
+                          None if x_out is None else x_out.data_ptr())
+        return dlam, dh
+
     def set_options(self, bgs_passes: int = 1, tikh_iters: int = 0, tikh_tau: float = 1e-3,
                     adapt_t: float = 0.0) -> None:
         """BGS passes per iteration, Tikhonov warm start, penalty adaptation (see deconv.h)."""
@@ -546,3 +567,56 @@ def _deconv_loss_fn():
 
         _LOSS_FN = _Fn
     return _LOSS_FN
+
+
+class DeconvSolve:
+    """torch.autograd.Function: x^iters of the unrolled partial ADMM as a
+    differentiable function of lambda (0-dim tensor) and the blur kernel h,
+    for any downstream loss.  forward runs the solve; backward runs
+    deconv_vjp with the incoming gradient on x (it recomputes the forward
+    from checkpoints every ckpt_every iterations) and returns dL/dlambda and
+    dL/dh.  y and mask are data (no gradient)."""
+
+    @staticmethod
+    def apply(lam, h, y, mask, shapes, mu: float, iters: int, channels: int = 1, ckpt_every: int = 10,
+              relax: float = 2.0):
+        return _deconv_solve_fn().apply(lam, h, y, mask, tuple(map(tuple, shapes)), mu, iters, channels,
+                                        ckpt_every, relax)
+
+
+_SOLVE_FN = None
+
+
+def _deconv_solve_fn():
+    global _SOLVE_FN
+    if _SOLVE_FN is None:
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, lam, h, y, mask, shapes, mu, iters, channels, ckpt_every, relax):
+                plan = Plan(list(shapes), h.detach(), mask, float(lam), mu, channels=channels, relax=relax)
+                try:
+                    x = plan.solve(y.detach(), iters)
+                    if plan.sync() != DECONV_OK:
+                        raise DeconvError(plan.sync(), "DeconvSolve.forward")
+                    x = x.clone()
+                finally:
+                    plan.close()
+                ctx.save_for_backward(lam.detach(), h.detach(), y.detach(), mask)
+                ctx.cfg = (shapes, mu, iters, channels, ckpt_every, relax)
+                return x
+
+            @staticmethod
+            def backward(ctx, gx):
+                lam, h, y, mask = ctx.saved_tensors
+                shapes, mu, iters, channels, ckpt_every, relax = ctx.cfg
+                plan = Plan(list(shapes), h, mask, float(lam), mu, channels=channels, relax=relax)
+                try:
+                    dlam, dh = plan.vjp(y, gx.contiguous().to(h.dtype), iters, ckpt_every)
+                finally:
+                    plan.close()
+                return (torch.tensor(dlam, dtype=h.dtype, device=h.device), dh) + (None,) * 8
+
+        _SOLVE_FN = _Fn
+    return _SOLVE_FN

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
       a.ybar[rowp + p] = obs ? yb : -(relax - T(1)) * yb;
       T xb;
       if (start) {
-        xb = a.lscale * (a.xs[rowp + p] - a.xtrue[rowp + p]);
+        xb = a.xseed ? a.xseed[rowp + p] : a.lscale * (a.xs[rowp + p] - a.xtrue[rowp + p]);
         abo[rowp + p] = mk<T>(T(0), T(0));
       } else {
         // ab_j for channel ch at the points pt = 0: (i, p), 1: (i, p-1), 2: (i-1, p).

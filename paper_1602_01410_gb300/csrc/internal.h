@@ -140,7 +140,8 @@ template <typename T> struct AdjArgs {
   T *ybar;               // in: yb of step j+1 (after C_{j+1}'s T~bb); out: yb'_j
   const T *xs;           // x_{j+1}
   const T *ds;           // d_j pairs
-  const T *xtrue;        // ADJ_START: ground truth for dL/dx
+  const T *xtrue;        // ADJ_START: ground truth for dL/dx (loss = mean squared error)
+  const T *xseed;        // ADJ_START, nullable: dL/dx^{iters} given by the caller (replaces xtrue)
   const uint32_t *mask;
   const void *tw2;
   cpair<T> *S_out;       // row spectra of tb + i xb

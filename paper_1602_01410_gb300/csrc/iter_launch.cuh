@@ -101,14 +101,12 @@ cudaError_t launch_row_half(const RowArgs<T> &a, const LaunchCfg &c, int half, c
   return launch_ptr(row_ptr<T>(c, half), a, row_half_cfg(c, half), s);
 }
 
-// Opt in to the dynamic shared memory a class needs (above 48 KB), with
-// the largest shared-memory carve-out of the SM's unified L1/shared storage:
-// left to itself the driver may pick a carve-out that holds one CTA where
-// the registers would allow two.
+// Opt in to the dynamic shared memory a class needs (above 48 KB).  The
+// shared-memory carve-out is left to the driver, which sizes it for the
+// occupancy the other limits allow and leaves the rest to L1 (the forward
+// row half reads its neighbours' rows through L1).
 static inline cudaError_t opt_in_smem(const void *fn, size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <typename T>

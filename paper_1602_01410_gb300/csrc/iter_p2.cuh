@@ -102,6 +102,15 @@ __device__ __forceinline__ void fft_reg(cx<T> (&v)[V], bool active, cx<T> *tile,
   }
 }
 
+// Register cap of the row kernels: three-channel FP32 rows with 16 values
+// per thread (3 R TT threads per pixel row) are held to 72 registers for
+// R = 3, 5 (so that three 288-thread CTAs fit one SM's 64 K registers) and
+// to 96 for R = 1 (two CTAs of two 1024-point rows; tighter caps spill).
+// (The inverse half and the y~ spectrum need fewer: 64 for R = 1.)
+template <typename T, int C, int R, int V, bool FWD = true> __host__ __device__ constexpr int row_reg_cap() {
+  return (C == 3 && V == 16 && sizeof(T) == 4) ? (R == 1 ? (FWD ? 96 : 64) : 72) : (sizeof(T) == 4 ? 128 : 255);
+}
+
 // All three kernels below handle L = R * 32 * TT (R in {1, 3, 5}): a
 // transform of length L is done by R groups of TT threads (fft_mixed); with
 // R = 1 it is fft_p2 alone.  Work item layout: group g of a CTA serves
@@ -118,7 +127,7 @@ __device__ __forceinline__ void fft_reg(cx<T> (&v)[V], bool active, cx<T> *tile,
 // Shared memory: [one region of R transpose tiles per (channel, row), which
 // the R groups also use as their exchange buffer][y~ C x Rb x N][mask words].
 template <typename T, int TT, int C, int R, int V>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(RowArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_reg_cap<T, C, R, V, false>())) row_inv_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, RS = R * GS;
   const int wi = blockIdx.x;
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_inv_p2_kernel(
 // is kept).  Same CTA layout as the inverse half; shared memory: one region
 // of R transpose tiles per (channel, row).
 template <typename T, int TT, int C, int R, int V>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kernel(RowArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_reg_cap<T, C, R, V, false>())) row_yspec_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, RS = R * GS;
   const int wi = blockIdx.x;
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_yspec_p2_kerne
 // holds y~ + i r, then the transpose tiles and the exchange buffer, then the
 // transformed row.
 template <typename T, int TT, int C, int R, bool ADAPT, int V>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_kernel(RowArgs<T> a) {
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_reg_cap<T, C, R, V>())) row_fwd_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, RS = R * GS;
   const int wi = blockIdx.x;

@@ -1225,8 +1225,11 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
 }
 
 template <typename T>
+// x_true: the loss is the mean squared error of x^{iters} against it; or
+// xseed (x_true NULL): dL/dx^{iters} is given (a vector-Jacobian product;
+// no loss is computed, loss_h receives 0).
 deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int iters, int k, char *gw,
-                     double *loss_h, double *dlambda_h, void *dh, void *x_out) {
+                     double *loss_h, double *dlambda_h, void *dh, void *x_out, const void *xseed = nullptr) {
   const Layout &L = p->L;
   GradLayout G;
   deconv_status st = grad_layout(p, iters, k, &G);
@@ -1265,10 +1268,14 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
   CK(cudaMemcpyAsync(at(G.o_xK), p->ws + L.o_xbuf, px, cudaMemcpyDeviceToDevice, s));
   if (x_out) CK(cudaMemcpyAsync(x_out, p->ws + L.o_xbuf, px, cudaMemcpyDeviceToDevice, s));
   const long long npx = L.total_px;
-  CK(launch_sqerr<T>(reinterpret_cast<const T *>(at(G.o_xK)), static_cast<const T *>(x_true), npx,
-                     reinterpret_cast<double *>(at(G.o_lpart)), kLossBlocks, s));
   double *res = reinterpret_cast<double *>(at(G.o_res));
-  CK(launch_sum(reinterpret_cast<const double *>(at(G.o_lpart)), kLossBlocks, 1.0 / (double)npx, res, s));
+  if (x_true) {
+    CK(launch_sqerr<T>(reinterpret_cast<const T *>(at(G.o_xK)), static_cast<const T *>(x_true), npx,
+                       reinterpret_cast<double *>(at(G.o_lpart)), kLossBlocks, s));
+    CK(launch_sum(reinterpret_cast<const double *>(at(G.o_lpart)), kLossBlocks, 1.0 / (double)npx, res, s));
+  } else {
+    CK(cudaMemsetAsync(res, 0, sizeof(double), s));
+  }
 
   // 2. Reverse sweep, one checkpoint segment at a time.
   CK(cudaMemsetAsync(res + 1, 0, 3 * sizeof(double), s));
@@ -1324,6 +1331,7 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
         aa.xs = start ? reinterpret_cast<const T *>(at(G.o_xK)) : reinterpret_cast<const T *>(at(G.o_segX) + jj * px);
         aa.ds = reinterpret_cast<const T *>(at(G.o_segD) + 2 * jj * px);
         aa.xtrue = static_cast<const T *>(x_true);
+        aa.xseed = static_cast<const T *>(xseed);
         aa.mask = p->at<uint32_t>(L.o_bits);
         aa.tw2 = p->ws + L.o_tw2;
         aa.S_out = reinterpret_cast<cpair<T> *>(at(G.o_Sr0));
@@ -1390,6 +1398,23 @@ extern "C" deconv_status deconv_grad(deconv_plan p, const void *y, const void *x
              ? grad_t<float>(p, y, x_true, iters, ckpt_every, static_cast<char *>(grad_ws), loss, dlambda, dh, x_out)
              : grad_t<double>(p, y, x_true, iters, ckpt_every, static_cast<char *>(grad_ws), loss, dlambda, dh,
                               x_out);
+}
+
+extern "C" deconv_status deconv_vjp(deconv_plan p, const void *y, const void *xbar, int32_t iters,
+                                    int32_t ckpt_every, void *grad_ws, size_t grad_ws_bytes, double *dlambda,
+                                    void *dh, void *x_out) {
+  if (!p || !y || !xbar || !grad_ws || !dlambda || !dh) return DECONV_EINVAL;
+  if (reinterpret_cast<uintptr_t>(grad_ws) % kAlign != 0) return DECONV_EINVAL;
+  GradLayout G;
+  deconv_status st = grad_layout(p, iters, ckpt_every, &G);
+  if (st != DECONV_OK) return st;
+  if (grad_ws_bytes < G.total) return DECONV_ENOMEM;
+  double loss = 0.0;
+  return p->L.dtype == DECONV_F32
+             ? grad_t<float>(p, y, nullptr, iters, ckpt_every, static_cast<char *>(grad_ws), &loss, dlambda, dh,
+                             x_out, xbar)
+             : grad_t<double>(p, y, nullptr, iters, ckpt_every, static_cast<char *>(grad_ws), &loss, dlambda, dh,
+                              x_out, xbar);
 }
 
 extern "C" {

@@ -106,3 +106,83 @@ def test_grad_fullsize_differentiation_workload():
     # measured: loss 6e-5, dlambda 7e-5, dh 4e-4 relative to the FP64 oracle
     prob = inputs.config_c5(count=2)
     check(prob, prob.iters, 10, 2e-3, ltol=1e-3)
+
+
+# ------------------------------------------- vector-Jacobian product ---
+
+def _tensors(prob):
+    import torch
+    dev = torch.device("cuda:0")
+    h = torch.tensor(prob.h, dtype=torch.float32, device=dev)
+    mask = torch.tensor(np.concatenate([m.ravel() for m in prob.mask]), dtype=torch.uint8, device=dev)
+    y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=torch.float32, device=dev)
+    return h, mask, y
+
+
+def test_vjp_against_central_differences_of_the_oracle():
+    # L(lambda, h) = <w, x^iters> for a random w: dL/dx = w.  The GPU reverse
+    # pass seeded with w against central differences of the FP64 oracle's
+    # forward pass, in lambda and along a random direction of h.
+    import torch
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(55, [(64, 64), (48, 80)], 5, mask_kind="random", frac=0.3, iters=5, lam=2e-3,
+                                 mu=2e-2)
+    iters = 5
+    rng = np.random.default_rng(55)
+    ws = [rng.standard_normal(a.shape).astype(np.float32).astype(np.float64) for a in prob.y]
+
+    def L(lam, h):
+        return sum(float(np.sum(w * oracle.admm(prob.y[j], prob.mask[j], h, lam, prob.mu, iters, relax=prob.relax)[0]))
+                   for j, w in enumerate(ws))
+
+    h, mask, y = _tensors(prob)
+    plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu)
+    wflat = torch.tensor(np.concatenate([w.ravel() for w in ws]), dtype=torch.float32, device=y.device)
+    dlam, dh = plan.vjp(y, wflat, iters, 2)
+    assert plan.sync() == 0
+    plan.close()
+    dh = dh.double().cpu().numpy()
+    eps = 1e-7
+    fd_lam = (L(prob.lam + eps, prob.h) - L(prob.lam - eps, prob.h)) / (2 * eps)
+    U = rng.standard_normal(prob.h.shape)
+    fd_h = (L(prob.lam, prob.h + eps * U) - L(prob.lam, prob.h - eps * U)) / (2 * eps)
+    print(f"vjp: dlambda {dlam:.6e} vs FD {fd_lam:.6e}; <dh, U> {np.sum(dh * U):.6e} vs FD {fd_h:.6e}")
+    assert abs(dlam - fd_lam) <= 2e-3 * abs(fd_lam)
+    assert abs(np.sum(dh * U) - fd_h) <= 2e-3 * np.sum(np.abs(dh * U))
+
+
+def test_vjp_with_the_squared_error_seed_equals_deconv_grad():
+    import torch
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(56, [(64, 128)], 7, mask_kind="random", frac=0.2, iters=6, lam=1e-3, mu=2e-2)
+    h, mask, y = _tensors(prob)
+    xt = torch.tensor(np.concatenate([a.ravel() for a in prob.x_true]), dtype=torch.float32, device=y.device)
+    plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu)
+    x = torch.empty_like(y)
+    loss, dlam_g, dh_g = plan.grad(y, xt, 6, 3, x_out=x)
+    seed = (x - xt) * np.float32(2.0 / x.numel())
+    dlam_v, dh_v = plan.vjp(y, seed, 6, 3)
+    assert plan.sync() == 0
+    plan.close()
+    assert abs(dlam_v - dlam_g) <= 1e-5 * abs(dlam_g)
+    assert torch.max(torch.abs(dh_v - dh_g)) <= 1e-5 * torch.max(torch.abs(dh_g))
+
+
+def test_deconv_solve_autograd_under_another_loss():
+    # a loss the library does not compute itself (weighted L1 of x): the
+    # autograd function's gradients equal the VJP with that loss's dL/dx
+    import torch
+    import paper_1602_01410_gb300 as pkg
+    prob = inputs.random_problem(57, [(64, 64)], 5, mask_kind="random", frac=0.3, iters=4, lam=2e-3, mu=2e-2)
+    h, mask, y = _tensors(prob)
+    lam = torch.tensor(prob.lam, dtype=torch.float32, device=y.device, requires_grad=True)
+    hp = h.clone().requires_grad_(True)
+    wt = torch.linspace(0.5, 1.5, y.numel(), device=y.device)
+    x = pkg.DeconvSolve.apply(lam, hp, y, mask, prob.shapes, prob.mu, 4)
+    loss = (wt * torch.abs(x - 0.5)).sum()
+    loss.backward()
+    plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu)
+    dlam, dh = plan.vjp(y, (wt * torch.sign(x.detach() - 0.5)).contiguous(), 4, 10)
+    plan.close()
+    assert abs(float(lam.grad) - dlam) <= 1e-5 * abs(dlam)
+    assert torch.max(torch.abs(hp.grad - dh)) <= 1e-5 * torch.max(torch.abs(dh))
