@@ -361,6 +361,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch tuning (the autotuner runs at plan set-up, outside the timing)")
     ap.add_argument("--tune-iters", type=int, default=30)
+    ap.add_argument("--tune", type=str, default="",
+                    help="a launch tuning as JSON (deconv_retune keywords) instead of the autotuner (profiling runs)")
     ap.add_argument("--images", type=str, default="",
                     help="comma-separated image indices of the batch to keep (small profiling cases)")
     ap.add_argument("--timed-only", action="store_true",
@@ -416,7 +418,12 @@ def main():
     mask = torch.tensor(mask_np, dtype=torch.uint8, device=dev)
     y = torch.tensor(y_np, dtype=dt, device=dev)
     stream = torch.cuda.Stream(device=dev)
+    pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu, channels=prob.channels, stream=stream).close()  # warm-up
+    torch.cuda.synchronize(dev)
+    t_plan = time.perf_counter()
     plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu, channels=prob.channels, stream=stream)
+    torch.cuda.synchronize(dev)
+    plan_ms = (time.perf_counter() - t_plan) * 1e3
     x = torch.empty_like(y)
     px = prob.pixels()
     f_unobs = float(1.0 - mask_np.mean())
@@ -432,7 +439,10 @@ def main():
             raise SystemExit("the gradient workload runs the default iteration only")
         plan.set_options(*options)
     tune = None
-    if not args.no_autotune:  # timed on the forward iteration (the gradient step reuses its passes)
+    if args.tune:
+        tune = json.loads(args.tune)
+        plan.retune(**tune)
+    elif not args.no_autotune:  # timed on the forward iteration (the gradient step reuses its passes)
         with torch.cuda.stream(stream):
             tune, _ = plan.autotune(y, args.tune_iters)
     if grad_mode:
@@ -488,7 +498,8 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": "Mpx*iter/s", "value": value, "unit": "Mpx*iter/s", "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-                              "config": {"workload": args.config, "iterations": prob.iters},
+                              "config": {"workload": args.config, "iterations": prob.iters,
+                                         "tune": tune if tune is not None else "default launch tuning"},
                               "clocks": clk, "timed_only": True}))
         plan.close()
         if world > 1:
@@ -572,6 +583,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if esz == 8 else "f32", "data": "synthetic (seeded generator)",
         "config": {"workload": f"{args.config}: {WORKLOADS[args.config]}",
                    "pixels_per_iter": px, "iterations": prob.iters,
+                   "plan_create_ms": plan_ms,
                    "l2": "flushed before every timed step (512 MB write); the plan's "
                          f"{plan.workspace_bytes / 2**20:.0f} MB workspace is reused across the step's iterations",
                    "parallelism": ("images sharded across ranks" if sharded else "replicas") if world > 1

@@ -161,7 +161,11 @@ deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
  * group of its own); 0 = the default, one group (every pass over the whole
  * batch), as is -1.  generic: 1 runs every image through the shared-memory
  * Stockham passes (the path of lengths without a register transform), 0 =
- * register transforms wherever they apply. */
+ * register transforms wherever they apply.  fused_rows: 0 runs the row pass
+ * of a plain iteration as two kernels (inverse half, forward half); 1 runs
+ * it (one BGS pass, fixed mu, no statistics) as one fused kernel that takes
+ * its row blocks from a work queue in order and waits, with a bound
+ * (deconv_set_wait_limit), for the x rows of the blocks above it. */
 typedef struct {
   int32_t row_ctas;
   int32_t col_ctas;
@@ -171,7 +175,18 @@ typedef struct {
                              lengths, 16 for 3 * 2^k and 5 * 2^k) */
   int32_t l2_group_mb;    /* image groups of the captured loop, MiB of intermediate per group; 0 or -1 = off */
   int32_t generic;        /* 1: Stockham passes for every image; 0: register transforms where they apply */
+  int32_t fused_rows;     /* 0: two row kernels; 1: the fused row pass for plain iterations */
 } deconv_tune;
+
+/* Bound of every device-side wait, in nanoseconds (default 2e9; the paper
+ * has no counterpart).  The fused row pass (deconv_tune.fused_rows) waits for flags of earlier work
+ * items of the same image; a wait that reaches the bound makes its item set
+ * an error word and return without its forward half, and deconv_sync then
+ * returns DECONV_ETIMEOUT (the results of that call are not valid).  0
+ * allows no waiting at all: any item that depends on another fails at once
+ * (a test of the error path).  The captured CUDA graph is rebuilt.  ns >= 0,
+ * else DECONV_EINVAL. */
+deconv_status deconv_set_wait_limit(deconv_plan plan, int64_t ns);
 
 /* Re-lays out a plan for another tuning (t = NULL: the defaults).  The
  * workspace of deconv_workspace_size() holds every tuning deconv_autotune
@@ -187,7 +202,8 @@ deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
  * in {152, 608}, fft_values and col_fft_values in {16, 32}, and for one
  * channel and one row class row_stage in {0, 1}); then, for a batch, the
  * image-group budgets l2_group_mb in {24, 48, 80} on the fastest of
- * those.  Keeps the fastest (best, best_ms_per_iter: nullable host outputs)
+ * those, and the fused row pass (fused_rows = 1) on the fastest so far.
+ * Keeps the fastest (best, best_ms_per_iter: nullable host outputs)
  * and leaves the plan in it with no iteration state.  y: device, batch
  * layout.  Synchronous. */
 deconv_status deconv_autotune(deconv_plan plan, const void *y, int32_t trial_iters, deconv_tune *best,

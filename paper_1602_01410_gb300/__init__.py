@@ -42,7 +42,8 @@ EXPORTS = ("deconv_workspace_size", "deconv_plan_create", "deconv_solve", "decon
            "deconv_solve_noalloc", "deconv_grad_workspace_size", "deconv_grad", "deconv_last_error",
            "deconv_state_bytes", "deconv_state_get", "deconv_state_set", "deconv_kernel_launches",
            "deconv_set_options", "deconv_get_mu", "deconv_fast_shape", "deconv_retune", "deconv_get_tune",
-           "deconv_autotune", "deconv_set_profiling", "deconv_graph_pass_times", "deconv_vjp")
+           "deconv_autotune", "deconv_set_profiling", "deconv_graph_pass_times", "deconv_vjp",
+           "deconv_set_wait_limit")
 
 
 class DeconvError(RuntimeError):
@@ -68,7 +69,7 @@ class deconv_options(ctypes.Structure):
 class deconv_tune(ctypes.Structure):
     _fields_ = [("row_ctas", ctypes.c_int32), ("col_ctas", ctypes.c_int32), ("row_stage", ctypes.c_int32),
                 ("fft_values", ctypes.c_int32), ("col_fft_values", ctypes.c_int32),
-                ("l2_group_mb", ctypes.c_int32), ("generic", ctypes.c_int32)]
+                ("l2_group_mb", ctypes.c_int32), ("generic", ctypes.c_int32), ("fused_rows", ctypes.c_int32)]
 
 
 TUNE_FIELDS = tuple(name for name, _ in deconv_tune._fields_)
@@ -96,6 +97,7 @@ def load() -> ctypes.CDLL:
         lib.deconv_solve_host.argtypes = [vp, vp, vp, i32]
         lib.deconv_profile_passes.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_float)]
         lib.deconv_set_profiling.argtypes = [vp, i32]
+        lib.deconv_set_wait_limit.argtypes = [vp, ctypes.c_int64]
         lib.deconv_graph_pass_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
         lib.deconv_sync.argtypes = [vp]
         lib.deconv_solve_noalloc.argtypes = [ctypes.POINTER(deconv_dims), vp, vp, vp, vp, dbl, dbl, i32, vp]
@@ -184,6 +186,10 @@ def deconv_profile_passes(plan: int, iters: int):
     return float(out[0]), float(out[1])
 
 
+def deconv_set_wait_limit(plan: int, ns: int) -> None:
+    _check(load().deconv_set_wait_limit(plan, int(ns)), "deconv_set_wait_limit")
+
+
 def deconv_set_profiling(plan: int, on: bool) -> None:
     _check(load().deconv_set_profiling(plan, 1 if on else 0), "deconv_set_profiling")
 
@@ -268,9 +274,9 @@ def deconv_get_mu(plan: int, nimg: int):
 
 
 def deconv_retune(plan: int, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
-                  col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0) -> None:
+                  col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0, fused_rows: int = 0) -> None:
     t = deconv_tune(int(row_ctas), int(col_ctas), int(row_stage), int(fft_values), int(col_fft_values),
-                    int(l2_group_mb), int(generic))
+                    int(l2_group_mb), int(generic), int(fused_rows))
     _check(load().deconv_retune(plan, ctypes.byref(t)), "deconv_retune")
 
 
@@ -483,8 +489,12 @@ class Plan:
         return best, ms
 
     def retune(self, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
-               col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0) -> None:
-        deconv_retune(self.handle, row_ctas, col_ctas, row_stage, fft_values, col_fft_values, l2_group_mb, generic)
+               col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0, fused_rows: int = 0) -> None:
+        deconv_retune(self.handle, row_ctas, col_ctas, row_stage, fft_values, col_fft_values, l2_group_mb, generic,
+                      fused_rows)
+
+    def set_wait_limit(self, ns: int) -> None:
+        deconv_set_wait_limit(self.handle, ns)
 
     def get_mu(self):
         """Per-image penalty of the next iteration (list of floats)."""

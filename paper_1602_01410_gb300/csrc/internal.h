@@ -26,6 +26,7 @@ struct ImageDesc {
   long long hhat;        // first complex of the image's H^ half-spectrum
   long long mask;        // first 32-bit word of the image's packed mask
   long long mask_plane;  // words per channel plane
+  long long halo;        // first element of the image's halo row (C x N: x of row M - 1, fused row pass)
   int tw_row, tw_col;    // twiddle-table offsets for lengths N and M
   int s2_row, s2_col;    // 4 sin^2(pi k / L) table offsets for N and M
   int tw2_row, tw2_col;  // [k1][t] twiddle-table offsets of the power-of-two (sub-)length, -1 if none
@@ -75,6 +76,14 @@ template <typename T> struct RowArgs {
   double lam64;           // lambda in double (tau = lambda / mu per image)
   double *partials;       // nullable: per work item [3] = sum dd^2, dz^2, J
   int *err;
+  // Fused row pass (row_fused_p2_kernel): the class's ticket counter and
+  // one flag per work item, the halo rows, the items of one launch and the
+  // bound of every wait in nanoseconds.
+  unsigned long long *ticket;
+  unsigned *flags;
+  T *halo;
+  int items;
+  long long wait_ns;
 };
 
 template <typename T> struct ColArgs {
@@ -112,6 +121,7 @@ struct LaunchCfg {
   int grid;      // CTAs
   size_t smem;   // dynamic shared memory per CTA
   size_t smem_fwd;  // KIND_P2 rows: the forward half's (smem is the inverse half's)
+  int fused;        // KIND_P2 rows: plain iterations run the fused row pass (one kernel)
 };
 
 // Kernel launchers (kernels_*.cu).
@@ -170,10 +180,14 @@ struct HhatJob {          // one half-spectrum to compute
   int M, N, Nh, K;
   long long out;          // complex offset in hhat
   long long h;            // element offset of the kernel
+  long long g;            // offset of the job's K x Nh row sums in the double2 scratch
 };
+// Row sums into G (total_g double2 over all jobs, g_begin per job), then the
+// half-spectra (total elements, job_begin per job).
 template <typename T>
 cudaError_t launch_hhat(const HhatJob *jobs_dev, int njobs, long long total, const T *h, void *hhat,
-                        const long long *job_begin_dev, cudaStream_t s);
+                        const long long *job_begin_dev, const long long *g_begin_dev, long long total_g, void *G,
+                        cudaStream_t s);
 cudaError_t launch_pack_mask(const ImageDesc *desc_dev, int nimg, long long total_words,
                              const long long *img_word_begin_dev, const uint8_t *mask, uint32_t *bits,
                              cudaStream_t s);

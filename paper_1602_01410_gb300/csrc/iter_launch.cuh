@@ -14,7 +14,7 @@ template <typename T> constexpr int kMaxNt = sizeof(T) == 4 ? 512 : 256;
 // one translation unit per (type, R) (p2_tables.cuh), which compile in
 // parallel.  half 0: inverse half, 1: forward half (stage 0 reads through
 // L1, 1 stages its rows (one channel), 2 adds penalty adaptation), 2: the y~
-// spectrum of an inner pass.
+// spectrum of an inner pass, 3: the fused row pass of a plain iteration.
 template <typename T, int R> const void *p2_row_kernel(int C, int tt, int v, int half, int stage);
 template <typename T, int R> const void *p2_col_kernel(int tt, int v, int ext);
 
@@ -74,7 +74,8 @@ static cudaError_t launch_ptr(const void *fn, const A &a, const LaunchCfg &c, cu
   return cudaLaunchKernelExC(&lc, fn, args);
 }
 
-// The configuration of one half of a register-FFT row pass (its own shared memory size).
+// The configuration of one half of a register-FFT row pass (its own shared
+// memory size; the fused pass uses the inverse half's).
 static inline LaunchCfg row_half_cfg(const LaunchCfg &c, int half) {
   LaunchCfg h = c;
   if (c.kind == KIND_P2 && half == 1) h.smem = c.smem_fwd;
@@ -93,7 +94,8 @@ cudaError_t launch_col(const ColArgs<T> &a, const LaunchCfg &c, cudaStream_t s) 
   return launch_ptr(col_ptr<T>(c), a, c, s);
 }
 
-// One half of a power-of-two row pass (0: inverse, 1: forward).  Kernels are
+// One half of a power-of-two row pass (0: inverse, 1: forward, 2: y~
+// spectrum, 3: the fused pass).  Kernels are
 // launched from the translation unit that opted them in to their shared
 // memory (each unit instantiates its own copy of a kernel template).
 template <typename T>
@@ -111,7 +113,7 @@ static inline cudaError_t opt_in_smem(const void *fn, size_t smem) {
 
 template <typename T>
 cudaError_t prepare_row(const LaunchCfg &c) {
-  for (int half = 0; half < (c.kind == KIND_P2 ? 3 : 1); ++half) {
+  for (int half = 0; half < (c.kind == KIND_P2 ? 4 : 1); ++half) {
     const void *fn = row_ptr<T>(c, half);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = opt_in_smem(fn, row_half_cfg(c, half).smem);

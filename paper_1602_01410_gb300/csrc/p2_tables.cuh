@@ -4,6 +4,7 @@
 // opt-in and the launch go through the same function pointer).
 #pragma once
 
+#include "iter_fused.cuh"
 #include "iter_launch.cuh"
 #include "iter_p2.cuh"
 
@@ -13,6 +14,7 @@ template <typename T, int TT, int C, int R, int V>
 static const void *p2_row_one(int half, int stage) {
   if (!half) return (const void *)row_inv_p2_kernel<T, TT, C, R, V>;
   if (half == 2) return (const void *)row_yspec_p2_kernel<T, TT, C, R, V>;
+  if (half == 3) return (const void *)row_fused_p2_kernel<T, TT, C, R, V>;
   if (stage == 2) return (const void *)row_fwd_p2_kernel<T, TT, C, R, true, V>;  // penalty adaptation
   if constexpr (C == 1)
     if (stage == 1) return (const void *)row_fwd_p2_staged_kernel<T, TT, C, R, V>;

@@ -49,6 +49,7 @@ struct Cls {
   int group = 0;
   std::vector<int> imgs;
   size_t o_imgs = 0;  // workspace offset of the image list
+  size_t o_ticket = 0, o_flags = 0;  // fused row pass: ticket counter, one flag per work item
 };
 
 struct Layout {
@@ -63,8 +64,10 @@ struct Layout {
   size_t esz = 4;
   std::vector<ImageDesc> desc;
   long long total_px = 0, total_spec = 0, total_hhat = 0, total_words = 0, total_tw = 0, total_s2 = 0;
+  long long total_halo = 0;
   std::vector<HhatJob> jobs;
-  std::vector<long long> job_begin, img_word_begin, img_px_begin;
+  std::vector<long long> job_begin, g_begin, img_word_begin, img_px_begin;
+  long long total_g = 0;  // K x Nh row sums of every H^ job (double2)
   std::vector<int> plane_img;
   std::vector<int> lengths;
   std::map<int, int> tw_off, s2_off;
@@ -72,7 +75,9 @@ struct Layout {
   int row_grid = 0, col_grid = 0;
   size_t row_smem = 0, col_smem = 0;
   size_t o_yt, o_d0, o_d1, o_Sa, o_Sb, o_hhat, o_bits, o_tw, o_tw2, o_s2, o_desc, o_jobs, o_jobbeg, o_wordbeg,
-      o_pxbeg, o_planeimg, o_meanpart, o_means, o_partials, o_err, o_xbuf, o_clsimgs, o_v, o_mu, o_apart, total;
+      o_pxbeg, o_planeimg, o_meanpart, o_means, o_partials, o_err, o_xbuf, o_clsimgs, o_v, o_mu, o_apart, o_halo,
+      o_hg, o_gbeg,
+      o_sync, sync_bytes, total;
 };
 
 bool is_pow2_32(int L) { return L >= 64 && L <= 1024 && (L & (L - 1)) == 0; }
@@ -387,6 +392,7 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     L.col_grid += L.C * D.col_tiles;
     if (row_key[j]) {
       rc.cfg.stage = row_stage;
+      rc.cfg.fused = (tune && tune->fused_rows) ? 1 : 0;
       rc.cfg.nt = p2_row_threads(L.C, D.Rb, rc.cfg.tt, rc.cfg.r);
       rc.cfg.smem =
           std::max(rc.cfg.smem, p2_row_smem_half(L.C, D.N, D.Rb, rc.cfg.tt, L.esz, rc.cfg.r, row_stage, 0, rc.cfg.v));
@@ -412,6 +418,8 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     L.total_spec += (long long)L.C * D.M * D.Nh;
     D.mask_plane = ((long long)D.M * D.N + 31) / 32;
     D.mask = L.total_words;
+    D.halo = L.total_halo;
+    L.total_halo += (long long)L.C * D.N;
     L.img_word_begin.push_back(L.total_words);
     L.total_words += L.C * D.mask_plane;
     for (int c = 0; c < L.C; ++c) {
@@ -422,7 +430,9 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
     auto key = std::make_tuple(D.M, D.N, kidx);
     auto it = hh.find(key);
     if (it == hh.end()) {
-      HhatJob job{D.M, D.N, D.Nh, L.K, L.total_hhat, (long long)kidx * L.K * L.K};
+      HhatJob job{D.M, D.N, D.Nh, L.K, L.total_hhat, (long long)kidx * L.K * L.K, L.total_g};
+      L.g_begin.push_back(L.total_g);
+      L.total_g += (long long)L.K * D.Nh;
       L.job_begin.push_back(L.hhat_total_elems);
       L.hhat_total_elems += (long long)D.M * D.Nh;
       L.jobs.push_back(job);
@@ -525,6 +535,24 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
   L.o_v = take(L.total_px * 2 * L.esz);
   L.o_mu = take((size_t)3 * L.B * sizeof(double));
   L.o_apart = take((size_t)L.total_row_items * 2 * sizeof(double));
+  L.o_halo = take(L.total_halo * L.esz);
+  L.o_hg = take((size_t)L.total_g * 16);
+  L.o_gbeg = take(L.g_begin.size() * sizeof(long long));
+  // fused row pass: per row class a 64-bit ticket counter and a flag per work item
+  {
+    size_t sync = 0;
+    for (auto &c : L.row_cls) {
+      c.o_ticket = sync;
+      c.o_flags = sync + 8;
+      sync = (sync + 8 + 4 * (size_t)c.cfg.grid + 7) / 8 * 8;
+    }
+    L.sync_bytes = sync;
+    L.o_sync = take(sync);
+    for (auto &c : L.row_cls) {
+      c.o_ticket += L.o_sync;
+      c.o_flags += L.o_sync;
+    }
+  }
   for (auto *v : {&L.row_cls, &L.col_cls})
     for (auto &c : *v) c.o_imgs = take(c.imgs.size() * sizeof(int));
   L.total = o;
@@ -540,7 +568,7 @@ std::vector<deconv_tune> tune_candidates(int channels) {
     for (int cfv : {16, 32})
       for (int st : channels == 1 ? std::vector<int>{0, 1} : std::vector<int>{0})
         for (int rc : {152, 608})
-          for (int cc : {152, 608}) v.push_back(deconv_tune{rc, cc, st, fv, cfv, 0, 0});
+          for (int cc : {152, 608}) v.push_back(deconv_tune{rc, cc, st, fv, cfv, 0, 0, 0});
   return v;
 }
 
@@ -564,7 +592,8 @@ struct deconv_plan_s {
   deconv_dims dims{};
   std::vector<int32_t> rows, cols, ksizes;
   size_t ws_bytes = 0;
-  deconv_tune tune{0, 0, -1, 0, 0};  // the launch tuning in force (deconv_get_tune)
+  deconv_tune tune{0, 0, -1, 0, 0, 0, 0, 0};  // the launch tuning in force (deconv_get_tune)
+  long long wait_ns = 2000000000LL;  // bound of every device-side wait (deconv_set_wait_limit)
   cudaGraphExec_t gexec = nullptr;
   // While a graph is captured: the kernel classes of one pass (disjoint sets
   // of images) fan out over side streams, so their launches run concurrently.
@@ -624,6 +653,11 @@ RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_i
   a.xbuf = p->at<T>(L.o_xbuf);
   a.partials = partials;
   a.err = p->at<int>(L.o_err);
+  a.ticket = p->at<unsigned long long>(c.o_ticket);
+  a.flags = p->at<unsigned>(c.o_flags);
+  a.halo = p->at<T>(L.o_halo);
+  a.items = c.cfg.grid;
+  a.wait_ns = p->wait_ns;
   if (p->adapt_t > 0.0) {
     a.mu_img = p->at<double>(L.o_mu);
     a.mu_prev_img = a.mu_img + L.B;
@@ -758,6 +792,9 @@ cudaError_t row_pass(deconv_plan_s *p, cudaStream_t s, int mode, const T *d_in, 
   }
   return each_class(p, s, idx, [&](size_t k, cudaStream_t sk) {
     const RowArgs<T> a = row_args<T>(p, cl[k], mode, d_in, d_out, x_out, partials, rx);
+    // a plain iteration without statistics: the fused row pass (one kernel)
+    if (mode == ROW_ITER && !partials && cl[k].cfg.kind == KIND_P2 && cl[k].cfg.fused)
+      return launch_row_half<T>(a, cfg_of(k), 3, sk);
     if (mode == ROW_INNER && cl[k].cfg.kind == KIND_P2) {
       cudaError_t e1 = launch_row_half<T>(a, cfg_of(k), 0, sk);  // z-update
       return e1 != cudaSuccess ? e1 : launch_row_half<T>(a, cfg_of(k), 2, sk);  // y~ spectrum
@@ -1020,11 +1057,12 @@ deconv_status retune_t(deconv_plan_s *p, const deconv_tune *t) {
   CK(cudaMemcpyAsync(p->ws + p->L.o_desc, p->L.desc.data(), p->L.desc.size() * sizeof(ImageDesc),
                      cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(p->ws + p->L.o_err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(p->ws + p->L.o_sync, 0, p->L.sync_bytes, s));  // new grids: tickets and flags restart
   CK(prepare_all<T>(p->L));
   CK(cudaStreamSynchronize(s));
   p->have_state = false;
   p->adapt_ready = false;
-  p->tune = t ? *t : deconv_tune{0, 0, -1, 0, 0, 0, 0};
+  p->tune = t ? *t : deconv_tune{0, 0, -1, 0, 0, 0, 0, 0};
   return DECONV_OK;
 }
 
@@ -1105,10 +1143,14 @@ deconv_status setup_t(deconv_plan_s *p, const void *h, const uint8_t *mask) {
   CK(cudaMemcpyAsync(p->ws + L.o_planeimg, L.plane_img.data(), L.plane_img.size() * sizeof(int),
                      cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(p->ws + L.o_err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(p->ws + L.o_sync, 0, L.sync_bytes, s));
   CK(cudaMemsetAsync(p->ws + L.o_d0, 0, L.total_px * 2 * L.esz, s));
   CK(cudaMemsetAsync(p->ws + L.o_d1, 0, L.total_px * 2 * L.esz, s));
+  CK(cudaMemcpyAsync(p->ws + L.o_gbeg, L.g_begin.data(), L.g_begin.size() * sizeof(long long),
+                     cudaMemcpyHostToDevice, s));
   CK(launch_hhat<T>(p->at<HhatJob>(L.o_jobs), (int)L.jobs.size(), L.hhat_total_elems, static_cast<const T *>(h),
-                    p->ws + L.o_hhat, p->at<long long>(L.o_jobbeg), s));
+                    p->ws + L.o_hhat, p->at<long long>(L.o_jobbeg), p->at<long long>(L.o_gbeg), L.total_g,
+                    p->ws + L.o_hg, s));
   CK(launch_pack_mask(p->at<ImageDesc>(L.o_desc), L.B, L.total_words, p->at<long long>(L.o_wordbeg), mask,
                       p->at<uint32_t>(L.o_bits), s));
   CK(prepare_all<T>(L));
@@ -1428,7 +1470,7 @@ deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes) {
   // room for every tuning the autotuner tries and for the generic passes
   // (they differ in the per-row-block arrays and the class lists only)
   std::vector<deconv_tune> all = tune_candidates(dims->channels);
-  all.push_back(deconv_tune{0, 0, -1, 0, 0, 0, 0});
+  all.push_back(deconv_tune{0, 0, -1, 0, 0, 0, 0, 0});
   for (deconv_tune t : all)
     for (int mb : {-1, 24, 48, 80})
       for (int gen : {0, 1}) {
@@ -1504,7 +1546,8 @@ deconv_status deconv_retune(deconv_plan p, const deconv_tune *t) {
   if (t && (t->row_ctas < 0 || t->col_ctas < 0 || t->row_ctas > 65536 || t->col_ctas > 65536 || t->row_stage > 1 ||
             (t->fft_values != 0 && t->fft_values != 16 && t->fft_values != 32) ||
             (t->col_fft_values != 0 && t->col_fft_values != 16 && t->col_fft_values != 32) ||
-            t->l2_group_mb < -1 || t->l2_group_mb > 65536 || (t->generic != 0 && t->generic != 1)))
+            t->l2_group_mb < -1 || t->l2_group_mb > 65536 || (t->generic != 0 && t->generic != 1) ||
+            (t->fused_rows != 0 && t->fused_rows != 1)))
     return DECONV_EINVAL;
   return p->L.dtype == DECONV_F32 ? retune_t<float>(p, t) : retune_t<double>(p, t);
 }
@@ -1552,7 +1595,7 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   // per CTA at 1024) keeps the kernel classes of a batch from running side
   // by side; it is tried for plans of one row class only.
   const bool one_class = p->L.row_cls.size() == 1;
-  std::vector<deconv_tune> cands{deconv_tune{0, 0, -1, 0, 0, 0, 0}};  // the defaults
+  std::vector<deconv_tune> cands{deconv_tune{0, 0, -1, 0, 0, 0, 0, 0}};  // the defaults
   for (const deconv_tune &t : tune_candidates(p->L.C))
     if (t.row_stage != 1 || one_class) cands.push_back(t);
   for (size_t k = 0; k < cands.size() && st == DECONV_OK; ++k) trial(cands[k]);
@@ -1565,6 +1608,12 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
       t.l2_group_mb = mb;
       trial(t);
     }
+  }
+  // Then the fused row pass instead of the two row kernels.
+  if (st == DECONV_OK && bms >= 0.f) {
+    deconv_tune t = bt;
+    t.fused_rows = 1;
+    trial(t);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1649,6 +1698,16 @@ deconv_status deconv_solve_host(deconv_plan p, const void *y_host, void *x_host,
   if (st != DECONV_OK) return st;
   CK(cudaMemcpyAsync(x_host, p->ws + L.o_xbuf, bytes, cudaMemcpyDeviceToHost, p->stream));
   return deconv_sync(p);
+}
+
+deconv_status deconv_set_wait_limit(deconv_plan p, int64_t ns) {
+  if (!p || ns < 0) return DECONV_EINVAL;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);  // the bound is a kernel argument of the captured launches
+    p->gexec = nullptr;
+  }
+  p->wait_ns = (long long)ns;
+  return DECONV_OK;
 }
 
 deconv_status deconv_set_profiling(deconv_plan p, int32_t on) {
@@ -1816,13 +1875,17 @@ deconv_status deconv_kernel_launches(deconv_plan p, int32_t iters, int32_t mode,
   if (!p || !count || iters < 0 || (mode != 0 && mode != 1)) return DECONV_EINVAL;
   const Layout &L = p->L;
   long long row = 0, col = (long long)L.col_cls.size();
-  for (const Cls &c : L.row_cls) row += c.cfg.kind == KIND_P2 ? 2 : 1;
+  long long row_init = 0;  // the initial row pass always runs the two halves
+  for (const Cls &c : L.row_cls) {
+    row_init += c.cfg.kind == KIND_P2 ? 2 : 1;
+    row += c.cfg.kind != KIND_P2 ? 1 : ((c.cfg.fused && p->adapt_t <= 0.0) ? 1 : 2);
+  }
   long long inner = 0;  // an inner BGS pass: the inverse half and the y~ spectrum on register-FFT classes
   for (const Cls &c : L.row_cls) inner += c.cfg.kind == KIND_P2 ? 2 : 1;
   // observed means (2 kernels), initial fill, initial row pass, warm-start steps
-  const long long init = 3 + row + (p->tikh_iters > 0 ? (long long)p->tikh_iters * col +
-                                                            (long long)(p->tikh_iters - 1) * inner + row
-                                                      : 0);
+  const long long init = 3 + row_init + (p->tikh_iters > 0 ? (long long)p->tikh_iters * col +
+                                                                 (long long)(p->tikh_iters - 1) * inner + row_init
+                                                           : 0);
   long long adapt = 0;  // penalty adaptation: a residual-norm launch per class and the per-image rule
   if (p->adapt_t > 0.0) adapt = (long long)L.row_cls.size() + 1;
   const long long per_iter = col + row + adapt + (long long)(p->passes - 1) * (col + inner);

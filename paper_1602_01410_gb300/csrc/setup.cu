@@ -6,68 +6,96 @@ namespace dcv {
 
 // H^(k1, k2) = sum_{p,q=-b..b} h[p+b][q+b] exp(-2 pi i (k1 p / M + k2 q / N)),
 // the DFT of the kernel placed with its origin at grid index (0, 0) (the
-// eigenvalues of the BCCB matrix T~ of Eq. (4)).  Evaluated directly in
-// double precision: the phases of the first tap in each direction are
-// reduced exactly in integers, the following taps' twiddles come from
-// multiplying by exp(-2 pi i k / L) (about (2b+1) ulp of drift in double),
-// then the sum is rounded once.
-template <typename T>
-__global__ void hhat_kernel(const HhatJob *jobs, int njobs, const long long *job_begin, long long total,
-                            const T *h, cx<T> *hhat) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= total) return;
+// eigenvalues of the BCCB matrix T~ of Eq. (4)), in double precision and
+// separably: first the K x (N/2+1) row sums
+//   G(p, k2) = sum_q h[p+b][q+b] exp(-2 pi i k2 q / N),
+// then H^(k1, k2) = sum_p G(p, k2) exp(-2 pi i k1 p / M), rounded once to T.
+// In each sum the phase of the first tap is reduced exactly in integers and
+// the following taps' twiddles come from multiplying by exp(-2 pi i k / L)
+// (about (2b+1) ulp of drift in double).
+__device__ __forceinline__ void root_pi(long long k, long long n, long long L, double *c, double *s) {
+  const long long ph = (((k * n) % L) + L) % L;
+  sincospi(-2.0 * (double)ph / (double)L, s, c);
+}
+
+__device__ __forceinline__ int find_job(const long long *begin, int njobs, long long e) {
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (job_begin[mid] <= e) lo = mid; else hi = mid - 1;
+    if (begin[mid] <= e) lo = mid; else hi = mid - 1;
   }
-  const HhatJob J = jobs[lo];
-  const long long loc = e - job_begin[lo];
+  return lo;
+}
+
+template <typename T>
+__global__ void hrow_kernel(const HhatJob *jobs, int njobs, const long long *g_begin, long long total, const T *h,
+                            double2 *G) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int j = find_job(g_begin, njobs, e);
+  const HhatJob J = jobs[j];
+  const long long loc = e - g_begin[j];
+  const int p = (int)(loc / J.Nh), k2 = (int)(loc - (long long)p * J.Nh);
+  const int b = J.K / 2;
+  double c, s, cs, ss;
+  root_pi(k2, -b, J.N, &c, &s);
+  root_pi(k2, 1, J.N, &cs, &ss);
+  double re = 0.0, im = 0.0;
+  for (int q = 0; q < J.K; ++q) {
+    const double hv = (double)h[J.h + (long long)p * J.K + q];
+    re += hv * c;
+    im += hv * s;
+    const double cn = c * cs - s * ss;
+    s = c * ss + s * cs;
+    c = cn;
+  }
+  G[J.g + loc] = make_double2(re, im);
+}
+
+template <typename T>
+__global__ void hcol_kernel(const HhatJob *jobs, int njobs, const long long *job_begin, long long total,
+                            const double2 *G, cx<T> *hhat) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int j = find_job(job_begin, njobs, e);
+  const HhatJob J = jobs[j];
+  const long long loc = e - job_begin[j];
   const int k1 = (int)(loc / J.Nh), k2 = (int)(loc - (long long)k1 * J.Nh);
   const int b = J.K / 2;
-  // exp(-2 pi i k n / L) at n = -b (exact phase) and the step exp(-2 pi i k / L)
-  auto root = [](long long k, long long n, long long L, double *c, double *s) {
-    const long long ph = (((k * n) % L) + L) % L;
-    sincospi(-2.0 * (double)ph / (double)L, s, c);
-  };
-  double cq0, sq0, cqs, sqs, cp, sp, cps, sps;
-  root(k2, -b, J.N, &cq0, &sq0);
-  root(k2, 1, J.N, &cqs, &sqs);
-  root(k1, -b, J.M, &cp, &sp);
-  root(k1, 1, J.M, &cps, &sps);
+  double c, s, cs, ss;
+  root_pi(k1, -b, J.M, &c, &s);
+  root_pi(k1, 1, J.M, &cs, &ss);
   double re = 0.0, im = 0.0;
-  for (int p = -b; p <= b; ++p) {
-    double rr = 0.0, ri = 0.0, c = cq0, s = sq0;
-    for (int q = -b; q <= b; ++q) {
-      const double hv = (double)h[J.h + (long long)(p + b) * J.K + (q + b)];
-      rr += hv * c;
-      ri += hv * s;
-      const double cn = c * cqs - s * sqs;
-      s = c * sqs + s * cqs;
-      c = cn;
-    }
-    re += rr * cp - ri * sp;
-    im += rr * sp + ri * cp;
-    const double cn = cp * cps - sp * sps;
-    sp = cp * sps + sp * cps;
-    cp = cn;
+  const double2 *g = G + J.g + k2;
+  for (int p = 0; p < J.K; ++p) {
+    const double2 v = g[(long long)p * J.Nh];
+    re += v.x * c - v.y * s;
+    im += v.x * s + v.y * c;
+    const double cn = c * cs - s * ss;
+    s = c * ss + s * cs;
+    c = cn;
   }
   hhat[J.out + loc] = mk<T>((T)re, (T)im);
 }
 
 template <typename T>
 cudaError_t launch_hhat(const HhatJob *jobs_dev, int njobs, long long total, const T *h, void *hhat,
-                        const long long *job_begin_dev, cudaStream_t s) {
+                        const long long *job_begin_dev, const long long *g_begin_dev, long long total_g, void *G,
+                        cudaStream_t s) {
   const int nt = 256;
-  const long long grid = (total + nt - 1) / nt;
-  hhat_kernel<T><<<(unsigned)grid, nt, 0, s>>>(jobs_dev, njobs, job_begin_dev, total, h,
-                                                reinterpret_cast<cx<T> *>(hhat));
+  hrow_kernel<T><<<(unsigned)((total_g + nt - 1) / nt), nt, 0, s>>>(jobs_dev, njobs, g_begin_dev, total_g, h,
+                                                                     static_cast<double2 *>(G));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  hcol_kernel<T><<<(unsigned)((total + nt - 1) / nt), nt, 0, s>>>(jobs_dev, njobs, job_begin_dev, total,
+                                                                  static_cast<const double2 *>(G),
+                                                                  reinterpret_cast<cx<T> *>(hhat));
   return cudaGetLastError();
 }
 template cudaError_t launch_hhat<float>(const HhatJob *, int, long long, const float *, void *, const long long *,
-                                        cudaStream_t);
+                                        const long long *, long long, void *, cudaStream_t);
 template cudaError_t launch_hhat<double>(const HhatJob *, int, long long, const double *, void *,
-                                         const long long *, cudaStream_t);
+                                         const long long *, const long long *, long long, void *, cudaStream_t);
 
 // Packs the byte mask (nonzero = observed) into 32-bit words, one bit per
 // pixel, each channel plane padded to whole words.

@@ -125,7 +125,7 @@ def test_vjp_against_central_differences_of_the_oracle():
     # forward pass, in lambda and along a random direction of h.
     import torch
     import paper_1602_01410_gb300 as pkg
-    prob = inputs.random_problem(55, [(64, 64), (48, 80)], 5, mask_kind="random", frac=0.3, iters=5, lam=2e-3,
+    prob = inputs.random_problem(55, [(64, 64), (64, 128)], 5, mask_kind="random", frac=0.3, iters=5, lam=2e-3,
                                  mu=2e-2)
     iters = 5
     rng = np.random.default_rng(55)
