@@ -283,11 +283,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((fused
       // every group of the row has read its inputs before the tiles overwrite them
       if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
     }
-    fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Reg);
-    if (active) {
-#pragma unroll
-      for (int j = 0; j < V; ++j) Reg[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
-    }
+    fft_reg_smem<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Reg);
     if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
     if (active) {
       cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + f) * Nh;

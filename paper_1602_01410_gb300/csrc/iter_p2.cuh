@@ -102,6 +102,57 @@ __device__ __forceinline__ void fft_reg(cx<T> (&v)[V], bool active, cx<T> *tile,
   }
 }
 
+// The transform of fft_reg with its result left in shared memory, in
+// natural order (E[k] = X[k], k < L), instead of in registers, for passes
+// that store the transformed line to shared memory anyway.  For R > 1 the
+// radix-R combine runs in place over E: the R TT threads of this transform
+// take the L2 positions k2 in turn, read E[r L2 + k2] for every r, apply
+// an R-point DFT in registers and write the R outputs back to the same
+// places (R reads and R writes per k2, where the register form reads all R
+// inputs once per output).  Contains __syncthreads when R > 1 (every thread
+// of the CTA calls it); for R = 1 the caller synchronises before reading E.
+template <typename T, int V, int TT, int R, int SIGN>
+__device__ __forceinline__ void fft_reg_smem(cx<T> (&v)[V], bool active, cx<T> *tile, int q, unsigned gm, int bar,
+                                             int gr, const cx<T> *__restrict__ tw2, const cx<T> *__restrict__ tw3,
+                                             const cx<T> *__restrict__ twab, cx<T> *E) {
+  constexpr int L2 = V * TT;
+  if (active) {
+    if constexpr (V == 32)
+      fft_p2<T, TT, SIGN>(v, tile, q, gm, tw2);
+    else
+      fft_v16<T, TT, SIGN>(v, tile, q, gm, bar, tw2, twab);
+  }
+  if constexpr (R == 1) {
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < V; ++j) E[reg_pos<V, TT>(q, j)] = v[j];
+    }
+  } else {
+    __syncthreads();  // E may overlay the transpose tiles of the other groups
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        const int k2 = reg_pos<V, TT>(q, j);
+        cx<T> w = __ldg(&tw3[gr * L2 + k2]);
+        if (SIGN > 0) w.y = -w.y;
+        E[gr * L2 + k2] = cmul<T>(v[j], w);
+      }
+    }
+    __syncthreads();
+    if (active) {
+      for (int k2 = gr * TT + q; k2 < L2; k2 += R * TT) {
+        cx<T> e[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) e[r] = E[r * L2 + k2];
+        Dft<T, R, SIGN>::run(e);
+#pragma unroll
+        for (int r = 0; r < R; ++r) E[r * L2 + k2] = e[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Register cap of the row kernels: three-channel FP32 rows with 16 values
 // per thread (3 R TT threads per pixel row) are held to 72 registers for
 // R = 3, 5 (so that three 288-thread CTAs fit one SM's 64 K registers) and
@@ -484,11 +535,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
     // every group of the row has read its inputs before the tiles overwrite them
     if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   }
-  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Cs);
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < V; ++j) Cs[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
-  }
+  fft_reg_smem<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Cs);
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   if (active) {
     cpair<T> *__restrict__ dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
@@ -633,11 +680,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
   if (R > 1) __syncthreads();  // every group has read its inputs before outputs overwrite Cs
   cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
   const unsigned gm = group_mask(TT);
-  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Ex);
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < V; ++j) Cs[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
-  }
+  fft_reg_smem<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Cs);
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   if (active) {
     cpair<T> *__restrict__ dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
@@ -723,11 +766,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((V == 
     for (int m = 0; m < V; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
-  fft_reg<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, col);
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < V; ++j) col[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
-  }
+  fft_reg_smem<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, col);
   __syncthreads();
   // EXT: a Tikhonov warm-start step (tikh > 0) or a per-image penalty.
   const T mu = (EXT && a.mu_img) ? T(a.mu_img[Dp - a.desc]) : a.mu, tikh = EXT ? a.tikh : T(0);
@@ -777,11 +816,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((V == 
     for (int m = 0; m < V; ++m) v[m] = col[R * (q + TT * m) + gr];
   }
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
-  fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, col);
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < V; ++j) col[reg_pos<V, TT>(q, j) + L2 * gr] = v[j];
-  }
+  fft_reg_smem<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, col);
   __syncthreads();
   if (lane_ok && scol < w) {
     const int ww = scol;

@@ -1293,13 +1293,41 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
     for (const auto &kv : adj_smem_of) CK(prepare_adj<T>(kv.first, G.v, L.C, kv.second));
   }
 
-  // 1. Forward with checkpoints of (y~, d, forward spectrum) every k iterations.
+  // Forward run of checkpoint segment c from its checkpoint, storing x_{j+1},
+  // d_j and the spectra of every step j of the segment for the reverse pass.
+  auto store_segment = [&](int c) -> deconv_status {
+    const int s0 = c * k, s1 = std::min(s0 + k, iters);
+    CK(cudaMemcpyAsync(p->ws + L.o_yt, at(G.o_ckyt) + c * px, px, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(at(G.o_segD), at(G.o_ckd) + 2 * c * px, 2 * px, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p->ws + L.o_Sa, at(G.o_ckS) + c * spec, spec, cudaMemcpyDeviceToDevice, s));
+    for (int j = s0; j < s1; ++j) {
+      const int jj = j - s0;
+      for (const Cls &cl : L.col_cls) {
+        ColArgs<T> ca = col_args<T>(p, cl, 0.0);
+        ca.spec_store = reinterpret_cast<cpair<T> *>(at(G.o_segSpec) + jj * spec);
+        CK(launch_col<T>(ca, cl.cfg, s));
+      }
+      CK(row_pass<T>(p, s, ROW_ITER, reinterpret_cast<const T *>(at(G.o_segD) + 2 * jj * px),
+                     reinterpret_cast<T *>(at(G.o_segD) + 2 * (jj + 1) * px),
+                     reinterpret_cast<T *>(at(G.o_segX) + jj * px), nullptr));
+    }
+    return DECONV_OK;
+  };
+
+  // 1. Forward with checkpoints of (y~, d, forward spectrum) every k
+  // iterations; the last segment runs storing its steps, so the reverse
+  // sweep need not recompute it (with k >= iters nothing is recomputed).
   st = init_state<T>(p, static_cast<const T *>(y), nullptr);
   if (st != DECONV_OK) return st;
   for (int c = 0; c < G.nck; ++c) {
     CK(cudaMemcpyAsync(at(G.o_ckyt) + c * px, p->ws + L.o_yt, px, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(at(G.o_ckd) + 2 * c * px, dbuf<T>(p, p->parity), 2 * px, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(at(G.o_ckS) + c * spec, p->ws + L.o_Sa, spec, cudaMemcpyDeviceToDevice, s));
+    if (c == G.nck - 1) {
+      st = store_segment(c);
+      if (st != DECONV_OK) return st;
+      break;
+    }
     const int n = std::min(k, iters - c * k);
     for (int it = 0; it < n; ++it) {
       st = iterate<T>(p, s, nullptr, nullptr, 0, 0);
@@ -1327,20 +1355,9 @@ deconv_status grad_t(deconv_plan_s *p, const void *y, const void *x_true, int it
   const ImageDesc *desc = p->at<ImageDesc>(L.o_desc);
   for (int c = G.nck - 1; c >= 0; --c) {
     const int s0 = c * k, s1 = std::min(s0 + k, iters);
-    CK(cudaMemcpyAsync(p->ws + L.o_yt, at(G.o_ckyt) + c * px, px, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(at(G.o_segD), at(G.o_ckd) + 2 * c * px, 2 * px, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(p->ws + L.o_Sa, at(G.o_ckS) + c * spec, spec, cudaMemcpyDeviceToDevice, s));
-    // Forward recompute of the segment, storing x_{j+1}, d_j and the spectra of step j.
-    for (int j = s0; j < s1; ++j) {
-      const int jj = j - s0;
-      for (const Cls &cl : L.col_cls) {
-        ColArgs<T> ca = col_args<T>(p, cl, 0.0);
-        ca.spec_store = reinterpret_cast<cpair<T> *>(at(G.o_segSpec) + jj * spec);
-        CK(launch_col<T>(ca, cl.cfg, s));
-      }
-      CK(row_pass<T>(p, s, ROW_ITER, reinterpret_cast<const T *>(at(G.o_segD) + 2 * jj * px),
-                     reinterpret_cast<T *>(at(G.o_segD) + 2 * (jj + 1) * px),
-                     reinterpret_cast<T *>(at(G.o_segX) + jj * px), nullptr));
+    if (c != G.nck - 1) {  // the last segment's steps are still stored from the forward run
+      st = store_segment(c);
+      if (st != DECONV_OK) return st;
     }
     // Reverse through the segment.
     for (int j = s1 - 1; j >= s0; --j) {
@@ -1895,9 +1912,12 @@ deconv_status deconv_kernel_launches(deconv_plan p, int32_t iters, int32_t mode,
   }
   if (iters < 1 || ckpt_every < 1) return DECONV_EINVAL;
   const long long nrc = (long long)L.row_cls.size();
-  // forward + loss (2) + recompute (iters steps) + reverse per step:
-  // inverse halves (not on the first), adjoint stencils, 2 reductions, column passes; taps (2 per image).
-  *count = init + (long long)iters * per_iter + 2 + (long long)iters * per_iter +
+  // forward + loss (2) + recompute (every segment but the last, stored by the
+  // forward run) + reverse per step: inverse halves (not on the first),
+  // adjoint stencils, 2 reductions, column passes; taps (2 per image).
+  const int k = std::min(ckpt_every, iters), nck = (iters + k - 1) / k;
+  const long long recompute = (long long)(nck - 1) * k;
+  *count = init + (long long)iters * per_iter + 2 + recompute * per_iter +
            (long long)(iters - 1) * nrc + (long long)iters * (nrc + 2 + col) + 2LL * L.B;
   return DECONV_OK;
 }

@@ -73,7 +73,7 @@ def test_grad_batch_shared_kernel_and_checkpoint_invariance():
     prob = inputs.random_problem(52, [(64, 128), (128, 64)], 7, mask_kind="random", frac=0.2, iters=6,
                                  lam=1e-3, mu=2e-2)
     a = check(prob, 6, 2, 2e-3)
-    for ck in (1, 6):
+    for ck in (1, 4, 6):  # 6 = iters: every step stored in the forward run; 4: a short last segment
         b = gpu_grad(prob, 6, ck)
         assert np.isclose(a[0], b[0], rtol=1e-6) and np.isclose(a[1], b[1], rtol=1e-4)
         assert np.max(np.abs(a[2] - b[2])) <= 1e-4 * np.max(np.abs(a[2]))
