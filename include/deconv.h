@@ -242,12 +242,15 @@ deconv_status deconv_solve_host(deconv_plan plan, const void *y_host, void *x_ho
  * on the host (loss, dlambda) and dL/dh in dh (device, the layout of h).
  * Reverse-mode differentiation of Eqs. (admm_aprox_1)-(admm_aprox_4) with
  * the over-relaxed z-update: the forward pass keeps (y~, d, forward
- * spectrum) every ckpt_every iterations; the reverse pass recomputes each
- * segment from its checkpoint and runs the adjoint iteration backwards (the
+ * spectrum) every ckpt_every iterations and stores every step of its last
+ * segment; the reverse pass recomputes each other segment from its
+ * checkpoint (none when ckpt_every >= iters, at the cost of a workspace
+ * holding every step) and runs the adjoint iteration backwards (the
  * x-step is self-adjoint; the vector soft-threshold contributes its
  * Jacobian, zero below the threshold).  grad_ws: device, 256-byte aligned,
  * at least deconv_grad_workspace_size() bytes.  x_out: NULL or device, the
- * batch layout, receives x^{iters}.  Power-of-two sizes 64..1024 only
+ * batch layout, receives x^{iters}.  Row and column lengths with a register
+ * transform only: 2^k for 64..1024 and 3 * 2^k, 5 * 2^k for 384..2560
  * (DECONV_EUNSUPPORTED otherwise).  Synchronises the stream; leaves the plan
  * state at x^{iters}'s last recomputed segment (use warm = 0 next). */
 deconv_status deconv_grad_workspace_size(deconv_plan plan, int32_t iters, int32_t ckpt_every, size_t *bytes);

@@ -7,26 +7,28 @@ template <typename T, int C>
 static const void *adj_ptr_c(int N, int v) {
   if (v == 16) {
     switch (N / 16) {
-      case 4: return (const void *)row_adj_p2_kernel<T, 4, C, 16>;
-      case 8: return (const void *)row_adj_p2_kernel<T, 8, C, 16>;
-      case 16: return (const void *)row_adj_p2_kernel<T, 16, C, 16>;
-      case 32: return (const void *)row_adj_p2_kernel<T, 32, C, 16>;
-      case 64: return (const void *)row_adj_p2_kernel<T, 64, C, 16>;
+      case 4: return (const void *)row_adj_p2_kernel<T, 4, C, 1, 16>;
+      case 8: return (const void *)row_adj_p2_kernel<T, 8, C, 1, 16>;
+      case 16: return (const void *)row_adj_p2_kernel<T, 16, C, 1, 16>;
+      case 32: return (const void *)row_adj_p2_kernel<T, 32, C, 1, 16>;
+      case 64: return (const void *)row_adj_p2_kernel<T, 64, C, 1, 16>;
     }
     return nullptr;
   }
   switch (N / 32) {
-    case 2: return (const void *)row_adj_p2_kernel<T, 2, C, 32>;
-    case 4: return (const void *)row_adj_p2_kernel<T, 4, C, 32>;
-    case 8: return (const void *)row_adj_p2_kernel<T, 8, C, 32>;
-    case 16: return (const void *)row_adj_p2_kernel<T, 16, C, 32>;
-    case 32: return (const void *)row_adj_p2_kernel<T, 32, C, 32>;
+    case 2: return (const void *)row_adj_p2_kernel<T, 2, C, 1, 32>;
+    case 4: return (const void *)row_adj_p2_kernel<T, 4, C, 1, 32>;
+    case 8: return (const void *)row_adj_p2_kernel<T, 8, C, 1, 32>;
+    case 16: return (const void *)row_adj_p2_kernel<T, 16, C, 1, 32>;
+    case 32: return (const void *)row_adj_p2_kernel<T, 32, C, 1, 32>;
   }
   return nullptr;
 }
 
+// Lengths 3 * 2^k and 5 * 2^k come from adjoint_r35.cu (16 values per thread).
 template <typename T>
 static const void *adj_ptr(int N, int v, int C) {
+  if (N % 3 == 0 || N % 5 == 0) return adj_ptr_r35<T>(N, v, C);
   return C == 3 ? adj_ptr_c<T, 3>(N, v) : adj_ptr_c<T, 1>(N, v);
 }
 

@@ -1,4 +1,5 @@
-// Reverse pass (gradient of the unrolled iteration) for power-of-two rows.
+// Reverse pass (gradient of the unrolled iteration) for the register-FFT
+// row lengths L = R V TT (R in {1, 3, 5}).
 //
 // Reverse of forward step j ((y~_j, v_j, d_j) -> x_{j+1} -> (y~_{j+1},
 // v_{j+1}, d_{j+1})), with a = D x_{j+1} + d_j and carried adjoints yb, vb, db:
@@ -31,11 +32,12 @@ __device__ __forceinline__ int find_adj(const ImageDesc *desc, const int *imgs, 
   return imgs[lo];
 }
 
-// V complex values per thread (32: fft_p2, 16: fft_v16), TT = N / V threads per row.
-template <typename T, int TT, int C, int V>
+// V complex values per thread (32: fft_p2, 16: fft_v16); R groups of TT
+// threads per (channel, row), each owning L2 = V TT pixels of the row.
+template <typename T, int TT, int C, int R, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(AdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = reg_group_stride<V, TT>();
+  constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT;
   const int wi = blockIdx.x;
   const int img = find_adj<T>(a.desc, a.cls_imgs, a.adj_begin, a.nimg, wi);
   const ImageDesc *Dp = &a.desc[img];
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
   const long long P = (long long)M * N, px0 = Dp->px;
   const int g = threadIdx.x / TT, q = threadIdx.x - g * TT;
   const int bar = 1 + g;  // named barrier of a 64-thread group (group_bar)
-  const int ch = g / Rb, hh = g - ch * Rb;
+  const int gr = g % R, row_id = g / R, ch = row_id / Rb, hh = row_id - ch * Rb;
   const bool active = ch < C && hh < nr;
   const int i = r0 + hh;
   const bool start = a.mode == ADJ_START;
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
   // transpose tiles (the tiles overwrite the staged rows after a barrier).
   const size_t staged = (size_t)C * (2 * (Rb + 2) + 4 * (Rb + 1)) * N * sizeof(T);
   const size_t tiles = (size_t)(blockDim.x / TT) * GS * sizeof(cx<T>);
-  cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)g * N;
+  cx<T> *Cs = reinterpret_cast<cx<T> *>(smem_raw + (staged > tiles ? staged : tiles)) + (size_t)row_id * N;
 
   if (!start) {
     for (int c = 0; c < C; ++c) {
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
     const long long rowp = px0 + ch * P + (long long)i * N;
     const uint32_t *mrow = a.mask + Dp->mask + ch * Dp->mask_plane + (long long)i * (N / 32);
     for (int m = 0; m < V; ++m) {
-      const int p = q + TT * m;
+      const int p = q + TT * m + L2 * gr;
       const int pm = (p == 0) ? N - 1 : p - 1;
       const T yb = start ? T(0) : a.ybar[rowp + p];
       const bool obs = (__ldg(&mrow[p >> 5]) >> (p & 31)) & 1u;
@@ -149,23 +151,24 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_adj_p2_kernel(
     }
   }
   __syncthreads();  // tiles below reuse the staged rows
+  cx<T> v[V];
   if (active) {
-    cx<T> v[V];
 #pragma unroll
-    for (int m = 0; m < V; ++m) v[m] = Cs[q + TT * m];
+    for (int m = 0; m < V; ++m) v[m] = Cs[R * (q + TT * m) + gr];
+  }
+  if (R > 1) __syncthreads();  // every group has read its inputs before the combine overwrites Cs
+  {
     cx<T> *tile = reinterpret_cast<cx<T> *>(smem_raw) + (size_t)g * GS;
     const unsigned gm = group_mask(TT);
     const cx<T> *tw = reinterpret_cast<const cx<T> *>(a.tw2);
-    if constexpr (V == 32)
-      fft_p2<T, TT, -1>(v, tile, q, gm, tw + Dp->tw2_row);
-    else
-      fft_v16<T, TT, -1>(v, tile, q, gm, bar, tw + Dp->tw16_row, tw + Dp->twab_row);
-#pragma unroll
-    for (int r = 0; r < V; ++r) tile[reg_pos<V, TT>(q, r)] = v[r];
-    group_bar<TT>(gm, bar);
+    fft_reg_smem<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw + (V == 32 ? Dp->tw2_row : Dp->tw16_row),
+                                  tw + Dp->tw3_row, tw + Dp->twab_row, Cs);
+    if (R == 1 && active) group_bar<TT>(gm, bar);
+  }
+  if (active) {
     cpair<T> *dst = a.S_out + Dp->spec + ((long long)ch * M + i) * Nh;
-    for (int k = q; k < Nh; k += TT) {
-      const cx<T> c1 = tile[k], c2 = tile[k == 0 ? 0 : N - k];
+    for (int k = q + TT * gr; k < Nh; k += TT * R) {
+      const cx<T> c1 = Cs[k], c2 = Cs[k == 0 ? 0 : N - k];
       cpair<T> o;
       o.ar = T(0.5) * (c1.x + c2.x);
       o.ai = T(0.5) * (c1.y - c2.y);
@@ -193,7 +196,7 @@ __global__ void sqerr_kernel(const T *x, const T *xt, long long n, double *part)
 }
 
 // Fixed-order sum of n doubles into out[0] (one CTA).
-__global__ void sum_kernel(const double *v, int n, double scale, double *out) {
+static __global__ void sum_kernel(const double *v, int n, double scale, double *out) {
   double s = 0.0;
   for (int e = threadIdx.x; e < n; e += blockDim.x) s += v[e];
   double z0 = 0.0, z1 = 0.0;

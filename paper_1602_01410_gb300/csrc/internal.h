@@ -160,6 +160,11 @@ template <typename T> struct AdjArgs {
 };
 
 
+// The reverse-pass row kernel of a row length 3 * 2^k or 5 * 2^k with v = 16
+// values per thread (adjoint_r35.cu; launch and shared-memory opt-in must use
+// the pointer it returns); NULL for any other length.
+template <typename T>
+const void *adj_ptr_r35(int N, int v, int C);
 // Reverse-pass row kernel for rows of length N with v complex values per thread (16 or 32).
 template <typename T>
 cudaError_t launch_adj(const AdjArgs<T> &a, int N, int v, int C, int grid, int nt, size_t smem, cudaStream_t s);

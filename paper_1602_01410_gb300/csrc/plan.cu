@@ -1195,11 +1195,14 @@ struct GradLayout {
 
 constexpr int kLossBlocks = 256;
 
-size_t adj_smem(int C, int N, int rb, int tt, size_t esz, int v = 32) {
+// Shared memory of the reverse row kernel: the staged rows (or the transpose
+// tiles of its r groups per row, which reuse them), then one row of N
+// complex values per (channel, row).
+size_t adj_smem(int C, int N, int rb, int tt, size_t esz, int v, int r) {
   const size_t staged = (size_t)C * (2 * (rb + 2) + 4 * (rb + 1)) * N * esz;
-  const int groups = p2_row_threads(C, rb, tt) / tt;
+  const int groups = p2_row_threads(C, rb, tt, r) / tt;
   const size_t tiles = (size_t)groups * p2_group_stride_hv(tt, v) * 2 * esz;
-  return std::max(staged, tiles) + (size_t)groups * N * 2 * esz;
+  return std::max(staged, tiles) + (size_t)((groups + r - 1) / r) * N * 2 * esz;
 }
 
 deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *G) {
@@ -1208,7 +1211,7 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
   if (iters < 1 || k < 1) return DECONV_EINVAL;
   for (const auto *v : {&L.row_cls, &L.col_cls})
     for (const Cls &c : *v)
-      if (c.cfg.kind != KIND_P2 || c.cfg.r != 1) return DECONV_EUNSUPPORTED;  // reverse pass: powers of two only
+      if (c.cfg.kind != KIND_P2) return DECONV_EUNSUPPORTED;  // reverse pass: register-transform lengths only
   G->v = 16;
   G->k = std::min(k, iters);
   G->nck = (iters + G->k - 1) / G->k;
@@ -1217,12 +1220,14 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
   G->items = 0;
   for (const Cls &c : L.row_cls) {
     const ImageDesc &D0 = L.desc[c.imgs[0]];
-    const int v = G->v, tt = D0.N / v;  // the adjoint row kernel: v values per thread
+    // the reverse row kernel: v values per thread, r groups of tt threads per row
+    const int v = G->v, r = c.cfg.r, tt = D0.N / (v * r);
     int rb = D0.Rb;
-    while (rb > 1 && (adj_smem(L.C, D0.N, rb, tt, L.esz, v) > kMaxSmem || p2_row_threads(L.C, rb, tt) > maxthr ||
-                      !p2_groups_ok(p2_row_threads(L.C, rb, tt), tt)))
+    while (rb > 1 && (adj_smem(L.C, D0.N, rb, tt, L.esz, v, r) > kMaxSmem ||
+                      p2_row_threads(L.C, rb, tt, r) > maxthr || !p2_groups_ok(p2_row_threads(L.C, rb, tt, r), tt)))
       --rb;
-    if (adj_smem(L.C, D0.N, rb, tt, L.esz, v) > kMaxSmem) return DECONV_EUNSUPPORTED;
+    if (adj_smem(L.C, D0.N, rb, tt, L.esz, v, r) > kMaxSmem || p2_row_threads(L.C, rb, tt, r) > maxthr)
+      return DECONV_EUNSUPPORTED;
     int grid = 0;
     for (int j : c.imgs) {
       G->adj_begin[j] = grid;
@@ -1230,8 +1235,8 @@ deconv_status grad_layout(const deconv_plan_s *p, int iters, int k, GradLayout *
     }
     G->rb.push_back(rb);
     G->grid.push_back(grid);
-    G->nt.push_back(p2_row_threads(L.C, rb, tt));
-    G->smem.push_back(adj_smem(L.C, D0.N, rb, tt, L.esz, v));
+    G->nt.push_back(p2_row_threads(L.C, rb, tt, r));
+    G->smem.push_back(adj_smem(L.C, D0.N, rb, tt, L.esz, v, r));
     G->items = std::max(G->items, grid);
   }
   const size_t px = L.total_px * L.esz, spec = L.total_spec * 4 * L.esz;

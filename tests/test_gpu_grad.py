@@ -1,9 +1,10 @@
 """GPU reverse pass (deconv_grad) against the FP64 oracle's reverse pass on
 the same seeded inputs: loss, dL/dlambda and dL/dh (every tap), for one and
-three channels, batches sharing one kernel, and several checkpoint
-intervals; the autograd wrapper; and the full-size differentiation workload
-(512 x 512, 15 x 15 Gaussian, 20% missing, 100 iterations, checkpoints
-every 10) on two images."""
+three channels, power-of-two and 3 * 2^k / 5 * 2^k lengths, batches sharing
+one kernel, and several checkpoint intervals (every step stored included);
+the autograd wrappers and the vector-Jacobian product; and the full-size
+differentiation workload (512 x 512, 15 x 15 Gaussian, 20% missing, 100
+iterations, checkpoints every 10) on two images."""
 import numpy as np
 import pytest
 
@@ -77,6 +78,17 @@ def test_grad_batch_shared_kernel_and_checkpoint_invariance():
         b = gpu_grad(prob, 6, ck)
         assert np.isclose(a[0], b[0], rtol=1e-6) and np.isclose(a[1], b[1], rtol=1e-4)
         assert np.max(np.abs(a[2] - b[2])) <= 1e-4 * np.max(np.abs(a[2]))
+
+
+def test_grad_radix_3_and_5_lengths():
+    # 384 = 3 * 128 and 640 = 5 * 128: the reverse row kernels with the
+    # radix-3 and radix-5 combine, as rows and as columns, one and three
+    # channels, a checkpoint segment boundary inside the run
+    prob = inputs.random_problem(58, [(384, 640), (640, 384)], 5, mask_kind="random", frac=0.3, iters=4, lam=2e-3,
+                                 mu=2e-2)
+    check(prob, 4, 3, 2e-3)
+    prob3 = inputs.random_problem(59, [(384, 384)], 5, mask_kind="bayer", channels=3, iters=3, lam=2e-3, mu=2e-2)
+    check(prob3, 3, 2, 2e-3)
 
 
 def test_grad_vectorial_tv():
