@@ -771,12 +771,20 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((V == 
   // EXT: a Tikhonov warm-start step (tikh > 0) or a per-image penalty.
   const T mu = (EXT && a.mu_img) ? T(a.mu_img[Dp - a.desc]) : a.mu, tikh = EXT ? a.tikh : T(0);
   const T scale = T(1) / (T(M) * T(N));
-  if (lane_ok && scol < w) {
-    const int ww = scol;
+  // Solve and store: a full tile (w = W) gives the first (nthr / w) w
+  // threads of the CTA a column ww and rows in turn, k1 fastest in the
+  // solve (conflict-free column accesses) and ww fastest in the store
+  // (whole 32-byte row segments); a ragged tile keeps the staging layout.
+  const bool full = w == Dp->W;
+  const int kstep = full ? nthr / w : rstep;
+  const bool full_on = full && (int)threadIdx.x < kstep * w;
+  const int sv_ww = full ? threadIdx.x / kstep : scol, sv_k0 = full ? threadIdx.x % kstep : r0t;
+  if (full_on || (!full && lane_ok && scol < w)) {
+    const int ww = sv_ww;
     const T s2w = S2s[M + ww];
     cx<T> *gacc = a.gacc ? reinterpret_cast<cx<T> *>(a.gacc) + base : nullptr;
     cx<T> *cy = St + (size_t)(2 * ww) * SR, *cr = cy + SR;
-    for (int k1 = r0t; k1 < M; k1 += rstep) {
+    for (int k1 = sv_k0; k1 < M; k1 += kstep) {
       const cx<T> hv = Hs[k1 * w + ww];
       const T den = hv.x * hv.x + hv.y * hv.y + ((EXT && tikh > T(0)) ? tikh : mu * (S2s[k1] + s2w));
       const T inv = scale / den;
@@ -818,10 +826,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((V == 
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   fft_reg_smem<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, col);
   __syncthreads();
-  if (lane_ok && scol < w) {
-    const int ww = scol;
+  if (full_on || (!full && lane_ok && scol < w)) {
+    const int ww = full ? threadIdx.x % w : scol;
     const cx<T> *cx_ = St + (size_t)(2 * ww) * SR, *ch_ = cx_ + SR;
-    for (int ii = r0t; ii < M; ii += rstep) {
+    for (int ii = full ? threadIdx.x / w : r0t; ii < M; ii += full ? nthr / w : rstep) {
       const cx<T> Xv = cx_[ii], HX = ch_[ii];
       cpair<T> c;
       c.ar = Xv.x;
