@@ -55,10 +55,11 @@ __device__ __forceinline__ bool wait_flag(const unsigned *f, unsigned epoch, lon
   }
 }
 
-// Register cap: three-channel FP32 rows with 16 values per thread hold
-// both halves' live ranges, so 80 (72 spills) for R = 3, 5 and 96 for R = 1.
+// Register cap: three-channel FP32 rows with 16 values per thread, 72 for
+// R = 3, 5 (three 288-thread CTAs per SM; measured faster than 80 despite
+// the spills of holding both halves' live ranges) and 96 for R = 1.
 template <typename T, int C, int R, int V> __host__ __device__ constexpr int fused_reg_cap() {
-  return (C == 3 && V == 16 && sizeof(T) == 4) ? (R == 1 ? 96 : 80) : (sizeof(T) == 4 ? 128 : 255);
+  return (C == 3 && V == 16 && sizeof(T) == 4) ? (R == 1 ? 96 : 72) : (sizeof(T) == 4 ? 128 : 255);
 }
 
 // Same CTA layout as the two halves: R groups of TT threads per (channel,

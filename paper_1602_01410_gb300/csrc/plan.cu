@@ -1488,20 +1488,16 @@ deconv_status deconv_workspace_size(const deconv_dims *dims, size_t *bytes) {
   Layout L;
   deconv_status st = build_layout(dims, &L);
   if (st != DECONV_OK) return st;
-  size_t total = L.total;
-  // room for every tuning the autotuner tries and for the generic passes
-  // (they differ in the per-row-block arrays and the class lists only)
-  std::vector<deconv_tune> all = tune_candidates(dims->channels);
-  all.push_back(deconv_tune{0, 0, -1, 0, 0, 0, 0, 0});
-  for (deconv_tune t : all)
-    for (int mb : {-1, 24, 48, 80})
-      for (int gen : {0, 1}) {
-        t.l2_group_mb = mb;
-        t.generic = gen;
-        Layout Lt;
-        if (build_layout(dims, &Lt, &t) == DECONV_OK) total = std::max(total, Lt.total);
-      }
-  *bytes = total;
+  // Room for every tuning the autotuner tries and for the generic passes.
+  // They share every array but the per-row-work-item ones (statistics and
+  // residual partials, 24 + 16 bytes; fused-pass flags, 4 bytes) and the
+  // class lists (at most one row and one column class per image, each list
+  // and ticket aligned to 256 bytes): a work item is at least one row, so
+  // the default layout plus that much for every row and class bounds them.
+  long long rows = 0;
+  for (int j = 0; j < dims->batch; ++j) rows += dims->rows[j];
+  const size_t extra = (size_t)rows * 44 + (size_t)(2 * dims->batch + 2) * 2 * kAlign + 8 * kAlign;
+  *bytes = align_up(L.total + extra);
   return DECONV_OK;
 }
 

@@ -23,9 +23,11 @@ pytestmark = pytest.mark.gpu
 
 # The autotuner's candidates: CTAs per row class and per column pass, staged
 # or L1 forward half (one channel, one row class), values per thread of the
-# row and column transforms; (0, 0, -1, 0, 0) is the default tuning.
+# row and column transforms; (0, 0, -1, 0, 0) is the default tuning; then the
+# fused row pass (the last field; image groups do not apply to one image).
 CANDIDATES = [(0, 0, -1, 0, 0)] + [(r, c, st, fv, cfv) for fv in (16, 32) for cfv in (16, 32) for st in (0, 1)
-                                   for r in (152, 608) for c in (152, 608)]
+                                   for r in (152, 608) for c in (152, 608)] + [(0, 0, -1, 0, 0, 0, 0, 1),
+                                                                               (608, 152, 0, 16, 32, 0, 0, 1)]
 
 
 @pytest.fixture(scope="module", autouse=True)
