@@ -598,13 +598,17 @@ def main():
         ms_col, ms_row, ms_it = plan.graph_pass_times()
         plan.set_profiling(False)
         passes = {}
-        for name, ms in (("col", ms_col), ("row", ms_row)):
+        for name, ms in (("col", ms_col), ("row", ms_row)) if ms_col >= 0 else ():
             b_px = alg[name]
             gbs = b_px * px / (ms / 1e3) / 1e9 / world if ms > 0 else None
             passes[name] = {"ms_per_iter": ms, "algorithmic_bytes_per_px": b_px, "achieved_gbs": gbs,
                             "frac": (gbs / peak) if gbs else None}
         passes["iteration_ms"] = ms_it
-        passes["dominant"] = "row" if ms_row >= ms_col else "col"
+        if ms_col >= 0:
+            passes["dominant"] = "row" if ms_row >= ms_col else "col"
+        else:
+            passes["note"] = ("the kernel classes run as independent chains, so their passes overlap: "
+                              "only the whole iteration is timed")
         passes["how"] = ("CUDA events captured between the passes of the CUDA graph (20-iteration loop), "
                          "one replay after the timed steps; the events replace the overlap of each pass's "
                          "launch with the previous pass's tail")

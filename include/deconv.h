@@ -165,7 +165,12 @@ deconv_status deconv_set_options(deconv_plan plan, const deconv_options *opts);
  * of a plain iteration as two kernels (inverse half, forward half); 1 runs
  * it (one BGS pass, fixed mu, no statistics) as one fused kernel that takes
  * its row blocks from a work queue in order and waits, with a bound
- * (deconv_set_wait_limit), for the x rows of the blocks above it. */
+ * (deconv_set_wait_limit), for the x rows of the blocks above it.
+ * chains: 1 runs the captured loop of a batch as one chain per kernel
+ * class (the images sharing a row and a column transform length): every
+ * chain iterates on a stream of its own and the chains join only at the
+ * end of the loop, so that no pass waits for the other classes' tails
+ * (the images are independent problems); it replaces l2_group_mb. */
 typedef struct {
   int32_t row_ctas;
   int32_t col_ctas;
@@ -176,6 +181,7 @@ typedef struct {
   int32_t l2_group_mb;    /* image groups of the captured loop, MiB of intermediate per group; 0 or -1 = off */
   int32_t generic;        /* 1: Stockham passes for every image; 0: register transforms where they apply */
   int32_t fused_rows;     /* 0: two row kernels; 1: the fused row pass for plain iterations */
+  int32_t chains;         /* 0: every pass over all classes; 1: one independent chain per kernel class */
 } deconv_tune;
 
 /* Bound of every device-side wait, in nanoseconds (default 2e9; the paper
@@ -202,7 +208,8 @@ deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
  * in {152, 608}, fft_values and col_fft_values in {16, 32}, and for one
  * channel and one row class row_stage in {0, 1}); then, for a batch, the
  * image-group budgets l2_group_mb in {24, 48, 80} on the fastest of
- * those, and the fused row pass (fused_rows = 1) on the fastest so far.
+ * those, the chains (chains = 1), and the fused row pass (fused_rows = 1)
+ * on the fastest so far.
  * Keeps the fastest (best, best_ms_per_iter: nullable host outputs)
  * and leaves the plan in it with no iteration state.  y: device, batch
  * layout.  Synchronous. */

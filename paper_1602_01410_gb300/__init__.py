@@ -69,7 +69,8 @@ class deconv_options(ctypes.Structure):
 class deconv_tune(ctypes.Structure):
     _fields_ = [("row_ctas", ctypes.c_int32), ("col_ctas", ctypes.c_int32), ("row_stage", ctypes.c_int32),
                 ("fft_values", ctypes.c_int32), ("col_fft_values", ctypes.c_int32),
-                ("l2_group_mb", ctypes.c_int32), ("generic", ctypes.c_int32), ("fused_rows", ctypes.c_int32)]
+                ("l2_group_mb", ctypes.c_int32), ("generic", ctypes.c_int32), ("fused_rows", ctypes.c_int32),
+                ("chains", ctypes.c_int32)]
 
 
 TUNE_FIELDS = tuple(name for name, _ in deconv_tune._fields_)
@@ -274,9 +275,10 @@ def deconv_get_mu(plan: int, nimg: int):
 
 
 def deconv_retune(plan: int, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
-                  col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0, fused_rows: int = 0) -> None:
+                  col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0, fused_rows: int = 0,
+                  chains: int = 0) -> None:
     t = deconv_tune(int(row_ctas), int(col_ctas), int(row_stage), int(fft_values), int(col_fft_values),
-                    int(l2_group_mb), int(generic), int(fused_rows))
+                    int(l2_group_mb), int(generic), int(fused_rows), int(chains))
     _check(load().deconv_retune(plan, ctypes.byref(t)), "deconv_retune")
 
 
@@ -489,9 +491,10 @@ class Plan:
         return best, ms
 
     def retune(self, row_ctas: int = 0, col_ctas: int = 0, row_stage: int = -1, fft_values: int = 0,
-               col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0, fused_rows: int = 0) -> None:
+               col_fft_values: int = 0, l2_group_mb: int = 0, generic: int = 0, fused_rows: int = 0,
+               chains: int = 0) -> None:
         deconv_retune(self.handle, row_ctas, col_ctas, row_stage, fft_values, col_fft_values, l2_group_mb, generic,
-                      fused_rows)
+                      fused_rows, chains)
 
     def set_wait_limit(self, ns: int) -> None:
         deconv_set_wait_limit(self.handle, ns)

@@ -55,8 +55,10 @@ struct Cls {
 struct Layout {
   int B = 0, C = 0, K = 0, dtype = 0, nt = 256, kernel_per_image = 0;
   std::vector<Cls> row_cls, col_cls;
-  // Image groups of the captured loop: the row and column classes of each.
+  // Image groups of the captured loop: the row and column classes of each;
+  // chains: the groups run side by side (else one after another).
   int ngroups = 1;
+  bool chains = false;
   std::vector<std::vector<int>> grp_row, grp_col;
   std::map<int, int> tw2_off;
   long long total_tw2 = 0;
@@ -227,11 +229,42 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
   // Kernel class of every image and pass: the register-FFT passes for the
   // lengths reg_fft_params accepts (key tt * 8 + r), the generic Stockham
   // passes otherwise (key 0).
-  // Image groups of the captured loop (first fit, largest intermediate
-  // first): each group's row-spectral intermediate within the budget, so
-  // that it stays in L2 from one pass to the next while the group runs.
+  // Kernel key of every image and pass: the register-FFT class (key
+  // p2_key(v, tt, r)) where reg_fft_params accepts the length, 0 = generic.
+  std::vector<int> row_key(L.B, 0), col_key(L.B, 0);
+  // Values per thread of the power-of-two register transforms: 16 (twice the
+  // threads, so twice the resident warps) unless the tuning asks for 32.
+  // Defaults (measured on GB300): rows 16; columns 32 for power-of-two
+  // lengths, 16 for 3 * 2^k and 5 * 2^k.
+  const int vrow = (tune && tune->fft_values > 0) ? tune->fft_values : 16;
+  const int vcol_set = (tune && tune->col_fft_values > 0) ? tune->col_fft_values : 0;
+  for (int j = 0; j < L.B; ++j) {
+    const int M = d->rows[j], N = d->cols[j];
+    int tt, r, v;
+    if (allow_p2 && reg_fft_params(N, &tt, &r, &v, vrow) && p2_row_threads(L.C, 1, tt, r) <= maxthr &&
+        p2_groups_ok(p2_row_threads(L.C, 1, tt, r), tt) && p2_row_smem(L.C, N, 1, tt, L.esz, r, L.C == 1, v) <= kMaxSmem)
+      row_key[j] = p2_key(v, tt, r);
+    const int vcol = vcol_set ? vcol_set : (is_pow2_32(M) ? 32 : 16);
+    if (allow_p2 && reg_fft_params(M, &tt, &r, &v, vcol) && p2_col_threads(1, tt, r) <= maxthr &&
+        p2_col_smem(M, 1, tt, L.esz, r, v) <= kMaxSmem)
+      col_key[j] = p2_key(v, tt, r);
+  }
+  // Image groups of the captured loop.  Chains: one group per (row kernel,
+  // column kernel) pair, the groups' iterations running side by side on
+  // streams of their own.  Otherwise groups for L2 residency (first fit,
+  // largest intermediate first): each group's row-spectral intermediate
+  // within the budget, all iterations of one group before the next.
   std::vector<int> grp(L.B, 0);
-  {
+  if (tune && tune->chains) {
+    std::map<std::pair<int, int>, int> pair_grp;
+    for (int j = 0; j < L.B; ++j) {
+      auto it = pair_grp.find({row_key[j], col_key[j]});
+      if (it == pair_grp.end()) it = pair_grp.emplace(std::make_pair(row_key[j], col_key[j]), (int)pair_grp.size()).first;
+      grp[j] = it->second;
+    }
+    L.ngroups = (int)pair_grp.size();
+    L.chains = L.ngroups > 1;
+  } else {
     const int mb = (tune && tune->l2_group_mb != 0) ? tune->l2_group_mb : kDefaultGroupMiB;
     if (mb > 0) {
       const long long budget = (long long)mb << 20;
@@ -253,38 +286,23 @@ deconv_status build_layout(const deconv_dims *d, Layout *Lo, const deconv_tune *
       L.ngroups = (int)used.size();
     }
   }
-  // Per-(group, kernel) keys: the kernel key (register-FFT class, 0 =
-  // generic) plus the group times kGroupKey.
+  // Per-(group, kernel) keys: the kernel key plus the group times kGroupKey.
   constexpr int kGroupKey = 4096;
-  std::vector<int> row_key(L.B, 0), col_key(L.B, 0);
   long long g_rows = 0, g_cols = 0;
   std::map<int, long long> p2_rows, p2_cols;
   std::map<int, int> p2_row_keys;  // distinct register row kernels (any group)
-  // Values per thread of the power-of-two register transforms: 16 (twice the
-  // threads, so twice the resident warps) unless the tuning asks for 32.
-  // Defaults (measured on GB300): rows 16; columns 32 for power-of-two
-  // lengths, 16 for 3 * 2^k and 5 * 2^k.
-  const int vrow = (tune && tune->fft_values > 0) ? tune->fft_values : 16;
-  const int vcol_set = (tune && tune->col_fft_values > 0) ? tune->col_fft_values : 0;
   for (int j = 0; j < L.B; ++j) {
     const int M = d->rows[j], N = d->cols[j];
-    int tt, r, v;
-    if (allow_p2 && reg_fft_params(N, &tt, &r, &v, vrow) && p2_row_threads(L.C, 1, tt, r) <= maxthr &&
-        p2_groups_ok(p2_row_threads(L.C, 1, tt, r), tt) && p2_row_smem(L.C, N, 1, tt, L.esz, r, L.C == 1, v) <= kMaxSmem) {
-      row_key[j] = p2_key(v, tt, r);
+    if (row_key[j]) {
       p2_rows[grp[j] * kGroupKey + row_key[j]] += M;
       p2_row_keys[row_key[j]] = 1;
     } else {
       g_rows += M;
     }
-    const int vcol = vcol_set ? vcol_set : (is_pow2_32(M) ? 32 : 16);
-    if (allow_p2 && reg_fft_params(M, &tt, &r, &v, vcol) && p2_col_threads(1, tt, r) <= maxthr &&
-        p2_col_smem(M, 1, tt, L.esz, r, v) <= kMaxSmem) {
-      col_key[j] = p2_key(v, tt, r);
+    if (col_key[j])
       p2_cols[grp[j] * kGroupKey + col_key[j]] += (long long)L.C * (N / 2 + 1);
-    } else {
+    else
       g_cols += (long long)L.C * (N / 2 + 1);
-    }
   }
   const int target = kTargetCtas;
   const int rb_pref = (int)std::max<long long>(2, (g_rows + target - 1) / target);
@@ -568,7 +586,7 @@ std::vector<deconv_tune> tune_candidates(int channels) {
     for (int cfv : {16, 32})
       for (int st : channels == 1 ? std::vector<int>{0, 1} : std::vector<int>{0})
         for (int rc : {152, 608})
-          for (int cc : {152, 608}) v.push_back(deconv_tune{rc, cc, st, fv, cfv, 0, 0, 0});
+          for (int cc : {152, 608}) v.push_back(deconv_tune{rc, cc, st, fv, cfv, 0, 0, 0, 0});
   return v;
 }
 
@@ -877,10 +895,13 @@ deconv_status ensure_graph(deconv_plan_s *p) {
   if (p->gexec) return DECONV_OK;
   const Layout &L = p->L;
   const bool grouped = L.ngroups > 1 && !(p->adapt_t > 0.0);
+  const bool chains = grouped && L.chains;
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   size_t nside = 0;
-  if (grouped) {
+  if (chains) {
+    nside = (size_t)L.ngroups - 1;  // one stream per chain (the first runs on cs)
+  } else if (grouped) {
     for (int g = 0; g < L.ngroups; ++g)
       nside = std::max(nside, std::max(L.grp_row[g].size(), L.grp_col[g].size()));
   } else {
@@ -889,6 +910,7 @@ deconv_status ensure_graph(deconv_plan_s *p) {
   nside = nside > 0 ? nside - 1 : 0;
   deconv_status st = DECONV_OK;
   if (nside > 0) {
+    // side streams: the class fan-out of a pass, or one stream per chain
     if (cudaEventCreateWithFlags(&p->fan_fork, cudaEventDisableTiming) != cudaSuccess) st = DECONV_ECUDA;
     for (size_t k = 0; k < nside && st == DECONV_OK; ++k) {
       cudaStream_t sk = nullptr;
@@ -898,7 +920,7 @@ deconv_status ensure_graph(deconv_plan_s *p) {
       if (cudaEventCreateWithFlags(&ek, cudaEventDisableTiming) != cudaSuccess) st = DECONV_ECUDA;
       else p->fan_join.push_back(ek);
     }
-    if (st == DECONV_OK) p->fan_main = cs;
+    if (st == DECONV_OK && !chains) p->fan_main = cs;
   }
   // Profiling events: one before the loop and one after every pass.
   for (cudaEvent_t e : p->prof_ev) cudaEventDestroy(e);
@@ -906,7 +928,9 @@ deconv_status ensure_graph(deconv_plan_s *p) {
   p->prof_kind.clear();
   p->prof_ran = false;
   if (p->profile && st == DECONV_OK) {
-    const size_t n = (size_t)kGraphIters * (grouped ? L.ngroups : 1) * 2 * p->passes + 1;
+    // chains: the passes of different groups overlap, so only the loop's
+    // start and end are marked
+    const size_t n = chains ? 2 : (size_t)kGraphIters * (grouped ? L.ngroups : 1) * 2 * p->passes + 1;
     for (size_t k = 0; k < n && st == DECONV_OK; ++k) {
       cudaEvent_t e = nullptr;
       if (cudaEventCreate(&e) != cudaSuccess) st = DECONV_ECUDA;
@@ -920,7 +944,25 @@ deconv_status ensure_graph(deconv_plan_s *p) {
     st = DECONV_ECUDA;
   const bool prof = p->profile && st == DECONV_OK;
   if (prof && cudaEventRecordWithFlags(p->prof_ev[0], cs, cudaEventRecordExternal) != cudaSuccess) st = DECONV_ECUDA;
-  if (grouped) {
+  if (chains) {
+    // each group (one row and one column kernel class) iterates on a stream
+    // of its own; the groups share no data, so they join only at the end
+    if (st == DECONV_OK && cudaEventRecord(p->fan_fork, cs) != cudaSuccess) st = DECONV_ECUDA;
+    for (int gi = 0; gi < L.ngroups && st == DECONV_OK; ++gi) {
+      cudaStream_t sg = gi == 0 ? cs : p->fan_side[gi - 1];
+      if (gi > 0 && cudaStreamWaitEvent(sg, p->fan_fork, 0) != cudaSuccess) st = DECONV_ECUDA;
+      p->parity = 0;
+      for (int k = 0; k < kGraphIters && st == DECONV_OK; ++k) {
+        st = iterate<T>(p, sg, nullptr, nullptr, 0, 0, gi, false);
+        p->parity ^= 1;
+      }
+      if (st == DECONV_OK && gi > 0 && cudaEventRecord(p->fan_join[gi - 1], sg) != cudaSuccess) st = DECONV_ECUDA;
+    }
+    for (int gi = 1; gi < L.ngroups && st == DECONV_OK; ++gi)
+      if (cudaStreamWaitEvent(cs, p->fan_join[gi - 1], 0) != cudaSuccess) st = DECONV_ECUDA;
+    if (prof && st == DECONV_OK && cudaEventRecordWithFlags(p->prof_ev[1], cs, cudaEventRecordExternal) != cudaSuccess)
+      st = DECONV_ECUDA;
+  } else if (grouped) {
     for (int gi = 0; gi < L.ngroups && st == DECONV_OK; ++gi) {
       p->parity = 0;
       for (int k = 0; k < kGraphIters && st == DECONV_OK; ++k) {
@@ -1062,7 +1104,7 @@ deconv_status retune_t(deconv_plan_s *p, const deconv_tune *t) {
   CK(cudaStreamSynchronize(s));
   p->have_state = false;
   p->adapt_ready = false;
-  p->tune = t ? *t : deconv_tune{0, 0, -1, 0, 0, 0, 0, 0};
+  p->tune = t ? *t : deconv_tune{0, 0, -1, 0, 0, 0, 0, 0, 0};
   return DECONV_OK;
 }
 
@@ -1565,7 +1607,7 @@ deconv_status deconv_retune(deconv_plan p, const deconv_tune *t) {
             (t->fft_values != 0 && t->fft_values != 16 && t->fft_values != 32) ||
             (t->col_fft_values != 0 && t->col_fft_values != 16 && t->col_fft_values != 32) ||
             t->l2_group_mb < -1 || t->l2_group_mb > 65536 || (t->generic != 0 && t->generic != 1) ||
-            (t->fused_rows != 0 && t->fused_rows != 1)))
+            (t->fused_rows != 0 && t->fused_rows != 1) || (t->chains != 0 && t->chains != 1)))
     return DECONV_EINVAL;
   return p->L.dtype == DECONV_F32 ? retune_t<float>(p, t) : retune_t<double>(p, t);
 }
@@ -1613,7 +1655,7 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   // per CTA at 1024) keeps the kernel classes of a batch from running side
   // by side; it is tried for plans of one row class only.
   const bool one_class = p->L.row_cls.size() == 1;
-  std::vector<deconv_tune> cands{deconv_tune{0, 0, -1, 0, 0, 0, 0, 0}};  // the defaults
+  std::vector<deconv_tune> cands{deconv_tune{0, 0, -1, 0, 0, 0, 0, 0, 0}};  // the defaults
   for (const deconv_tune &t : tune_candidates(p->L.C))
     if (t.row_stage != 1 || one_class) cands.push_back(t);
   for (size_t k = 0; k < cands.size() && st == DECONV_OK; ++k) trial(cands[k]);
@@ -1626,6 +1668,13 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
       t.l2_group_mb = mb;
       trial(t);
     }
+  }
+  // Then independent chains per kernel class, for a batch.
+  if (st == DECONV_OK && bms >= 0.f && p->L.B > 1 && !(p->adapt_t > 0.0)) {
+    deconv_tune t = bt;
+    t.l2_group_mb = 0;
+    t.chains = 1;
+    trial(t);
   }
   // Then the fused row pass instead of the two row kernels.
   if (st == DECONV_OK && bms >= 0.f) {
@@ -1740,8 +1789,16 @@ deconv_status deconv_set_profiling(deconv_plan p, int32_t on) {
 }
 
 deconv_status deconv_graph_pass_times(deconv_plan p, float *ms_host) {
-  if (!p || !ms_host || !p->profile || !p->prof_ran || p->prof_ev.size() != p->prof_kind.size() + 1)
-    return DECONV_EINVAL;
+  if (!p || !ms_host || !p->profile || !p->prof_ran || p->prof_ev.size() < 2) return DECONV_EINVAL;
+  if (p->prof_kind.empty()) {  // chains: only the whole loop is timed
+    float all = 0.f;
+    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaEventElapsedTime(&all, p->prof_ev.front(), p->prof_ev.back()));
+    ms_host[0] = ms_host[1] = -1.f;
+    ms_host[2] = all / (float)kGraphIters;
+    return DECONV_OK;
+  }
+  if (p->prof_ev.size() != p->prof_kind.size() + 1) return DECONV_EINVAL;
   CK(cudaStreamSynchronize(p->stream));
   double t[2] = {0.0, 0.0};
   for (size_t k = 0; k < p->prof_kind.size(); ++k) {

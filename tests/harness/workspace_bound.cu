@@ -22,12 +22,13 @@ int main() {
     if (deconv_workspace_size(&d, &bound) != DECONV_OK) { printf("%s: unsupported\n", g.name); continue; }
     size_t mx = 0;
     std::vector<deconv_tune> all = tune_candidates(g.C);
-    all.push_back(deconv_tune{0, 0, -1, 0, 0, 0, 0, 0});
+    all.push_back(deconv_tune{0, 0, -1, 0, 0, 0, 0, 0, 0});
     for (deconv_tune t : all)
       for (int mb : {-1, 1, 24, 48, 80})
         for (int gen : {0, 1})
-          for (int fr : {0, 1}) {
-            t.l2_group_mb = mb; t.generic = gen; t.fused_rows = fr;
+          for (int fr : {0, 1})
+            for (int chn : {0, 1}) {
+            t.l2_group_mb = mb; t.generic = gen; t.fused_rows = fr; t.chains = chn;
             Layout Lt;
             if (build_layout(&d, &Lt, &t) == DECONV_OK) mx = std::max(mx, Lt.total);
           }

@@ -183,16 +183,20 @@ def test_generic_passes_on_pow2_sizes():
     assert rel_l2(xg, xo) <= 1e-5
 
 
-def test_image_groups_of_the_captured_loop_change_nothing():
+def test_image_groups_and_chains_of_the_captured_loop_change_nothing():
     # images are independent problems: running each image's 20-iteration
-    # loops before the next image's (groups of one image) gives the same
-    # bits as every pass over the whole batch (one group)
+    # loops before the next image's (groups of one image), or every kernel
+    # class's loop on a stream of its own (chains, here including a class of
+    # the generic passes), gives the same bits as every pass over the whole
+    # batch (one group)
     prob = inputs.random_problem(29, [(128, 256), (384, 384), (96, 160), (64, 64)], 7, mask_kind="random",
                                  frac=0.3, iters=45)
     one, _, _ = gpu_solve(prob, tune={"l2_group_mb": -1})
     each, _, _ = gpu_solve(prob, tune={"l2_group_mb": 1})
-    for a, b in zip(one, each):
+    chains, _, _ = gpu_solve(prob, tune={"chains": 1})
+    for a, b, c in zip(one, each, chains):
         assert np.array_equal(a, b)
+        assert np.array_equal(a, c)
     xo, _ = oracle_solve(prob)
     assert rel_l2(each, xo) <= 1e-4
 
