@@ -898,16 +898,18 @@ deconv_status ensure_graph(deconv_plan_s *p) {
   const bool chains = grouped && L.chains;
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  size_t nside = 0;
+  // Side streams besides cs: one per chain but the first (which runs on
+  // cs), or the class fan-out of a pass (its classes but the first).
+  size_t lanes = 0;
   if (chains) {
-    nside = (size_t)L.ngroups - 1;  // one stream per chain (the first runs on cs)
+    lanes = (size_t)L.ngroups;
   } else if (grouped) {
     for (int g = 0; g < L.ngroups; ++g)
-      nside = std::max(nside, std::max(L.grp_row[g].size(), L.grp_col[g].size()));
+      lanes = std::max(lanes, std::max(L.grp_row[g].size(), L.grp_col[g].size()));
   } else {
-    nside = std::max(L.row_cls.size(), L.col_cls.size());
+    lanes = std::max(L.row_cls.size(), L.col_cls.size());
   }
-  nside = nside > 0 ? nside - 1 : 0;
+  const size_t nside = lanes > 0 ? lanes - 1 : 0;
   deconv_status st = DECONV_OK;
   if (nside > 0) {
     // side streams: the class fan-out of a pass, or one stream per chain
@@ -948,6 +950,7 @@ deconv_status ensure_graph(deconv_plan_s *p) {
     // each group (one row and one column kernel class) iterates on a stream
     // of its own; the groups share no data, so they join only at the end
     if (st == DECONV_OK && cudaEventRecord(p->fan_fork, cs) != cudaSuccess) st = DECONV_ECUDA;
+    if (st == DECONV_OK && p->fan_side.size() + 1 < (size_t)L.ngroups) st = DECONV_ECUDA;  // one stream per chain
     for (int gi = 0; gi < L.ngroups && st == DECONV_OK; ++gi) {
       cudaStream_t sg = gi == 0 ? cs : p->fan_side[gi - 1];
       if (gi > 0 && cudaStreamWaitEvent(sg, p->fan_fork, 0) != cudaSuccess) st = DECONV_ECUDA;
