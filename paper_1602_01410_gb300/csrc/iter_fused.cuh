@@ -184,72 +184,20 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((fused
     const int fu = f == 0 ? M - 1 : f - 1, fd = f + 1 == M ? 0 : f + 1;
     cx<T> v[V];
     if constexpr (C > 1) {
-      // the channel groups of a row share the squared norms of a at (f,p)
-      // and (f-1,p) through the region (the norm at (f,p-1) is the left pixel's)
-      T *N0 = reinterpret_cast<T *>(Reg), *NU = N0 + N;
+      // the pixel-major prox step (norm over channels in the thread)
+      const int f0 = fbeg + rd * Rb;
+      T no_dd = T(0), no_tv = T(0);
+      finite = prox_rows_pm<T, C>(xrow, dg, yt + px0, dout + px0, P, M, N, f0, min(Rb, fend - f0), false, tau, mu,
+                                  reinterpret_cast<cx<T> *>(smem_raw), (size_t)Rb * RS, (size_t)RS, false, no_dd,
+                                  no_tv) &&
+               finite;
+      __syncthreads();  // the rows' y~ + i r are in the regions
       if (active) {
-        const T *xr = xrow(ch, f), *xu = xrow(ch, fu), *xd = xrow(ch, fd);
-        const cx<T> *dr = dg + ch * P + (long long)f * N, *dru = dg + ch * P + (long long)fu * N;
-#pragma unroll 4
-        for (int m = 0; m < V; ++m) {
-          const int p = q + TT * m + L2 * gr;
-          const int p1 = (p + 1 == N) ? 0 : p + 1;
-          const T x0 = xr[p], xup = xu[p];
-          const cx<T> d0 = dr[p], du = dru[p];
-          const T a_h = (xr[p1] - x0) + d0.x, a_v = (xd[p] - x0) + d0.y;
-          const T a_hu = (xu[p1] - xup) + du.x, a_vu = (x0 - xup) + du.y;
-          N0[p] = a_h * a_h + a_v * a_v;
-          NU[p] = a_hu * a_hu + a_vu * a_vu;
-        }
-      }
-      __syncthreads();
-      if (active) {
-        const T *xr = xrow(ch, f), *xu = xrow(ch, fu), *xd = xrow(ch, fd);
-        const cx<T> *dr = dg + ch * P + (long long)f * N, *dru = dg + ch * P + (long long)fu * N;
-        const T *N0r = reinterpret_cast<const T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)hh * RS);
-        const size_t cstride = (size_t)Rb * RS * 2;  // floats between the channels' regions of this slot
-        const T *yrow = yt + px0 + ch * P + (long long)f * N;
-#pragma unroll 4
-        for (int m = 0; m < V; ++m) {
-          const int p = q + TT * m + L2 * gr;
-          const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
-          T s0 = T(0), sl = T(0), su = T(0);
 #pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const T *n0 = N0r + c * cstride;
-            s0 += n0[p];
-            sl += n0[pm];
-            su += n0[N + p];
-          }
-          const T x0 = xr[p], xup = xu[p];
-          const cx<T> d0 = dr[p];
-          const T dlh = dr[pm].x, duv = dru[p].y;
-          const T ah0 = (xr[p1] - x0) + d0.x, av0 = (xd[p] - x0) + d0.y;
-          const T ahl = (x0 - xr[pm]) + dlh, avu = (x0 - xup) + duv;
-          const T g0 = s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0);
-          const T gl = sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0);
-          const T gu = su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0);
-          dout[px0 + ch * P + (long long)f * N + p] = mk<T>((T(1) - g0) * ah0, (T(1) - g0) * av0);
-          const T r = mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
-                            ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
-          const T yv = yrow[p];
-          finite = finite && isfinite(r) && isfinite(yv);
-          v[m] = mk<T>(yv, r);
-        }
+        for (int m = 0; m < V; ++m) v[m] = Reg[R * (q + TT * m) + gr];
       }
-      __syncthreads();  // every channel group has read the norms before the region is reused
-      if (R > 1) {      // natural order -> decimation-in-time order of the sub-transforms
-        if (active) {
-#pragma unroll
-          for (int m = 0; m < V; ++m) Reg[q + TT * m + L2 * gr] = v[m];
-        }
-        __syncthreads();
-        if (active) {
-#pragma unroll
-          for (int m = 0; m < V; ++m) v[m] = Reg[R * (q + TT * m) + gr];
-        }
-        __syncthreads();
-      }
+      // every group of the row has read its inputs before the tiles overwrite them
+      if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
     } else {
       if (active) {
         const T *xr = xrow(0, f), *xu = xrow(0, fu), *xd = xrow(0, fd);
@@ -264,13 +212,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((fused
           const T ah0 = (xrr - x0) + d0.x, av0 = (xdn - x0) + d0.y;
           const T ahl = (x0 - xl) + dl.x, avl = (xdl - xl) + dl.y;
           const T ahu = (xul - xup) + du.x, avu = (x0 - xup) + du.y;
-          const T s0 = ah0 * ah0 + av0 * av0, sl = ahl * ahl + avl * avl, su = ahu * ahu + avu * avu;
-          const T g0 = s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0);
-          const T gl = sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0);
-          const T gu = su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0);
-          dout[px0 + (long long)f * N + p] = mk<T>((T(1) - g0) * ah0, (T(1) - g0) * av0);
-          const T r = mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
-                            ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
+          const T s0 = sq2<T>(ah0, av0), sl = sq2<T>(ahl, avl), su = sq2<T>(ahu, avu);
+          const T g0 = shrink_g<T>(s0, tau, tau2), gl = shrink_g<T>(sl, tau, tau2), gu = shrink_g<T>(su, tau, tau2);
+          dout[px0 + (long long)f * N + p] = mk<T>(prox_d<T>(g0, ah0), prox_d<T>(g0, av0));
+          const T r = prox_r<T>(mu, gl, ahl, g0, ah0, gu, avu, av0);
           const T yv = yrow[p];
           finite = finite && isfinite(r) && isfinite(yv);
           Reg[p] = mk<T>(yv, r);

@@ -322,6 +322,143 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
   }
 }
 
+// The prox/dual step in explicitly rounded operations: every kernel that
+// evaluates it (the row kernels, their staged and fused variants) gets the
+// same bits, whatever multiply-adds the compiler would otherwise contract.
+template <typename T> struct Rn;
+template <> struct Rn<float> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct Rn<double> {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+// |(a, b)|^2
+template <typename T> __device__ __forceinline__ T sq2(T a, T b) { return Rn<T>::fma(a, a, Rn<T>::mul(b, b)); }
+// shrinkage factor of the (vectorial) TV prox at squared norm s: max(0, 1 - tau / sqrt(s))
+template <typename T> __device__ __forceinline__ T shrink_g(T s, T tau, T tau2) {
+  return s > tau2 ? Rn<T>::fma(-tau, rsqrt_t<T>(s), T(1)) : T(0);
+}
+// one component of d^{k+1} = (1 - g) a
+template <typename T> __device__ __forceinline__ T prox_d(T g, T a) { return Rn<T>::mul(Rn<T>::add(T(1), -g), a); }
+// r = mu D^T (v - d^{k+1}) at (f,p) from (2g - 1) a at (f,p-1), (f,p), (f-1,p):
+// mu ((2 gl - 1) ahl - (2 g0 - 1) ah0 + (2 gu - 1) avu - (2 g0 - 1) av0)
+template <typename T> __device__ __forceinline__ T prox_r(T mu, T gl, T ahl, T g0, T ah0, T gu, T avu, T av0) {
+  const T w0 = Rn<T>::fma(T(2), g0, T(-1)), wl = Rn<T>::fma(T(2), gl, T(-1)), wu = Rn<T>::fma(T(2), gu, T(-1));
+  const T h = Rn<T>::fma(wl, ahl, -Rn<T>::mul(w0, ah0)), v = Rn<T>::fma(wu, avu, -Rn<T>::mul(w0, av0));
+  return Rn<T>::mul(mu, Rn<T>::add(h, v));
+}
+
+// ------------------------------------------- forward half, prox step ---
+// Prox/dual step of a plain iteration's forward half (fixed penalty, no
+// statistics) for rows f0 .. f0 + nrows - 1 of one image, every channel,
+// pixel-major: a full warp takes a run of 32 pixels of one row, each lane
+// one pixel and all C channels of it, so the squared norm over channels of
+// the vectorial TV prox stays in the thread.  Per channel and pixel:
+//   a = D x + d,  g = max(0, 1 - tau / |a|)  (|a| over channels),
+//   d^{k+1} = (1 - g) a,  r = mu D^T (v - d^{k+1}) with v - d^{k+1} = (2g - 1) a,
+// with D the periodic forward differences (a_h = x(f,p+1) - x(f,p) + d_h,
+// a_v = x(f+1,p) - x(f,p) + d_v), so r at (f,p) needs a and g at (f,p),
+// (f,p-1) and (f-1,p).  The values at p-1 and p+1 come from the adjacent
+// lanes; at the ends of a run, lane c < C reads channel c's pixels just
+// outside it and passes them on.  Each input is read once per run: x on
+// rows f-1, f, f+1, d on rows f-1 and f, y~ on row f.  Writes d^{k+1} and
+// leaves y~ + i r of channel c, row f0 + j at reg0[c cstride + j rstride + p].
+// Every lane of a warp runs the same iterations (N is a multiple of 32);
+// the threads of a partial last warp take no run.  init: d = 0, g = 1.
+// stats: adds ||d^{k+1} - d^k||^2 of its pixels to s_dd and their TV,
+// sum_p sqrt(sum_c |D x|^2), to s_tv (per-thread partials).
+// Returns false if some r or y~ is not finite.
+template <typename T, int C, class XRow>
+__device__ __forceinline__ bool prox_rows_pm(const XRow &xrow, const cx<T> *__restrict__ dg,
+                                             const T *__restrict__ yg, cx<T> *__restrict__ dout, long long P, int M,
+                                             int N, int f0, int nrows, bool init, T tau, T mu, cx<T> *reg0,
+                                             size_t cstride, size_t rstride, bool stats, T &s_dd, T &s_tv) {
+  static_assert(C >= 1 && C <= 32, "one lane per channel at the ends of a run");
+  constexpr unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, runs = N >> 5;
+  const int ce = lane < C ? lane : 0;
+  const T tau2 = tau * tau;
+  bool finite = true;
+  for (int ck = threadIdx.x >> 5; ck < nrows * runs; ck += nw) {
+    const int j = ck / runs, base = (ck - j * runs) << 5, p = base + lane;
+    const int f = f0 + j, fu = f == 0 ? M - 1 : f - 1, fd = f + 1 == M ? 0 : f + 1;
+    const int pl = base == 0 ? N - 1 : base - 1, pe = base + 32 == N ? 0 : base + 32;
+    const long long of = (long long)f * N, ofu = (long long)fu * N;
+    T x0[C], xd[C], xu[C], yv[C];
+    cx<T> d0[C], du[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      x0[c] = xrow(c, f)[p];
+      xd[c] = xrow(c, fd)[p];
+      xu[c] = xrow(c, fu)[p];
+      yv[c] = yg[c * P + of + p];
+      d0[c] = init ? mk<T>(T(0), T(0)) : dg[c * P + of + p];
+      du[c] = init ? mk<T>(T(0), T(0)) : dg[c * P + ofu + p];
+    }
+    // channel ce's pixels just outside the run: (f, pl), (f+1, pl), (f, pe), (f-1, pe)
+    T lx = T(0), lxd = T(0), rx = T(0), rxu = T(0);
+    cx<T> dl = mk<T>(T(0), T(0));
+    if (lane < C) {
+      lx = xrow(ce, f)[pl];
+      lxd = xrow(ce, fd)[pl];
+      rx = xrow(ce, f)[pe];
+      rxu = xrow(ce, fu)[pe];
+      if (!init) dl = dg[ce * P + of + pl];
+    }
+    T s0 = T(0), su = T(0), tv = T(0), ah0[C], av0[C], avu[C];
+    T el_h = T(0), el_n = T(0);  // on lane c: a_h and |a_c|^2 of channel c at (f, pl)
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T xb = __shfl_sync(full, x0[c], 0);  // x(c, f, base)
+      T xr1 = __shfl_down_sync(full, x0[c], 1), xu1 = __shfl_down_sync(full, xu[c], 1);
+      const T erx = __shfl_sync(full, rx, c), erxu = __shfl_sync(full, rxu, c);
+      if (lane == 31) {
+        xr1 = erx;
+        xu1 = erxu;
+      }
+      const T gh = xr1 - x0[c], gv = xd[c] - x0[c];
+      ah0[c] = gh + d0[c].x;
+      av0[c] = gv + d0[c].y;
+      if (stats) tv += sq2<T>(gh, gv);
+      const T ahu = (xu1 - xu[c]) + du[c].x;
+      avu[c] = (x0[c] - xu[c]) + du[c].y;
+      s0 += sq2<T>(ah0[c], av0[c]);
+      su += sq2<T>(ahu, avu[c]);
+      if (lane == c) {
+        el_h = (xb - lx) + dl.x;
+        el_n = sq2<T>(el_h, (lxd - lx) + dl.y);
+      }
+    }
+    T sl = T(0);  // |a|^2 at (f, pl), summed in channel order (lane 0 uses it)
+#pragma unroll
+    for (int c = 0; c < C; ++c) sl += __shfl_sync(full, el_n, c);
+    const T g0 = init ? T(1) : shrink_g<T>(s0, tau, tau2);
+    const T gu = init ? T(1) : shrink_g<T>(su, tau, tau2);
+    const T gle = init ? T(1) : shrink_g<T>(sl, tau, tau2);
+    T gl = __shfl_up_sync(full, g0, 1);
+    if (lane == 0) gl = gle;
+    if (stats) s_tv += sqrt(tv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      T ahl = __shfl_up_sync(full, ah0[c], 1);
+      const T eh = __shfl_sync(full, el_h, c);
+      if (lane == 0) ahl = eh;
+      const long long o = c * P + of + p;
+      const T dnh = prox_d<T>(g0, ah0[c]), dnv = prox_d<T>(g0, av0[c]);
+      dout[o] = mk<T>(dnh, dnv);
+      if (stats) s_dd += (dnh - d0[c].x) * (dnh - d0[c].x) + (dnv - d0[c].y) * (dnv - d0[c].y);
+      const T r = prox_r<T>(mu, gl, ahl, g0, ah0[c], gu, avu[c], av0[c]);
+      finite = finite && isfinite(r) && isfinite(yv[c]);
+      reg0[c * cstride + j * rstride + p] = mk<T>(yv[c], r);
+    }
+  }
+  return finite;
+}
+
 // ----------------------------------------------------------- row (R2) ---
 // Forward half.  Each thread reads the x, d and y~ values of its own pixels
 // straight from global memory (the neighbours at p-1, p+1 and in rows i-1,
@@ -378,62 +515,19 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
   T s_dd = T(0), s_tv = T(0), s_dv = T(0);
   bool finite = true;
   cx<T> v[V];
-  // Several channels, no statistics: the channel groups of a row share the
-  // per-channel squared norms of a at (i,p) and (i-1,p) through shared memory
-  // (the norm at (i,p-1) is that of the pixel to the left), instead of each
-  // group recomputing every channel's neighbourhood.
-  bool shared_norms = false;
-  if constexpr (C > 1 && !ADAPT) shared_norms = !stats;
-  if (shared_norms) {
-    T *N0 = reinterpret_cast<T *>(Cs), *NU = N0 + N;  // this (channel, row): |a(i,p)|^2, |a(i-1,p)|^2
-    const T *xr = xg + ch * P + (long long)i * N, *xu = xg + ch * P + (long long)iu * N,
-            *xd = xg + ch * P + (long long)id * N;
-    const cx<T> *dr = dg + ch * P + (long long)i * N, *dru = dg + ch * P + (long long)iu * N;
-    if (active) {
-#pragma unroll 4
-      for (int m = 0; m < V; ++m) {
-        const int p = q + TT * m + L2 * gr;
-        const int p1 = (p + 1 == N) ? 0 : p + 1;
-        const T x0 = xr[p], xup = xu[p];
-        const cx<T> d0 = init ? mk<T>(T(0), T(0)) : dr[p], du = init ? mk<T>(T(0), T(0)) : dru[p];
-        const T a_h = (xr[p1] - x0) + d0.x, a_v = (xd[p] - x0) + d0.y;
-        const T a_hu = (xu[p1] - xup) + du.x, a_vu = (x0 - xup) + du.y;
-        N0[p] = a_h * a_h + a_v * a_v;
-        NU[p] = a_hu * a_hu + a_vu * a_vu;
-      }
-    }
-    __syncthreads();
-    if (active) {
-      const T *N0r = reinterpret_cast<const T *>(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)hh * RS);
-      const size_t cstride = (size_t)Rb * RS * 2;  // floats between the channels' regions of this row
-#pragma unroll 4
-      for (int m = 0; m < V; ++m) {
-        const int p = q + TT * m + L2 * gr;
-        const int pm = (p == 0) ? N - 1 : p - 1, p1 = (p + 1 == N) ? 0 : p + 1;
-        T s0 = T(0), sl = T(0), su = T(0);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const T *n0 = N0r + c * cstride;
-          s0 += n0[p];
-          sl += n0[pm];
-          su += n0[N + p];
-        }
-        const T x0 = xr[p], xup = xu[p];
-        const cx<T> d0 = init ? mk<T>(T(0), T(0)) : dr[p];
-        const T dlh = init ? T(0) : dr[pm].x, duv = init ? T(0) : dru[p].y;
-        const T ah0 = (xr[p1] - x0) + d0.x, av0 = (xd[p] - x0) + d0.y;
-        const T ahl = (x0 - xr[pm]) + dlh, avu = (x0 - xup) + duv;
-        const T g0 = init ? T(1) : (s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0));
-        const T gl = init ? T(1) : (sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0));
-        const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
-        dout[px0 + ch * P + (long long)i * N + p] = mk<T>((T(1) - g0) * ah0, (T(1) - g0) * av0);
-        const T r = a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
-                            ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
-        const T yv = yg[ch * P + (long long)i * N + p];
-        finite = finite && isfinite(r) && isfinite(yv);
-        v[m] = mk<T>(yv, r);
-      }
-    }
+  // Several channels, fixed penalty: the pixel-major prox step, each input
+  // read once per row and the norm over channels summed in the thread.  One
+  // channel, or penalty adaptation: every thread evaluates its own (channel,
+  // pixel) with the whole neighbourhood over channels (for one channel the
+  // neighbours are the adjacent lanes' pixels, L1 hits, and no CTA-wide
+  // barrier is needed before the transform).
+  bool pixel_major = false;
+  if constexpr (C > 1 && !ADAPT) pixel_major = true;
+  if (pixel_major) {
+    auto xrow = [&](int c, int row) -> const T * { return xg + c * P + (long long)row * N; };
+    finite = prox_rows_pm<T, C>(xrow, dg, yg, dout + px0, P, M, N, r0, nr, init, tau, a.mu,
+                                reinterpret_cast<cx<T> *>(smem_raw), (size_t)Rb * RS, (size_t)RS, stats, s_dd,
+                                s_tv);
   } else if (active) {
 #pragma unroll 4
     for (int m = 0; m < V; ++m) {
@@ -455,12 +549,12 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
         }
         const T gh = xrr - x0, gv = xdn - x0;
         const T a_h = gh + d0.x, a_v = gv + d0.y;
-        s0 += a_h * a_h + a_v * a_v;
-        tv += gh * gh + gv * gv;
+        s0 += sq2<T>(a_h, a_v);
+        tv += sq2<T>(gh, gv);
         const T a_hl = (x0 - xl) + dl.x, a_vl = (xdl - xl) + dl.y;
-        sl += a_hl * a_hl + a_vl * a_vl;
+        sl += sq2<T>(a_hl, a_vl);
         const T a_hu = (xul - xup) + du.x, a_vu = (x0 - xup) + du.y;
-        su += a_hu * a_hu + a_vu * a_vu;
+        su += sq2<T>(a_hu, a_vu);
         if (c == ch) {
           ah0 = a_h;
           av0 = a_v;
@@ -470,10 +564,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
           dv0 = d0.y;
         }
       }
-      const T g0 = init ? T(1) : (s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0));
-      const T gl = init ? T(1) : (sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0));
-      const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
-      const T dnh = (T(1) - g0) * ah0, dnv = (T(1) - g0) * av0;
+      const T g0 = init ? T(1) : shrink_g<T>(s0, tau, tau2);
+      const T gl = init ? T(1) : shrink_g<T>(sl, tau, tau2);
+      const T gu = init ? T(1) : shrink_g<T>(su, tau, tau2);
+      const T dnh = prox_d<T>(g0, ah0), dnv = prox_d<T>(g0, av0);
       const long long o = px0 + ch * P + (long long)i * N + p;
       if (ADAPT && norms) {
         // residuals of Eq. (varying_penalty): d^{i+1} - d^i and v^{i+1} - v^i
@@ -495,8 +589,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
       }
       const T r = ADAPT ? mur * (((sc1 * gl - sc) * ahl - (sc1 * g0 - sc) * ah0) +
                                  ((sc1 * gu - sc) * avu - (sc1 * g0 - sc) * av0))
-                        : a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
-                                  ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
+                        : prox_r<T>(a.mu, gl, ahl, g0, ah0, gu, avu, av0);
       const T yv = yg[ch * P + (long long)i * N + p];
       finite = finite && isfinite(r) && isfinite(yv);
       Cs[p] = mk<T>(yv, r);
@@ -512,29 +605,14 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
     return;
   }
   if (!finite) atomicOr(a.err, 1);
-  if (shared_norms) {
-    __syncthreads();  // every channel group has read the norms before the region is reused
-    if (R > 1) {  // natural order -> decimation-in-time order of the sub-transforms
-      if (active) {
+  // the rows' y~ + i r are in the regions (written by any warp on the plain path)
+  if (R > 1 || pixel_major) __syncthreads(); else group_bar<TT>(gm, bar);
+  if (active) {
 #pragma unroll
-        for (int m = 0; m < V; ++m) Cs[q + TT * m + L2 * gr] = v[m];
-      }
-      __syncthreads();
-      if (active) {
-#pragma unroll
-        for (int m = 0; m < V; ++m) v[m] = Cs[R * (q + TT * m) + gr];
-      }
-      __syncthreads();
-    }
-  } else {
-    if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
-    if (active) {
-#pragma unroll
-      for (int m = 0; m < V; ++m) v[m] = Cs[R * (q + TT * m) + gr];
-    }
-    // every group of the row has read its inputs before the tiles overwrite them
-    if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
+    for (int m = 0; m < V; ++m) v[m] = Cs[R * (q + TT * m) + gr];
   }
+  // every group of the row has read its inputs before the tiles overwrite them
+  if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   fft_reg_smem<T, V, TT, R, -1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Cs);
   if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
   if (active) {
@@ -639,12 +717,12 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
         const cx<T> du = init ? mk<T>(T(0), T(0)) : dr[p - N];
         const T gh = xrr - x0, gv = xdn - x0;
         const T a_h = gh + d0.x, a_v = gv + d0.y;
-        s0 += a_h * a_h + a_v * a_v;
-        tv += gh * gh + gv * gv;
+        s0 += sq2<T>(a_h, a_v);
+        tv += sq2<T>(gh, gv);
         const T a_hl = (x0 - xl) + dl.x, a_vl = (xdl - xl) + dl.y;
-        sl += a_hl * a_hl + a_vl * a_vl;
+        sl += sq2<T>(a_hl, a_vl);
         const T a_hu = (xul - xup) + du.x, a_vu = (x0 - xup) + du.y;
-        su += a_hu * a_hu + a_vu * a_vu;
+        su += sq2<T>(a_hu, a_vu);
         if (c == ch) {
           ah0 = a_h;
           av0 = a_v;
@@ -654,17 +732,16 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) row_fwd_p2_staged_
           dv0 = d0.y;
         }
       }
-      const T g0 = init ? T(1) : (s0 > tau2 ? T(1) - tau * rsqrt_t<T>(s0) : T(0));
-      const T gl = init ? T(1) : (sl > tau2 ? T(1) - tau * rsqrt_t<T>(sl) : T(0));
-      const T gu = init ? T(1) : (su > tau2 ? T(1) - tau * rsqrt_t<T>(su) : T(0));
-      const T dnh = (T(1) - g0) * ah0, dnv = (T(1) - g0) * av0;
+      const T g0 = init ? T(1) : shrink_g<T>(s0, tau, tau2);
+      const T gl = init ? T(1) : shrink_g<T>(sl, tau, tau2);
+      const T gu = init ? T(1) : shrink_g<T>(su, tau, tau2);
+      const T dnh = prox_d<T>(g0, ah0), dnv = prox_d<T>(g0, av0);
       dout[px0 + ch * P + (long long)i * N + p] = mk<T>(dnh, dnv);
       if (stats) {
         s_dd += (dnh - dh0) * (dnh - dh0) + (dnv - dv0) * (dnv - dv0);
         if (ch == 0) s_tv += sqrt(tv);
       }
-      const T r = a.mu * (((T(2) * gl - T(1)) * ahl - (T(2) * g0 - T(1)) * ah0) +
-                          ((T(2) * gu - T(1)) * avu - (T(2) * g0 - T(1)) * av0));
+      const T r = prox_r<T>(a.mu, gl, ahl, g0, ah0, gu, avu, av0);
       const T yv = Ys[((size_t)ch * Rb + hh) * N + p];
       finite = finite && isfinite(r) && isfinite(yv);
       Cs[p] = mk<T>(yv, r);
