@@ -185,12 +185,14 @@ typedef struct {
 } deconv_tune;
 
 /* Bound of every device-side wait, in nanoseconds (default 2e9; the paper
- * has no counterpart).  The fused row pass (deconv_tune.fused_rows) waits for flags of earlier work
- * items of the same image; a wait that reaches the bound makes its item set
- * an error word and return without its forward half, and deconv_sync then
- * returns DECONV_ETIMEOUT (the results of that call are not valid).  0
- * allows no waiting at all: any item that depends on another fails at once
- * (a test of the error path).  The captured CUDA graph is rebuilt.  ns >= 0,
+ * has no counterpart).  The inverse row half waits for the bulk copies of
+ * its row spectra into shared memory; the fused row pass
+ * (deconv_tune.fused_rows) waits for flags of earlier work items of the
+ * same image.  A wait that reaches the bound makes its block set an error
+ * word and return (the inverse half without its rows, a fused item without
+ * its forward half), and deconv_sync then returns DECONV_ETIMEOUT (the
+ * results of that call are not valid).  0 allows no waiting at all: every
+ * such wait fails at once (a test of the error path).  The captured CUDA graph is rebuilt.  ns >= 0,
  * else DECONV_EINVAL. */
 deconv_status deconv_set_wait_limit(deconv_plan plan, int64_t ns);
 

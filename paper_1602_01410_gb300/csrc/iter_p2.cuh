@@ -15,6 +15,7 @@
 //                row loads and stores and transformed in place.
 #pragma once
 
+#include "bulk.cuh"
 #include "fft.cuh"
 #include "internal.h"
 #include "iter_kernels.cuh"
@@ -171,8 +172,10 @@ template <typename T, int C, int R, int V, bool FWD = true> __host__ __device__ 
 // ----------------------------------------------------------- row (R1) ---
 // Inverse half of the row pass: Rb rows per CTA, no halo.  Inverse row DFT
 // of X + i HX -> x, T~x; z-update of y~; x to the plan's x buffer (read by
-// R2) and optionally to x_out.  The CTA's y~ rows and mask words are staged
-// into shared memory asynchronously while the transforms run.  Statistics:
+// R2) and optionally to x_out.  The rows' spectra arrive in shared memory
+// by bulk copies (one per row, the TMA engine, completed on an mbarrier
+// with a bounded wait); the CTA's y~ rows and mask words are staged with
+// cp.async while the transforms run.  Statistics:
 // ||dz||^2 and the data-fit half of the objective.  ROW_ADJ (reverse pass):
 // xbuf <- b, yt <- yt + T~b instead of the z-update.
 // Shared memory: [one region of R transpose tiles per (channel, row), which
@@ -206,8 +209,23 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
   const cx<T> *tw2 = reinterpret_cast<const cx<T> *>(a.tw2) + (V == 32 ? Dp->tw2_row : Dp->tw16_row);
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
   const cx<T> *twab = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->twab_row;
+  // The row spectra (N/2 + 1 pairs, contiguous) arrive in the rows' regions
+  // by bulk copies, one per (channel, row); each region holds them (RS >= N
+  // + 2 elements) and starts on a 16-byte boundary.
+  static_assert(RS >= R * V * TT + 2 && (RS * sizeof(cx<T>)) % 16 == 0, "row region holds the row spectrum");
+  __shared__ uint64_t spec_bar;  // completion of the spectra's bulk copies
+  const bool spec_in = !init;    // iteration and reverse modes transform the row spectra
 
   griddep_wait();
+  if (spec_in && threadIdx.x == 0) {
+    const unsigned row_bytes = (unsigned)(Nh * sizeof(cpair<T>));
+    mbar_init(&spec_bar);
+    mbar_arrive_expect_tx(&spec_bar, row_bytes * (unsigned)(C * nr));
+    for (int c = 0; c < C; ++c)
+      for (int h = 0; h < nr; ++h)
+        bulk_g2s(reinterpret_cast<cx<T> *>(smem_raw) + (size_t)(c * Rb + h) * RS,
+                 a.S_in + Dp->spec + ((long long)c * M + r0 + h) * Nh, row_bytes, &spec_bar);
+  }
   if (!init && !adj) {
     for (int c = 0; c < C; ++c) {
       copy_async<T>(Ys + (size_t)c * Rb * N, yt + px0 + c * P + (long long)r0 * N, nr * N, threadIdx.x, blockDim.x);
@@ -216,6 +234,18 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
     }
   }
   cp_async_commit();
+  if (spec_in) {
+    __syncthreads();  // the barrier's initialisation is visible to every thread
+    const bool ok = mbar_wait(&spec_bar, 0, a.wait_ns);
+    if (!__syncthreads_and(ok)) {  // uniform: the whole CTA leaves, its rows untouched
+      if (threadIdx.x == 0) {
+        atomicOr(a.err, 2);
+        (void)mbar_wait(&spec_bar, 0, a.wait_ns);  // the copies still in flight
+      }
+      cp_async_wait_all();
+      return;
+    }
+  }
 
   const bool stats = a.partials != nullptr;  // per-thread partials in T, FP64 only for the reduction
   T s_dz = T(0), s_fit = T(0);
@@ -226,7 +256,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
 #pragma unroll
       for (int j = 0; j < V; ++j) v[j] = mk<T>(yt[rowp + reg_pos<V, TT>(q, j) + L2 * gr], T(0));
     } else {
-      const cpair<T> *src = a.S_in + Dp->spec + ((long long)ch * M + i) * Nh;
+      const cpair<T> *src = reinterpret_cast<const cpair<T> *>(Ex);
 #pragma unroll
       for (int m = 0; m < V; ++m) {
         const int n = R * (q + TT * m) + gr;
@@ -235,7 +265,11 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
       }
     }
   }
-  if (!init) fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Ex);
+  if (!init) {
+    // every group of the row has read the spectrum before the tiles overwrite it
+    if (R > 1) __syncthreads(); else group_bar<TT>(gm, bar);
+    fft_reg<T, V, TT, R, +1>(v, active, tile, q, gm, bar, gr, tw2, tw3, twab, Ex);
+  }
   cp_async_wait_all();
   __syncthreads();
   if (active && adj) {
@@ -795,7 +829,7 @@ template <typename T, int TT, int R, bool EXT, int V>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((V == 16 && sizeof(T) == 4) ? 80 : 128)
     col_pass_p2_kernel(ColArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, SR = R * GS + 4;
+  constexpr int GS = reg_group_stride<V, TT>(), SR = R * GS + 4;
   const int wi = blockIdx.x;
   const ImageDesc *Dp = &a.desc[find_item(a.desc, a.cls_imgs, a.nimg, wi, false)];
   const int M = Dp->M, N = Dp->N, Nh = Dp->Nh;
