@@ -20,6 +20,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Bound of the wait for copies still in flight after a wait ran out (they
+// complete in microseconds), independent of the caller's limit so that a
+// block never leaves while a copy into its shared memory is pending.
+constexpr long long kDrainNs = 1000000000LL;
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // Barrier with one expected arrival per phase (the issuing thread's).

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
     if (!__syncthreads_and(ok)) {  // uniform: the whole CTA leaves, its rows untouched
       if (threadIdx.x == 0) {
         atomicOr(a.err, 2);
-        (void)mbar_wait(&spec_bar, 0, a.wait_ns);  // the copies still in flight
+        (void)mbar_wait(&spec_bar, 0, kDrainNs);  // the copies still in flight land before the block leaves
       }
       cp_async_wait_all();
       return;

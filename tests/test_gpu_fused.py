@@ -9,8 +9,10 @@ oracle, and its bounded waits.
   boundary and two items up) and many rows per item, over 45 iterations
   (two replays of the captured 20-iteration loop);
 * a wait limit of 0 (no waiting allowed): every item that depends on
-  another gives up at once, the call reports DECONV_ETIMEOUT, and the plan
-  works again once the limit is restored.
+  another gives up at once (fused row pass), or every inverse row half
+  gives up on the bulk copies of its row spectra (two-kernel row pass); the
+  call reports DECONV_ETIMEOUT, and the plan works again once the limit is
+  restored.
 
 Waits in these tests are bounded at 50 ms."""
 import numpy as np
@@ -72,7 +74,8 @@ def test_fused_row_pass_matches_the_two_kernels_and_the_oracle(C, kind, sizes, K
         assert rel_l2([a], [b]) <= 1e-4
 
 
-def test_wait_limit_zero_reports_a_timeout_and_the_plan_recovers():
+@pytest.mark.parametrize("fused", [1, 0])  # the fused items' flags / the inverse half's bulk copies
+def test_wait_limit_zero_reports_a_timeout_and_the_plan_recovers(fused):
     import torch
     import paper_1602_01410_gb300 as pkg
     prob = inputs.random_problem(95, [(128, 128), (96, 160)], 5, mask_kind="random", frac=0.3, iters=3)
@@ -81,7 +84,7 @@ def test_wait_limit_zero_reports_a_timeout_and_the_plan_recovers():
     mask = torch.tensor(np.concatenate([m.ravel() for m in prob.mask]), dtype=torch.uint8, device=dev)
     y = torch.tensor(np.concatenate([a.ravel() for a in prob.y]), dtype=torch.float32, device=dev)
     plan = pkg.Plan(prob.shapes, h, mask, prob.lam, prob.mu)
-    plan.retune(row_ctas=608, fused_rows=1)  # several row blocks per image: items wait on one another
+    plan.retune(row_ctas=608, fused_rows=fused)  # several row blocks per image: items wait on one another
     plan.set_wait_limit(0)
     plan.solve(y, 3)
     assert plan.sync() == pkg.DECONV_ETIMEOUT
