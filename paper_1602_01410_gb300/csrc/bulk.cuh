@@ -48,6 +48,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                : "memory");
 }
 
+// Prefetch into L2 (a hint with no completion to wait for) of the 16-byte
+// granules covering [src, src + bytes): the span is widened to 16-byte
+// boundaries, as the bulk prefetch requires, so the caller's buffer must
+// own the granules around its ends (the plan's buffers start on 256-byte
+// boundaries and are padded to them).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(src) + bytes + 15) & ~uintptr_t(15);
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+
 // True once the phase of the given parity has completed.
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, unsigned parity) {
   unsigned ok;

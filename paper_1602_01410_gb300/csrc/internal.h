@@ -84,6 +84,7 @@ template <typename T> struct RowArgs {
   T *halo;
   int items;
   long long wait_ns;
+  int prefetch;  // forward half: L2 prefetch of the block's input rows (the state does not fit L2)
 };
 
 template <typename T> struct ColArgs {

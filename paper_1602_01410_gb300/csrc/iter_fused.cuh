@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((fused
     const int f = fbeg + rd * Rb + hh;
     const bool active = ch < C && f < fend;
     const int fu = f == 0 ? M - 1 : f - 1, fd = f + 1 == M ? 0 : f + 1;
+    if (a.prefetch)
+      prefetch_fwd_rows<T, C>(xrow, dg, yt + px0, P, M, N, fbeg + rd * Rb, min(Rb, fend - (fbeg + rd * Rb)), false);
     cx<T> v[V];
     if constexpr (C > 1) {
       // the pixel-major prox step (norm over channels in the thread)

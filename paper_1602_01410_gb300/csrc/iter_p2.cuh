@@ -386,6 +386,33 @@ template <typename T> __device__ __forceinline__ T prox_r(T mu, T gl, T ahl, T g
   return Rn<T>::mul(mu, Rn<T>::add(h, v));
 }
 
+// L2 prefetch of every row the forward half of rows f0 .. f0 + nrows - 1
+// reads, every channel: x on rows f0 - 1 .. f0 + nrows (periodic), d on rows
+// f0 - 1 .. f0 + nrows - 1 (unless init), y~ on rows f0 .. f0 + nrows - 1.
+// Issued by the lanes of warp 0, one bulk prefetch per row, so that the
+// loads of the block's later pixels find their rows in L2.  A row need not
+// start on a 16-byte boundary (the images before it in the batch can have
+// any size); bulk_prefetch_l2 widens each span to whole 16-byte granules,
+// which stay inside the plan's 256-byte aligned, padded buffers.
+template <typename T, int C, class XRow>
+__device__ __forceinline__ void prefetch_fwd_rows(const XRow &xrow, const cx<T> *dg, const T *yg, long long P, int M,
+                                                  int N, int f0, int nrows, bool init) {
+  if (threadIdx.x >= 32) return;
+  const int nx = nrows + 2, nd = init ? 0 : nrows + 1, per = nx + nd + nrows;
+  for (int t = threadIdx.x; t < C * per; t += 32) {
+    const int c = t / per, r = t - c * per;
+    if (r < nx) {
+      const int row = (f0 - 1 + r + M) % M;
+      bulk_prefetch_l2(xrow(c, row), N * sizeof(T));
+    } else if (r < nx + nd) {
+      const int row = (f0 - 1 + (r - nx) + M) % M;
+      bulk_prefetch_l2(dg + c * P + (long long)row * N, N * sizeof(cx<T>));
+    } else {
+      bulk_prefetch_l2(yg + c * P + (long long)(f0 + r - nx - nd) * N, N * sizeof(T));
+    }
+  }
+}
+
 // ------------------------------------------- forward half, prox step ---
 // Prox/dual step of a plain iteration's forward half (fixed penalty, no
 // statistics) for rows f0 .. f0 + nrows - 1 of one image, every channel,
@@ -531,8 +558,10 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
   const cx<T> *tw3 = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->tw3_row;
   const cx<T> *twab = reinterpret_cast<const cx<T> *>(a.tw2) + Dp->twab_row;
   const unsigned gm = group_mask(TT);
+  auto xrow = [&](int c, int row) -> const T * { return xg + c * P + (long long)row * N; };
 
   griddep_wait();
+  if (a.prefetch) prefetch_fwd_rows<T, C>(xrow, dg, yg, P, M, N, r0, nr, init);
   // Penalty: fixed, or per image (adaptation): tau = lambda / mu^i, r with
   // mu^{i+1} and d^{i+1} rescaled by s (v - s d^{i+1} = ((1+s) g - s) a).
   const bool norms = ADAPT && a.mode == ROW_NORMS;
@@ -558,7 +587,6 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
   bool pixel_major = false;
   if constexpr (C > 1 && !ADAPT) pixel_major = true;
   if (pixel_major) {
-    auto xrow = [&](int c, int row) -> const T * { return xg + c * P + (long long)row * N; };
     finite = prox_rows_pm<T, C>(xrow, dg, yg, dout + px0, P, M, N, r0, nr, init, tau, a.mu,
                                 reinterpret_cast<cx<T> *>(smem_raw), (size_t)Rb * RS, (size_t)RS, stats, s_dd,
                                 s_tv);

@@ -21,6 +21,7 @@ namespace {
 
 constexpr int kGraphIters = 20;          // iterations per captured graph (even: d ping-pong returns to 0)
 constexpr int kTargetCtas = 2 * 152;     // aim for two CTAs per SM on a 152-SM GB300
+constexpr size_t kL2PrefetchMin = (size_t)64 << 20;  // workspace above which the forward half prefetches its rows
 constexpr size_t kMaxSmem = 227 * 1024 - 2048;  // opt-in dynamic shared memory per CTA, minus static use
 constexpr size_t kAlign = 256;
 
@@ -676,6 +677,9 @@ RowArgs<T> row_args(const deconv_plan_s *p, const Cls &c, int mode, const T *d_i
   a.halo = p->at<T>(L.o_halo);
   a.items = c.cfg.grid;
   a.wait_ns = p->wait_ns;
+  // A state that fits comfortably in the 126 MB L2 stays there from pass to
+  // pass; only a larger one gains from the forward half's row prefetch.
+  a.prefetch = p->L.total > kL2PrefetchMin ? 1 : 0;
   if (p->adapt_t > 0.0) {
     a.mu_img = p->at<double>(L.o_mu);
     a.mu_prev_img = a.mu_img + L.B;
