@@ -208,10 +208,11 @@ deconv_status deconv_get_tune(deconv_plan plan, deconv_tune *t);
  * builds the CUDA graph; the plan's options apply; the fastest repetition
  * counts) under the default tuning and each candidate (row_ctas and col_ctas
  * in {152, 608}, fft_values and col_fft_values in {16, 32}, and for one
- * channel and one row class row_stage in {0, 1}); then, for a batch, the
- * image-group budgets l2_group_mb in {24, 48, 80} on the fastest of
- * those, the chains (chains = 1), and the fused row pass (fused_rows = 1)
- * on the fastest so far.
+ * channel and one row class row_stage in {0, 1}); then, for a problem of
+ * at most 2^20 channel-pixels, the shared-memory passes (generic = 1) on
+ * the fastest of those; then, for a batch, the image-group budgets
+ * l2_group_mb in {24, 48, 80} and the chains (chains = 1), and the fused
+ * row pass (fused_rows = 1), each on the fastest so far.
  * Keeps the fastest (best, best_ms_per_iter: nullable host outputs)
  * and leaves the plan in it with no iteration state.  y: device, batch
  * layout.  Synchronous. */

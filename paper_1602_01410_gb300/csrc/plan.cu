@@ -1666,6 +1666,16 @@ deconv_status deconv_autotune(deconv_plan p, const void *y, int32_t trial_iters,
   for (const deconv_tune &t : tune_candidates(p->L.C))
     if (t.row_stage != 1 || one_class) cands.push_back(t);
   for (size_t k = 0; k < cands.size() && st == DECONV_OK; ++k) trial(cands[k]);
+  // Then the shared-memory (Stockham) passes, for a small problem: there the
+  // register transforms give each row or column only L/16 or L/32 threads
+  // (4 for a 64-point FP64 row) and run long dependent chains per thread.
+  long long px = 0;
+  for (size_t b = 0; b < p->rows.size(); ++b) px += (long long)p->rows[b] * p->cols[b] * p->L.C;
+  if (st == DECONV_OK && bms >= 0.f && px <= (1LL << 20)) {
+    deconv_tune t = bt;
+    t.generic = 1;
+    trial(t);
+  }
   // Then the image-group budget of the captured loop, for a batch.
   if (st == DECONV_OK && bms >= 0.f && p->L.B > 1 && !(p->adapt_t > 0.0)) {
     const deconv_tune shape = bt;
