@@ -2,7 +2,8 @@
 // launch tuning a plan can be retuned to (the autotuner's candidates, image
 // groups, the generic passes, the fused row pass), for several batch
 // geometries: compiled against the library's plan.cu and linked with its
-// other objects; exit status = number of geometries whose bound is short.
+// other objects; exit status = number of geometries whose bound is short,
+// plus one if some layout puts a bulk-read buffer off a kAlign boundary.
 #include "plan.cu"
 #include <cstdio>
 int main() {
@@ -12,7 +13,7 @@ int main() {
     {"c4", {1280,1536,512,1536,1536,512,768,1024,512,1536,1280,1280,1024,1024,1024,1024,768,1024,512,1024,1536,1280,1536,512,1280,768,512,512,1536,512,512,1280}, {}, 3, 13},
     {"gen", {96,45,60}, {160,75,54}, 1, 7}, {"rgb", {64,45}, {80,50}, 3, 5}, {"c5", {512,512,512,512,512,512,512,512}, {}, 1, 15},
     {"odd", {100, 75, 243}, {90, 125, 64}, 1, 5}};
-  int bad = 0;
+  int bad = 0, misaligned = 0;
   for (auto &g : gs) {
     if (g.N.empty()) g.N = g.M;
     deconv_dims d{};
@@ -30,10 +31,20 @@ int main() {
             for (int chn : {0, 1}) {
             t.l2_group_mb = mb; t.generic = gen; t.fused_rows = fr; t.chains = chn;
             Layout Lt;
-            if (build_layout(&d, &Lt, &t) == DECONV_OK) mx = std::max(mx, Lt.total);
+            if (build_layout(&d, &Lt, &t) == DECONV_OK) {
+              mx = std::max(mx, Lt.total);
+              // The buffers the bulk copies and L2 prefetches read start on
+              // kAlign boundaries and the workspace is padded to one, so a
+              // prefetch widened to 16-byte granules stays inside its buffer.
+              for (size_t o : {Lt.o_yt, Lt.o_d0, Lt.o_d1, Lt.o_Sa, Lt.o_Sb, Lt.o_xbuf, Lt.o_halo, Lt.total})
+                if (o % kAlign != 0) {
+                  printf("%s: offset %zu not on a %zu-byte boundary\n", g.name, o, kAlign);
+                  ++misaligned;
+                }
+            }
           }
     printf("%s: bound %zu exact max %zu slack %zd %s\n", g.name, bound, mx, (ssize_t)(bound - mx), bound >= mx ? "ok" : "TOO SMALL");
     if (bound < mx) ++bad;
   }
-  return bad;
+  return bad + (misaligned ? 1 : 0);
 }
