@@ -264,7 +264,7 @@ def subset_problem(prob, idx):
 # workload's pixels).  A workload without a capture of the current kernels
 # reports traffic null.
 ITER_TRAFFIC_BYTES_PER_PX = {
-    "c4": (64.01, "profiles/traffic_c4_1536_rgb_ncu.md: ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+    "c4": (63.85, "profiles/traffic_c4_1536_rgb_ncu.md: ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
                   "three kernels of one iteration on the four 1536x1536 RGB frames (cold cache), per channel-pixel, "
                   "times the pixels of one iteration"),
 }
