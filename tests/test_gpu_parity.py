@@ -263,3 +263,22 @@ def test_vectorial_tv_register_passes_without_stats():
     xo, _ = oracle_solve(prob)
     for a, b in zip(xg, xo):
         assert rel_l2([a], [b]) <= 3e-5
+
+
+@pytest.mark.parametrize("C,kind,sizes", [
+    (1, "random", [(90, 75), (1024, 1024), (768, 768)]),
+    (3, "bayer", [(90, 75), (768, 768), (512, 512)]),
+])
+def test_forward_row_prefetch_on_rows_off_16_byte_boundaries(C, kind, sizes):
+    # A workspace above the plan's 64 MiB threshold turns on the forward
+    # half's L2 prefetch of its input rows; the 90 x 75 first image (6,750
+    # pixels per channel) puts every row of the images after it off a
+    # 16-byte boundary, so each prefetch span must be widened to whole
+    # granules inside its buffer.
+    import paper_1602_01410_gb300 as pkg
+    d, _keep = pkg.make_dims([m for m, n in sizes], [n for m, n in sizes], 7, channels=C)
+    assert pkg.deconv_workspace_size(d) > 64 << 20
+    prob = inputs.random_problem(61 + C, sizes, 7, mask_kind=kind, channels=C, frac=0.3, iters=2)
+    xg, _, _ = gpu_solve(prob)
+    xo, _ = oracle_solve(prob)
+    assert rel_l2(xg, xo) <= 2e-5  # two FP32 iterations (one: <= 1e-5 in the tests above)
