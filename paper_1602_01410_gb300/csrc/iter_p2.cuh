@@ -521,10 +521,13 @@ __device__ __forceinline__ bool prox_rows_pm(const XRow &xrow, const cx<T> *__re
 }
 
 // ----------------------------------------------------------- row (R2) ---
-// Forward half.  Each thread reads the x, d and y~ values of its own pixels
-// straight from global memory (the neighbours at p-1, p+1 and in rows i-1,
-// i+1 are read by adjacent lanes and by the CTAs of adjacent rows, so they
-// come from L1/L2).  From them: the prox factor g at (i,p), (i,p-1), (i-1,p)
+// Forward half.  When the plan's state exceeds L2, warp 0 first prefetches
+// the block's input rows into L2 (prefetch_fwd_rows).  Several channels,
+// fixed penalty: the pixel-major prox step (prox_rows_pm).  Otherwise each
+// thread reads the x, d and y~ values of its own pixels straight from
+// global memory (the neighbours at p-1, p+1 and in rows i-1, i+1 are read
+// by adjacent lanes and by the CTAs of adjacent rows, so they come from
+// L1/L2).  From them: the prox factor g at (i,p), (i,p-1), (i-1,p)
 // (norm over channels), d^{i+1} = (1-g) a, r = mu D^T (v - d^{i+1}) with
 // v - d^{i+1} = (2g - 1) a; then the forward row DFT of y~ + i r, split into
 // (Y_row, R_row).  Statistics: ||dd||^2 and the TV half of the objective.
