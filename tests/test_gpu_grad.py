@@ -109,7 +109,7 @@ def test_autograd_function():
     loss = pkg.DeconvLoss.apply(lam, h, y, mask, xt, prob.shapes, prob.mu, 4)
     (3.0 * loss).backward()
     Lo, dlo, dho = oracle_grad(prob, 4)
-    assert abs(float(loss) - Lo) <= 1e-5 * Lo
+    assert abs(float(loss.detach()) - Lo) <= 1e-5 * Lo
     assert abs(float(lam.grad) - 3 * dlo) <= 2e-3 * abs(3 * dlo)
     assert np.max(np.abs(h.grad.double().cpu().numpy() - 3 * dho)) <= 2e-3 * np.max(np.abs(3 * dho))
 
