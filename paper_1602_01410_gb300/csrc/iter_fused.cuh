@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((fused
     row_fused_p2_kernel(RowArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int GS = reg_group_stride<V, TT>(), L2 = V * TT, RS = R * GS;
+  static_assert((R * V * TT) % 32 == 0, "the pixel-major step takes whole 32-pixel runs of a row");
   __shared__ unsigned long long s_ticket;
   __shared__ int s_ok;
   griddep_wait();

@@ -587,6 +587,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 512 : 256) __maxnreg__((row_r
   // pixel) with the whole neighbourhood over channels (for one channel the
   // neighbours are the adjacent lanes' pixels, L1 hits, and no CTA-wide
   // barrier is needed before the transform).
+  static_assert((R * V * TT) % 32 == 0, "the pixel-major step takes whole 32-pixel runs of a row");
   bool pixel_major = false;
   if constexpr (C > 1 && !ADAPT) pixel_major = true;
   if (pixel_major) {
