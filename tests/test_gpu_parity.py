@@ -172,6 +172,10 @@ def test_pow2_passes_vectorial_tv_and_stats():
     for j in range(2):
         assert rel_l2([xg[j]], [xo[j]]) <= 3e-5
         assert np.allclose(sg[j][:, 2], so[j][:, 3], rtol=1e-4)
+        # ||dd||^2 (the forward half's pixel-major step, summed over the
+        # three channels) and ||dz||^2, every iteration
+        assert np.allclose(sg[j][:, 0], so[j][:, 0], rtol=2e-3, atol=1e-12)
+        assert np.allclose(sg[j][:, 1], so[j][:, 1], rtol=2e-3, atol=1e-12)
 
 
 def test_generic_passes_on_pow2_sizes():
@@ -237,6 +241,10 @@ def test_mixed_radix_vectorial_tv_and_stats():
     for j in range(2):
         assert rel_l2([xg[j]], [xo[j]]) <= 3e-5
         assert np.allclose(sg[j][:, 2], so[j][:, 3], rtol=1e-4)
+        # ||dd||^2 (the forward half's pixel-major step, summed over the
+        # three channels) and ||dz||^2, every iteration
+        assert np.allclose(sg[j][:, 0], so[j][:, 0], rtol=2e-3, atol=1e-12)
+        assert np.allclose(sg[j][:, 1], so[j][:, 1], rtol=2e-3, atol=1e-12)
 
 
 def test_mixed_radix_twenty_iterations():
